@@ -1,0 +1,228 @@
+/*
+ * lagh.h -- C ABI of the GB300 (sm_103a) Lagrangian hydrodynamics library.
+ *
+ * The library advances the semi-discrete full-order model of "Reduced order
+ * models for Lagrangian hydrodynamics" (arXiv 2104.11404), Section 2:
+ *
+ *   M_V dv/dt = -F(v,e,x) . 1,   M_E de/dt = F(v,e,x)^T . v,   dx/dt = v
+ *                                                        (eq:fom, eq:combinedForce)
+ *
+ * on a Cartesian box mesh with an H1 Q_k kinematic space (positions x,
+ * velocities v) and a discontinuous L2 Q_{k-1} thermodynamic space (specific
+ * internal energy e), with the RK2-average integrator (eq:RK2-avg) and the
+ * automatic time step control of Section 2.2.3 (estimate eq:adaptive-timestep).
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Layout.  Kinematic vectors (v, x, F.1, accelerations) have N_V = dim * nnodes
+ *   entries, component major: entry [c * nnodes + node].  Nodes are numbered
+ *   lexicographically with x fastest: node = I + n0 (J + n1 K), n_c = n_c^el k + 1.
+ *   Thermodynamic vectors (e, F^T.v) have N_E = nelem * k^dim entries, element
+ *   major (elements lexicographic, x fastest), dofs lexicographic inside the
+ *   element.  All values are IEEE double.
+ * Pointers.  "device" pointers must be CUDA device (or managed) memory; "host
+ *   or device" pointers may be either (the library copies with the CUDA
+ *   unified address space).  The caller owns every pointer it passes; the
+ *   library never frees or keeps them after the call returns.
+ * Streams.  Work is ordered on the stream given to lh_create (a cudaStream_t
+ *   passed as void*; NULL = the legacy default stream).  Calls that return a
+ *   host value (estimates, iteration counts, statistics, get_state)
+ *   synchronize that stream before returning; the others only enqueue.
+ * Errors.  Every function returns an lh_status.  On failure lh_last_error(ctx)
+ *   describes the cause.  Conditions detected on the device (tangled element,
+ *   non-finite state, CG not converged, dt collapse, barrier time-out) are
+ *   reported by the next call that synchronizes.
+ * Memory.  lh_create allocates every work array of the context; no other
+ *   call of a single-instance context allocates device memory.
+ */
+#ifndef LAGH_H
+#define LAGH_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LH_API __attribute__((visibility("default")))
+#else
+#define LH_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lh_status {
+  LH_OK = 0,
+  LH_EINVAL = 1,       /* invalid argument or descriptor */
+  LH_ENOMEM = 2,       /* device allocation failed */
+  LH_ECUDA = 3,        /* a CUDA runtime call failed */
+  LH_ETANGLED = 4,     /* |J| <= 0 at a quadrature point (inverted element) */
+  LH_ENONFINITE = 5,   /* NaN or Inf in the state */
+  LH_EDTMIN = 6,       /* step size collapsed below dt_min_frac * t_final */
+  LH_ECG = 7,          /* CG did not reach cg_rtol within cg_maxit iterations */
+  LH_ETIMEOUT = 8,     /* a device-wide barrier waited longer than its limit */
+  LH_EUNSUPPORTED = 9  /* valid but not built (order/dimension/quadrature) */
+} lh_status;
+
+typedef enum lh_precision {
+  LH_FP64 = 0,  /* every step in double precision */
+  LH_MIXED = 1  /* quadrature-point stress and the element force matrix in
+                   FP32; positions, time integration, CG residuals and dot
+                   products, F.1 / F^T.v contractions and energy in FP64 */
+} lh_precision;
+
+typedef enum lh_problem_id {
+  LH_SEDOV = 1,         /* point blast, Section 6.1.2 */
+  LH_TAYLOR_GREEN = 2,  /* Taylor-Green vortex, Section 6.1.3 (2D: with its
+                           manufactured energy source) */
+  LH_GRESHO = 3,        /* Gresho vortex, Section 6.1.1 */
+  LH_UNIFORM = 4        /* uniform gas at rest (tests) */
+} lh_problem_id;
+
+/* Cartesian box [lo, hi] split into nx x ny (x nz) equal elements. */
+typedef struct lh_mesh_desc {
+  int32_t dim;              /* 2 or 3 */
+  int32_t nx, ny, nz;       /* elements per direction (nz unused in 2D) */
+  double lo[3], hi[3];
+} lh_mesh_desc;
+
+/* Discretisation: H1 order k (Q_k / Q_{k-1} pair) and Gauss-Legendre points
+ * per direction.  Built: dim 2 with k = 1, 2, 3 and dim 3 with k = 1, 2, each
+ * with nq = 2k. */
+typedef struct lh_disc_desc {
+  int32_t order;
+  int32_t nq;
+} lh_disc_desc;
+
+/* Physics and control constants.  lh_default_phys fills the defaults of
+ * Section 2.2.3 (cfl = 0.5, cfl_mu = 2.5, beta1 = 0.85, beta2 = 1.02,
+ * gamma_dt = 0.8) and q1 = 0.5, q2 = 2, cg_rtol = 1e-14, cg_maxit = 500,
+ * dt_min_frac = 1e-12. */
+typedef struct lh_phys_desc {
+  int32_t problem;       /* lh_problem_id */
+  int32_t visc;          /* artificial viscosity on (1) / off (0) */
+  int32_t source;        /* manufactured energy source (Taylor-Green 2D) */
+  int32_t cg_maxit;
+  double gamma;          /* adiabatic index of eq:EOS */
+  double blast_energy;   /* Sedov: total energy deposited in the origin element */
+  double e_uniform;      /* LH_UNIFORM: specific internal energy */
+  double cfl, cfl_mu;    /* alpha and alpha_mu of eq:adaptive-timestep */
+  double beta1, beta2, gamma_dt;  /* step control constants, Section 2.2.3 */
+  double q1, q2;         /* linear and quadratic viscosity coefficients */
+  double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2 */
+  double dt_min_frac;    /* dt < dt_min_frac * t_final -> LH_EDTMIN */
+} lh_phys_desc;
+
+typedef struct lh_layout_info {
+  int64_t nv;            /* N_V = dim * nnodes */
+  int64_t ne;            /* N_E = nelem * k^dim */
+  int64_t nqp;           /* nelem * nq^dim */
+  int64_t nelem, nnodes;
+  int32_t dim, order, nq;
+  int32_t ndof_h1;       /* (k+1)^dim nodes per element */
+  int32_t ndof_l2;       /* k^dim energy dofs per element */
+  int32_t nqe;           /* nq^dim quadrature points per element */
+  int32_t nodes_per_dim[3];
+  int32_t precision;     /* lh_precision */
+  int64_t n_essential;   /* essential (wall-normal) velocity components */
+} lh_layout_info;
+
+typedef struct lh_run_stats {
+  int64_t steps;         /* accepted steps */
+  int64_t rejects;       /* repeated step attempts (dt >= tau) */
+  int64_t cg_iters;      /* CG iterations summed over all solves */
+  double t;              /* time reached */
+  double dt;             /* next proposed step size */
+  double energy0;        /* total energy 1/2 v.M_V.v + 1.M_E.e before the run */
+  double energy;         /* ... after the run */
+  double wall_ms;        /* time-loop wall clock (CUDA events on the stream) */
+} lh_run_stats;
+
+typedef struct lh_ctx lh_ctx;
+typedef struct lh_batch lh_batch;
+
+LH_API void lh_default_phys(lh_phys_desc* phys);
+LH_API const char* lh_status_string(lh_status s);
+
+/* Creates a context: validates the descriptors, builds the basis tables and
+ * quadrature data of the initial mesh, allocates every work array on the
+ * device and leaves the state uninitialised.  precision: lh_precision.
+ * stream: cudaStream_t as void*.  Errors: LH_EINVAL, LH_EUNSUPPORTED,
+ * LH_ENOMEM, LH_ECUDA.  *out is NULL on failure. */
+LH_API lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* disc,
+                    const lh_phys_desc* phys, int32_t precision, void* stream,
+                    lh_ctx** out);
+/* Frees every device and host resource of the context (NULL is allowed). */
+LH_API lh_status lh_destroy(lh_ctx* ctx);
+/* Message of the last failing call on this context ("" if none). */
+LH_API const char* lh_last_error(const lh_ctx* ctx);
+LH_API lh_status lh_layout(const lh_ctx* ctx, lh_layout_info* info);
+
+/* Initial condition of the problem (Section 6.1): x at the H1 nodes of the
+ * box, v interpolated at the H1 nodes, e interpolated at the L2 nodes (Sedov:
+ * e_0 = E_0 / (rho_0 |K_0|) in the origin element).  Sets t = 0 and marks the
+ * step size for estimation by the next step. */
+LH_API lh_status lh_init_state(lh_ctx* ctx);
+/* Copies the state in (host or device pointers, N_V / N_E / N_V doubles).
+ * dt <= 0 asks the next step for a fresh estimate. */
+LH_API lh_status lh_set_state(lh_ctx* ctx, const double* v, const double* e,
+                       const double* x, double t, double dt);
+/* Copies the state out (host or device pointers; any may be NULL) and
+ * synchronizes.  Reports a pending device error. */
+LH_API lh_status lh_get_state(lh_ctx* ctx, double* v, double* e, double* x, double* t,
+                       double* dt);
+
+/* One force evaluation on the given state (eq:forceOneforceTv), all device
+ * pointers: F1 (N_V) = F.1 with the essential components set to zero;
+ * if vtest != NULL, FTv (N_E) = F^T.vtest; dt_est (host, may be NULL) = the
+ * minimum over quadrature points of eq:adaptive-timestep (0 if an element is
+ * inverted).  Synchronizes when dt_est != NULL. */
+LH_API lh_status lh_force(lh_ctx* ctx, const double* v, const double* e,
+                   const double* x, const double* vtest, double* F1,
+                   double* FTv, double* dt_est);
+
+/* Hyper-reduced evaluation (Section 3.3, eq:rom-hr): the same force restricted
+ * to the n listed elements (device int32 ids, each in [0, nelem)).  Outputs
+ * are element-local and ordered like the list: F1_local (n x dim x ndof_h1,
+ * row [slot][c][i]) and, if vtest != NULL, FTv_local (n x ndof_l2).  No
+ * boundary condition is applied to element-local rows.  dt_est as lh_force
+ * over the listed elements. */
+LH_API lh_status lh_force_sampled(lh_ctx* ctx, const int32_t* elem_ids, int64_t n,
+                           const double* v, const double* e, const double* x,
+                           const double* vtest, double* F1_local,
+                           double* FTv_local, double* dt_est);
+
+/* y = M_V x (device pointers, N_V): the kinematic mass matrix of eq:fom,
+ * partially assembled, no boundary condition. */
+LH_API lh_status lh_mass_apply_v(lh_ctx* ctx, const double* in, double* out);
+/* Solves M_V out = rhs on the non-essential components (essential entries of
+ * out are zero) by Jacobi-preconditioned CG from a zero guess (Section 2.2.1
+ * momentum equation).  iters / relres (host, may be NULL) return the
+ * iteration count and ||r||/||b||; both make the call synchronize.
+ * LH_ECG if cg_maxit is reached. */
+LH_API lh_status lh_mass_solve_v(lh_ctx* ctx, const double* rhs, double* out,
+                          int32_t* iters, double* relres);
+/* out = M_E^{-1} rhs (device pointers, N_E), block diagonal per element. */
+LH_API lh_status lh_mass_solve_e(lh_ctx* ctx, const double* rhs, double* out);
+/* Total energy 1/2 v.M_V.v + 1.M_E.e of the context state (host double). */
+LH_API lh_status lh_total_energy(lh_ctx* ctx, double* energy);
+
+/* One RK2-average step of size dt on the context state (eq:RK2-avg), without
+ * step control (replay of a known step sequence).  tau (host, may be NULL)
+ * = min of the estimate over both stages; synchronizes when given. */
+LH_API lh_status lh_step_fixed(lh_ctx* ctx, double dt, double* tau);
+/* One step attempt under the control of Section 2.2.3; *accepted = 1 if the
+ * state advanced, 0 if the attempt was rejected and dt reduced by beta1.
+ * t_final bounds the step (the last step is clamped to land on it). */
+LH_API lh_status lh_step(lh_ctx* ctx, double t_final, int32_t* accepted, double* t,
+                  double* dt);
+/* Runs the step control loop to t_final (or max_steps accepted steps) with
+ * device-side accept/redo decisions, one CUDA graph launch per attempt.
+ * stats (host, may be NULL).  dt_log (device, may be NULL) receives the
+ * accepted step sizes in order, at most dt_log_cap of them. */
+LH_API lh_status lh_run_to(lh_ctx* ctx, double t_final, int64_t max_steps,
+                    lh_run_stats* stats, double* dt_log, int64_t dt_log_cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LAGH_H */

@@ -1,0 +1,191 @@
+// Internal declarations of the GB300 Lagrangian hydro library (not part of
+// the C ABI).  Every kernel is templated on the space dimension DIM, the H1
+// order K and the 1D Gauss-Legendre count NQ (= 2K).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "lagh.h"
+
+namespace lagh {
+
+constexpr int kMaxOrder = 3;          // K
+constexpr int kMaxQ = 2 * kMaxOrder;  // NQ
+
+// device-side error bits (Ctl::status)
+enum : int {
+  kDevTangled = 1,
+  kDevNonFinite = 2,
+  kDevCG = 4,
+  kDevTimeout = 8,
+  kDevDtMin = 16,
+};
+
+constexpr __host__ __device__ int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// 1D tables on [0,1], passed by value (kernel parameter space).
+struct Basis1D {
+  double B[kMaxQ][kMaxOrder + 1];   // H1 Lagrange (Gauss-Lobatto nodes) at qp
+  double G[kMaxQ][kMaxOrder + 1];   // its derivative
+  double L[kMaxQ][kMaxOrder];       // L2 Lagrange (Gauss-Legendre nodes) at qp
+  double W[kMaxQ];                  // Gauss-Legendre weights
+  double M1[kMaxOrder + 1][kMaxOrder + 1];  // 1D H1 reference mass matrix
+  float Bf[kMaxQ][kMaxOrder + 1];
+  float Gf[kMaxQ][kMaxOrder + 1];
+  float Lf[kMaxQ][kMaxOrder];
+  float Wf[kMaxQ];
+  double MEinv[81];                 // reference M_E^{-1} (ndof_l2^2 <= 81)
+  double L2int[27];                 // integral of each reference L2 basis function
+};
+
+struct Geom {
+  int dim, k, nq;
+  int n[3];        // elements per direction (1 if unused)
+  int nn[3];       // H1 nodes per direction
+  int64_t nnodes, nelem, nv, ne;
+  double lo[3];    // box origin
+  double h[3];     // element widths
+  double J0inv[3]; // diagonal of the initial Jacobian inverse (Cartesian mesh)
+  double ell0;     // initial length scale |K_0|^{1/d} / k
+  double detJ0;    // |K_0|
+};
+
+struct Phys {
+  double gamma, cfl, cfl_mu, q1, q2;
+  int visc, source, problem;
+};
+
+// Device control block of the time loop (one per context).
+struct Ctl {
+  double t, dt, dt_use, t_final, dt_min;
+  unsigned long long tau_bits[2];   // per-stage min estimate, ordered bits
+  long long steps, rejects, attempts, cg_iters, max_steps;
+  long long dt_log_cap;
+  double* dt_log;
+  int last;       // dt_use was clamped to land on t_final
+  int done;       // loop finished (t_final, max_steps or error)
+  int accepted;   // last attempt accepted
+  int status;     // kDev* error bits
+  int cg_last_iters;
+  double cg_last_relres;
+  double tau_last;  // min estimate over both stages of the last attempt
+  int fixed;        // replay mode: accept every attempt
+};
+
+// Grid barrier state (cooperative persistent kernels).
+struct Barrier {
+  unsigned int count;
+  unsigned int gen;
+};
+
+// Work arrays of one context (all device pointers).
+struct Arrays {
+  double *v, *e, *x;            // current state
+  double *vh, *eh, *xh;         // half-step state S^{n+1/2}
+  double *vn, *en, *xn;         // candidate state S^{n+1} (committed if accepted)
+  double *vbar;                 // (v^n + v^{n+1}) / 2
+  double *F1E;                  // element-local F.1 [nelem][dim][nd1]
+  double *rhs, *acc;            // CG right-hand side and solution
+  double *r, *z, *p, *Ap;       // CG vectors
+  double *ApE;                  // element-local M p [nelem][dim][nd1]
+  double *D;                    // FP64 path: stress weights [nelem][dim*dim][nqe]
+  float *FK;                    // mixed path: element force matrices [nelem][dim*nd1][nd2]
+  double *srcE;                 // energy source [N_E]
+  double *rho0K;                // rho0 |J0| per element
+  double *dinv;                 // 1 / diag(M_s) per node
+  double *partials;             // reduction partials [4][max_blocks]
+  double *tmpE;                 // N_E scratch
+  double *tmpV;                 // N_V scratch
+  double *aux;                  // 16 doubles of API scratch (estimates, flags, energy)
+  Barrier* bar;
+  Ctl* ctl;
+};
+
+}  // namespace lagh
+
+struct lh_ctx {
+  lagh::Geom g;
+  lagh::Phys ph;
+  lagh::Basis1D basis;
+  lh_phys_desc phys_desc;
+  int precision;
+  cudaStream_t stream;
+  lagh::Arrays a;
+  lagh::Ctl* ctl_host;      // pinned mirror of the control block
+  int num_sms;
+  int cg_blocks;            // cooperative grid size of the CG kernel
+  int cg_threads;
+  double cg_rtol;
+  int cg_maxit;
+  cudaStream_t work;          // stream the step graph is captured and launched on
+  int own_work;               // work stream created by the context
+  cudaGraphExec_t step_graph;
+  int graph_ready;            // 1: graph built, -1: capture unsupported (eager launches)
+  cudaEvent_t ev0, ev1;
+  std::string err;
+};
+
+namespace lagh {
+
+// ---- host helpers (setup.cu) ----
+lh_status set_error(lh_ctx* c, lh_status s, const std::string& msg);
+lh_status cuda_check(lh_ctx* c, cudaError_t e, const char* what);
+void build_basis(int k, int nq, int dim, Basis1D* b);
+lh_status device_status(lh_ctx* c);  // reads ctl->status (synchronizes)
+
+// ---- kernel launchers (force.cu, mass.cu, step.cu) ----
+// Force on an explicit state.  list/nlist: element subset (NULL = all, slot =
+// element).  Outputs: F1E (element-local rows, slot major), D (if store_D),
+// FK (mixed, if store_FK), FTvE (if vtest), srcE (if source), tau slot.
+struct ForceArgs {
+  const double *v, *e, *x, *vtest;
+  const int32_t* list;
+  int64_t nslots;
+  double* F1E;
+  double* D;
+  float* FK;
+  double* FTvE;
+  double* srcE;
+  unsigned long long* tau_bits;
+  int* status;
+  const Ctl* ctl;     // if non-NULL and ctl->done, the kernel returns at once
+};
+cudaError_t launch_force(const lh_ctx* c, const ForceArgs& fa, cudaStream_t s);
+
+// Node gather of an element-local kinematic vector: out = scale * gather(E),
+// essential components set to zero when apply_bc.
+cudaError_t launch_gather(const lh_ctx* c, const double* E, double* out, double scale,
+                          int apply_bc, const Ctl* ctl, cudaStream_t s);
+
+// Energy update: e_out = e_base + coef * M_E^{-1} (F^T w + src), coef =
+// frac * ctl->dt_use (or frac * dt if ctl == NULL).
+struct EnergyArgs {
+  const double* w;       // kinematic test vector (N_V)
+  const double* D;       // FP64 path
+  const float* FK;       // mixed path
+  const double* srcE;    // may be NULL
+  const double* e_base;
+  double* e_out;
+  double frac;
+  double dt;
+  const Ctl* ctl;
+};
+cudaError_t launch_energy_update(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s);
+
+// Mass operations.
+cudaError_t launch_mass_apply(const lh_ctx* c, const double* in, double* out, cudaStream_t s);
+// Jacobi-PCG on M_V out = rhs (non-essential components); iteration count,
+// relative residual and failures are written to c->a.ctl.
+cudaError_t launch_cg(const lh_ctx* c, const double* rhs, double* out, const Ctl* gate,
+                      cudaStream_t s);
+cudaError_t launch_mass_solve_e(const lh_ctx* c, const double* rhs, double* out, cudaStream_t s);
+// Total energy 1/2 v.M_V.v + 1.M_E.e into *out (device double).
+cudaError_t launch_total_energy(const lh_ctx* c, const double* v, const double* e, double* out,
+                                cudaStream_t s);
+cudaError_t cg_occupancy(lh_ctx* c);
+cudaError_t prepare_kernels(const lh_ctx* c);
+
+}  // namespace lagh

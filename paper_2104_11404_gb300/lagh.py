@@ -1,0 +1,240 @@
+"""Thin Python binding of the C ABI in include/lagh.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library _lib/liblagh.so; this module only
+converts descriptors, passes device pointers of torch tensors (or host
+pointers where the ABI allows them) and turns status codes into exceptions.
+Importing it does not need a GPU; creating a context does.  There is no
+fallback: if the library is missing the calls raise.
+"""
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "_lib", "liblagh.so")
+
+LH_OK, LH_EINVAL, LH_ENOMEM, LH_ECUDA, LH_ETANGLED, LH_ENONFINITE, LH_EDTMIN, LH_ECG, \
+    LH_ETIMEOUT, LH_EUNSUPPORTED = range(10)
+LH_FP64, LH_MIXED = 0, 1
+LH_SEDOV, LH_TAYLOR_GREEN, LH_GRESHO, LH_UNIFORM = 1, 2, 3, 4
+
+# every entry point declared in include/lagh.h
+API_NAMES = [
+    "lh_default_phys", "lh_status_string", "lh_create", "lh_destroy", "lh_last_error",
+    "lh_layout", "lh_init_state", "lh_set_state", "lh_get_state", "lh_force",
+    "lh_force_sampled", "lh_mass_apply_v", "lh_mass_solve_v", "lh_mass_solve_e",
+    "lh_total_energy", "lh_step_fixed", "lh_step", "lh_run_to",
+]
+
+
+class lh_mesh_desc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class lh_disc_desc(ctypes.Structure):
+    _fields_ = [("order", ctypes.c_int32), ("nq", ctypes.c_int32)]
+
+
+class lh_phys_desc(ctypes.Structure):
+    _fields_ = [("problem", ctypes.c_int32), ("visc", ctypes.c_int32), ("source", ctypes.c_int32),
+                ("cg_maxit", ctypes.c_int32), ("gamma", ctypes.c_double),
+                ("blast_energy", ctypes.c_double), ("e_uniform", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("cfl_mu", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
+                ("gamma_dt", ctypes.c_double), ("q1", ctypes.c_double), ("q2", ctypes.c_double),
+                ("cg_rtol", ctypes.c_double), ("dt_min_frac", ctypes.c_double)]
+
+
+class lh_layout_info(ctypes.Structure):
+    _fields_ = [("nv", ctypes.c_int64), ("ne", ctypes.c_int64), ("nqp", ctypes.c_int64),
+                ("nelem", ctypes.c_int64), ("nnodes", ctypes.c_int64),
+                ("dim", ctypes.c_int32), ("order", ctypes.c_int32), ("nq", ctypes.c_int32),
+                ("ndof_h1", ctypes.c_int32), ("ndof_l2", ctypes.c_int32), ("nqe", ctypes.c_int32),
+                ("nodes_per_dim", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
+                ("n_essential", ctypes.c_int64)]
+
+
+class lh_run_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("rejects", ctypes.c_int64),
+                ("cg_iters", ctypes.c_int64), ("t", ctypes.c_double), ("dt", ctypes.c_double),
+                ("energy0", ctypes.c_double), ("energy", ctypes.c_double),
+                ("wall_ms", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.c_void_p  # device or host double*, passed as an address
+_lib = None
+
+
+def load():
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liblagh.so is not built: run paper_2104_11404_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    S = ctypes.c_int
+    L.lh_default_phys.argtypes = [ctypes.POINTER(lh_phys_desc)]
+    L.lh_default_phys.restype = None
+    L.lh_status_string.argtypes = [S]
+    L.lh_status_string.restype = ctypes.c_char_p
+    L.lh_create.argtypes = [ctypes.POINTER(lh_mesh_desc), ctypes.POINTER(lh_disc_desc),
+                            ctypes.POINTER(lh_phys_desc), ctypes.c_int32, _vp,
+                            ctypes.POINTER(_vp)]
+    L.lh_destroy.argtypes = [_vp]
+    L.lh_last_error.argtypes = [_vp]
+    L.lh_last_error.restype = ctypes.c_char_p
+    L.lh_layout.argtypes = [_vp, ctypes.POINTER(lh_layout_info)]
+    L.lh_init_state.argtypes = [_vp]
+    L.lh_set_state.argtypes = [_vp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double]
+    L.lh_get_state.argtypes = [_vp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_double),
+                               ctypes.POINTER(ctypes.c_double)]
+    L.lh_force.argtypes = [_vp, _dp, _dp, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_double)]
+    L.lh_force_sampled.argtypes = [_vp, _vp, ctypes.c_int64, _dp, _dp, _dp, _dp, _dp, _dp,
+                                   ctypes.POINTER(ctypes.c_double)]
+    L.lh_mass_apply_v.argtypes = [_vp, _dp, _dp]
+    L.lh_mass_solve_v.argtypes = [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_double)]
+    L.lh_mass_solve_e.argtypes = [_vp, _dp, _dp]
+    L.lh_total_energy.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
+    L.lh_step_fixed.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    L.lh_step.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.lh_run_to.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(lh_run_stats),
+                            _dp, ctypes.c_int64]
+    for name in API_NAMES:
+        if name not in ("lh_default_phys", "lh_status_string", "lh_last_error"):
+            getattr(L, name).restype = S
+    _lib = L
+    return L
+
+
+class LaghError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (status_string(status), status, msg))
+        self.status = status
+
+
+def status_string(s):
+    return load().lh_status_string(s).decode()
+
+
+def _ptr(t):
+    """Address of a tensor / array buffer (None -> NULL)."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if hasattr(t, "ctypes"):
+        return t.ctypes.data
+    return int(t)
+
+
+# ---- functions with the names of the C ABI --------------------------------
+
+def lh_default_phys():
+    p = lh_phys_desc()
+    load().lh_default_phys(ctypes.byref(p))
+    return p
+
+
+def lh_create(mesh, disc, phys, precision, stream=None):
+    h = _vp()
+    st = load().lh_create(ctypes.byref(mesh), ctypes.byref(disc), ctypes.byref(phys),
+                          int(precision), stream, ctypes.byref(h))
+    if st != LH_OK:
+        raise LaghError(st, "lh_create failed")
+    return h
+
+
+def _check(ctx, st):
+    if st != LH_OK:
+        raise LaghError(st, load().lh_last_error(ctx).decode())
+
+
+def lh_destroy(ctx):
+    load().lh_destroy(ctx)
+
+
+def lh_layout(ctx):
+    info = lh_layout_info()
+    _check(ctx, load().lh_layout(ctx, ctypes.byref(info)))
+    return info
+
+
+def lh_init_state(ctx):
+    _check(ctx, load().lh_init_state(ctx))
+
+
+def lh_set_state(ctx, v, e, x, t=0.0, dt=0.0):
+    _check(ctx, load().lh_set_state(ctx, _ptr(v), _ptr(e), _ptr(x), float(t), float(dt)))
+
+
+def lh_get_state(ctx, v=None, e=None, x=None):
+    t = ctypes.c_double()
+    dt = ctypes.c_double()
+    _check(ctx, load().lh_get_state(ctx, _ptr(v), _ptr(e), _ptr(x), ctypes.byref(t),
+                                    ctypes.byref(dt)))
+    return t.value, dt.value
+
+
+def lh_force(ctx, v, e, x, F1, vtest=None, FTv=None, want_dt=True):
+    dt = ctypes.c_double()
+    _check(ctx, load().lh_force(ctx, _ptr(v), _ptr(e), _ptr(x), _ptr(vtest), _ptr(F1), _ptr(FTv),
+                                ctypes.byref(dt) if want_dt else None))
+    return dt.value if want_dt else None
+
+
+def lh_force_sampled(ctx, elem_ids, n, v, e, x, F1_local, vtest=None, FTv_local=None,
+                     want_dt=True):
+    dt = ctypes.c_double()
+    _check(ctx, load().lh_force_sampled(ctx, _ptr(elem_ids), int(n), _ptr(v), _ptr(e), _ptr(x),
+                                        _ptr(vtest), _ptr(F1_local), _ptr(FTv_local),
+                                        ctypes.byref(dt) if want_dt else None))
+    return dt.value if want_dt else None
+
+
+def lh_mass_apply_v(ctx, a, out):
+    _check(ctx, load().lh_mass_apply_v(ctx, _ptr(a), _ptr(out)))
+
+
+def lh_mass_solve_v(ctx, rhs, out):
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    _check(ctx, load().lh_mass_solve_v(ctx, _ptr(rhs), _ptr(out), ctypes.byref(it),
+                                       ctypes.byref(rr)))
+    return it.value, rr.value
+
+
+def lh_mass_solve_e(ctx, rhs, out):
+    _check(ctx, load().lh_mass_solve_e(ctx, _ptr(rhs), _ptr(out)))
+
+
+def lh_total_energy(ctx):
+    E = ctypes.c_double()
+    _check(ctx, load().lh_total_energy(ctx, ctypes.byref(E)))
+    return E.value
+
+
+def lh_step_fixed(ctx, dt):
+    tau = ctypes.c_double()
+    _check(ctx, load().lh_step_fixed(ctx, float(dt), ctypes.byref(tau)))
+    return tau.value
+
+
+def lh_step(ctx, t_final):
+    acc = ctypes.c_int32()
+    t = ctypes.c_double()
+    dt = ctypes.c_double()
+    _check(ctx, load().lh_step(ctx, float(t_final), ctypes.byref(acc), ctypes.byref(t),
+                               ctypes.byref(dt)))
+    return bool(acc.value), t.value, dt.value
+
+
+def lh_run_to(ctx, t_final, max_steps=2 ** 62, dt_log=None, dt_log_cap=0):
+    stats = lh_run_stats()
+    st = load().lh_run_to(ctx, float(t_final), int(max_steps), ctypes.byref(stats), _ptr(dt_log),
+                          int(dt_log_cap))
+    _check(ctx, st)
+    return {k: getattr(stats, k) for k, _ in lh_run_stats._fields_}

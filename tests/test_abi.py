@@ -1,0 +1,70 @@
+"""CPU-side checks of the boundary: the CUDA library builds for sm_103a, loads
+without a GPU and exports every entry point that include/lagh.h declares; the
+Python binding names them all; the seeded input generators are reproducible."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "lagh.h")).read()
+    return sorted(set(re.findall(r"^LH_API [^(]*?\b(lh_\w+)\(", txt, flags=re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("lh_create", "lh_force", "lh_force_sampled", "lh_mass_solve_v",
+                 "lh_mass_solve_e", "lh_step", "lh_step_fixed", "lh_run_to", "lh_layout",
+                 "lh_init_state"):
+        assert must in names
+
+
+def test_library_builds_loads_and_exports_every_symbol():
+    from paper_2104_11404_gb300 import build, lagh
+    path = build.build()
+    assert os.path.exists(path)
+    L = lagh.load()
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert sorted(lagh.API_NAMES) == _declared()
+    # host-only calls work without a GPU
+    p = lagh.lh_default_phys()
+    assert p.cfl == 0.5 and p.cfl_mu == 2.5 and p.beta1 == 0.85 and p.beta2 == 1.02
+    assert p.gamma_dt == 0.8
+    assert lagh.status_string(lagh.LH_ECG) == "CG did not converge"
+
+
+def test_splitmix64_reference_value():
+    from paper_2104_11404_gb300.workloads import SplitMix64
+    # published first output of splitmix64 seeded with 0
+    assert SplitMix64(0).next_u64() == 0xE220A8397B1DCDAF
+
+
+def test_batch_instances_and_samples_reproducible():
+    from paper_2104_11404_gb300 import workloads as W
+    a = W.batch_instances(512)
+    b = W.batch_instances(512)
+    assert a == b and len(a) == 512
+    ns = [c["n"][0] for c in a]
+    assert set(ns) == set(W.BATCH_SIZES)
+    assert all(0.1 <= c["blast_energy"] < 1.0 and 1.3 <= c["gamma"] < 1.67 for c in a)
+    s = W.element_sample(2304, stream=7)
+    assert len(s) == 116 and np.all(np.diff(s) > 0) and s[0] >= 0 and s[-1] < 2304
+    assert np.array_equal(s, W.element_sample(2304, stream=7))
+    assert not np.array_equal(s, W.element_sample(2304, stream=8))
+
+
+def test_layout_sizes_match_oracle():
+    import oracle as O
+    from paper_2104_11404_gb300 import workloads as W
+    for name, cfg in W.CONFIGS.items():
+        nv, ne, nel = W.sizes(cfg)
+        if nel > 5000:
+            continue
+        o = O.Oracle(dim=cfg["dim"], nx=cfg["n"][0], ny=cfg["n"][1], nz=cfg["n"][2],
+                     order=cfg["order"], problem=O.UNIFORM)
+        assert (o.nv, o.ne, o.nelem) == (nv, ne, nel)

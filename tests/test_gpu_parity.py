@@ -1,0 +1,243 @@
+"""Parity of the CUDA library (through the C ABI) with the CPU oracle.
+
+FP64 path: <= 1e-12 relative per evaluation and per step, <= 1e-8 relative
+L2 at final time when the GPU replays the oracle's accepted step sizes.
+Mixed path: FP32 stress, so <= 1e-5 relative per force evaluation and
+<= 1e-4 relative L2 in velocity and energy at final time, with the total
+energy conserved to 1e-10 relative (the FP64 contractions of the FP32
+element matrices keep the RK2-average energy balance exact).
+"""
+import numpy as np
+import pytest
+
+from paper_2104_11404_gb300 import workloads as W
+from tests._pair import dev, gpu_for, host, max_rel, oracle_for, random_state, rel_l2
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+# (dim, order, elements) spanning several CTAs and a ragged last CTA
+SMALL = [(2, 1, (9, 7, 1)), (2, 2, (5, 7, 1)), (2, 3, (3, 5, 1)), (3, 1, (3, 4, 2)),
+         (3, 2, (3, 2, 3))]
+
+
+def _cfg(dim, k, n, problem=W.SEDOV, visc=1):
+    return dict(dim=dim, n=n, order=k, problem=problem, gamma=1.4, lo=(0.0, 0.0, 0.0),
+                hi=(1.0, 1.0, 1.0), visc=visc, blast_energy=0.25, t_final=0.1)
+
+
+@pytest.mark.parametrize("dim,k,n", SMALL)
+@pytest.mark.parametrize("visc", [0, 1])
+def test_force_fp64(dim, k, n, visc):
+    cfg = _cfg(dim, k, n, visc=visc)
+    o = oracle_for(cfg)
+    g = gpu_for(cfg)
+    v, e, x = random_state(o, cfg, seed=100 + dim * 10 + k)
+    w = random_state(o, cfg, seed=7)[0]
+    F1o, FTvo, dto, st = o.force(v, e, x, vtest=w)
+    assert st == 0
+    F1, FTv, dt = g.force(dev(v), dev(e), dev(x), vtest=dev(w))
+    assert max_rel(F1o, host(F1)) <= 1e-12
+    assert max_rel(FTvo, host(FTv)) <= 1e-12
+    assert abs(dt - dto) <= 1e-12 * dto
+
+
+@pytest.mark.parametrize("dim,k,n", SMALL)
+def test_force_mixed(dim, k, n):
+    cfg = _cfg(dim, k, n)
+    o = oracle_for(cfg)
+    g = gpu_for(cfg, precision="mixed")
+    v, e, x = random_state(o, cfg, seed=200 + dim * 10 + k)
+    w = random_state(o, cfg, seed=8)[0]
+    F1o, FTvo, dto, _ = o.force(v, e, x, vtest=w)
+    F1, FTv, dt = g.force(dev(v), dev(e), dev(x), vtest=dev(w))
+    assert max_rel(F1o, host(F1)) <= 1e-5
+    assert max_rel(FTvo, host(FTv)) <= 1e-5
+    assert abs(dt - dto) <= 1e-5 * dto
+    # the energy identity holds to FP64 rounding of the FP32 element matrices
+    F1h, FTvh = host(F1), host(FTv)
+    assert abs(w @ F1h - FTvh.sum()) <= 1e-13 * np.abs(w).max() * np.abs(F1h).sum()
+
+
+@pytest.mark.parametrize("dim,k,n", SMALL)
+def test_mass_operators(dim, k, n):
+    cfg = _cfg(dim, k, n)
+    o = oracle_for(cfg)
+    g = gpu_for(cfg)
+    rng = np.random.default_rng(dim * 100 + k)
+    a = rng.normal(size=o.nv)
+    assert max_rel(o.mass_apply_v(a), host(g.mass_apply_v(dev(a)))) <= 1e-14
+    xo, _, _, st = o.mass_solve_v(a)
+    xg, its, rr = g.mass_solve_v(dev(a))
+    assert st == 0 and rr <= 1e-14 and its > 0
+    assert rel_l2(xo, host(xg)) <= 1e-12
+    assert np.all(host(xg)[W.essential_mask(cfg)] == 0.0)
+    b = rng.normal(size=o.ne)
+    assert max_rel(o.mass_solve_e(b), host(g.mass_solve_e(dev(b)))) <= 1e-13
+
+
+def _replay(cfg, nsteps, precision="fp64", tol=1e-12):
+    """Oracle runs free; the GPU replays the oracle's accepted steps."""
+    o = oracle_for(cfg)
+    v, e, x = o.init_state()
+    g = gpu_for(cfg, precision=precision)
+    g.init_state()
+    vg, eg, xg, t, _ = g.get_state()
+    assert max_rel(v, host(vg)) <= 1e-15 and max_rel(e, host(eg)) <= 1e-15
+    assert max_rel(x, host(xg)) <= 1e-15
+    worst = 0.0
+    for _ in range(nsteps):
+        stats, log, st = o.run(1e9, v, e, x, dt=0.0 if _ == 0 else dt_next, max_steps=1)
+        assert st == 0
+        dt_next = stats["dt"]
+        tau = g.step_fixed(log[0])
+        vg, eg, xg, _, _ = g.get_state()
+        for a, b in ((v, vg), (e, eg), (x, xg)):
+            worst = max(worst, rel_l2(a, host(b)))
+    assert worst <= tol, worst
+    return o, g
+
+
+@pytest.mark.parametrize("name,n,steps", [("sedov2d_8", (8, 8), 12), ("tg2d_64", (16, 16), 8),
+                                           ("gresho2d_256", (8, 8), 6),
+                                           ("sedov3d_32", (4, 4, 4), 6)])
+def test_steps_fp64_per_step(name, n, steps):
+    cfg = W.scaled(name, n=n)
+    _replay(cfg, steps)
+
+
+def test_sedov_full_run_replay_fp64():
+    """2D blast to t = 0.8: the GPU replays the oracle's accepted step sizes;
+    final fields within 1e-8 (eq:relerrors) and energy conserved."""
+    cfg = W.CONFIGS["sedov2d_8"]
+    o = oracle_for(cfg)
+    v, e, x = o.init_state()
+    stats, log, st = o.run(cfg["t_final"], v, e, x)
+    assert st == 0
+    g = gpu_for(cfg)
+    g.init_state()
+    E0 = g.total_energy()
+    for dt in log:
+        g.step_fixed(float(dt))
+    vg, eg, xg, t, _ = g.get_state()
+    assert abs(t - cfg["t_final"]) < 1e-12
+    assert rel_l2(v, host(vg)) <= 1e-8
+    assert rel_l2(e, host(eg)) <= 1e-8
+    assert rel_l2(x, host(xg)) <= 1e-8
+    assert abs(g.total_energy() - E0) <= 1e-12 * E0
+
+
+def test_sedov_free_running_control_fp64():
+    """Device-side step control against the oracle's control loop."""
+    cfg = W.CONFIGS["sedov2d_8"]
+    o = oracle_for(cfg)
+    v, e, x = o.init_state()
+    stats, log, st = o.run(cfg["t_final"], v, e, x)
+    g = gpu_for(cfg)
+    g.init_state()
+    dt_log = torch.zeros(10000, dtype=torch.float64, device="cuda")
+    gs = g.run_to(cfg["t_final"], dt_log=dt_log)
+    assert gs["t"] == cfg["t_final"]
+    assert gs["steps"] == stats["steps"] and gs["rejects"] == stats["rejects"]
+    assert np.allclose(host(dt_log)[: gs["steps"]], log, rtol=1e-10, atol=0)
+    vg, eg, xg, _, _ = g.get_state()
+    assert rel_l2(v, host(vg)) <= 1e-8 and rel_l2(e, host(eg)) <= 1e-8
+    assert abs(gs["energy"] - gs["energy0"]) <= 1e-12 * gs["energy0"]
+
+
+def test_taylor_green_mixed_accuracy_and_energy():
+    cfg = W.scaled("tg2d_64", n=(16, 16), t_final=0.1)
+    o = oracle_for(cfg)
+    v, e, x = o.init_state()
+    stats, log, st = o.run(cfg["t_final"], v, e, x)
+    g = gpu_for(cfg, precision="mixed")
+    g.init_state()
+    for dt in log:
+        g.step_fixed(float(dt))
+    vg, eg, xg, _, _ = g.get_state()
+    assert rel_l2(v, host(vg)) <= 1e-4
+    assert rel_l2(e, host(eg)) <= 1e-4
+    assert rel_l2(x, host(xg)) <= 1e-6
+
+
+def test_sedov_mixed_energy_drift():
+    cfg = W.CONFIGS["sedov2d_8"]
+    o = oracle_for(cfg)
+    v, e, x = o.init_state()
+    stats, log, st = o.run(0.3, v, e, x)
+    g = gpu_for(cfg, precision="mixed")
+    g.init_state()
+    E0 = g.total_energy()
+    for dt in log:
+        g.step_fixed(float(dt))
+    assert abs(g.total_energy() - E0) <= 1e-10 * E0
+    vg, eg, xg, _, _ = g.get_state()
+    assert rel_l2(v, host(vg)) <= 1e-4 and rel_l2(e, host(eg)) <= 1e-4
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+@pytest.mark.parametrize("dim,k,n", [(2, 2, (6, 5, 1)), (3, 2, (3, 3, 2)), (2, 3, (4, 3, 1))])
+def test_force_sampled(dim, k, n, precision, tol):
+    cfg = _cfg(dim, k, n)
+    o = oracle_for(cfg)
+    g = gpu_for(cfg, precision=precision)
+    v, e, x = random_state(o, cfg, seed=31)
+    w = random_state(o, cfg, seed=32)[0]
+    ids = W.element_sample(o.nelem, frac=0.3, stream=dim * 10 + k)
+    F1l, FTvl, dt = g.force_sampled(dev(ids), dev(v), dev(e), dev(x), vtest=dev(w))
+    F1l = host(F1l).reshape(len(ids), dim * o.nd1)
+    FTvl = host(FTvl).reshape(len(ids), o.nd2)
+    from tests import _fem_ref as R
+    mesh = R.CartesianMesh(dim, n[:dim], k)
+    taus = []
+    for s, el in enumerate(ids):
+        FK = o.element_force_matrix(int(el), v, e, x)
+        cn = mesh.conn(int(el))
+        wl = np.concatenate([w[c * o.nnodes + cn] for c in range(dim)])
+        assert max_rel(FK.sum(axis=1), F1l[s]) <= tol
+        assert max_rel(FK.T @ wl, FTvl[s]) <= tol
+    # empty list: nothing to do
+    F1e, _, _ = g.force_sampled(dev(np.zeros(0, dtype=np.int32)), dev(v), dev(e), dev(x))
+    assert F1e.numel() == 0
+
+
+def test_device_errors_are_reported():
+    from paper_2104_11404_gb300 import lagh
+    cfg = _cfg(2, 2, (4, 4, 1))
+    o = oracle_for(cfg)
+    g = gpu_for(cfg)
+    v, e, x = o.init_state()
+    # inverted element: swap two corner nodes of element 0
+    xt = x.copy()
+    nn = 9
+    xt[0], xt[2] = xt[2], xt[0]
+    with pytest.raises(lagh.LaghError) as ei:
+        g.force(dev(v), dev(e), dev(xt))
+    assert ei.value.status == lagh.LH_ETANGLED
+    en = e.copy()
+    en[5] = np.nan
+    with pytest.raises(lagh.LaghError) as ei:
+        g.force(dev(v), dev(en), dev(x))
+    assert ei.value.status == lagh.LH_ENONFINITE
+    g1 = gpu_for(cfg, cg_maxit=1)
+    with pytest.raises(lagh.LaghError) as ei:
+        g1.mass_solve_v(dev(np.random.default_rng(0).normal(size=o.nv)))
+    assert ei.value.status == lagh.LH_ECG
+    g2 = gpu_for(cfg, phys_overrides={"dt_min_frac": 0.05})
+    g2.init_state()
+    g2.set_state(dev(v), dev(e), dev(x), t=0.0, dt=0.5)
+    with pytest.raises(lagh.LaghError) as ei:
+        g2.run_to(1.0)
+    assert ei.value.status == lagh.LH_EDTMIN
+
+
+def test_invalid_descriptors():
+    from paper_2104_11404_gb300 import lagh
+    cfg = _cfg(3, 3, (2, 2, 2))
+    with pytest.raises(lagh.LaghError) as ei:
+        gpu_for(cfg)
+    assert ei.value.status == lagh.LH_EUNSUPPORTED
+    cfg = _cfg(2, 2, (0, 2, 1))
+    with pytest.raises(lagh.LaghError) as ei:
+        gpu_for(cfg)
+    assert ei.value.status == lagh.LH_EINVAL
