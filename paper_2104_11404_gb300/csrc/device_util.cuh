@@ -119,20 +119,23 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 }
 
 // Block minimum of the ordered bits, then one atomicMin per block (min is
-// exact and order-independent, so the result is deterministic).
+// exact and order-independent, so the result is deterministic).  Works for
+// any block size (a shared-memory tree, no partial-warp shuffles).
+// sh: >= 256 entries; blockDim.x <= 256.
 __device__ __forceinline__ void block_min_to(unsigned long long v, unsigned long long* sh,
                                              unsigned long long* dst) {
-  v = warp_min_u64(v);
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tid = threadIdx.x, n = blockDim.x;
   __syncthreads();
-  if (lane == 0) sh[w] = v;
+  sh[tid] = v;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long m = sh[0];
-    int nw = (blockDim.x + 31) >> 5;
-    for (int i = 1; i < nw; ++i) m = sh[i] < m ? sh[i] : m;
-    atomicMin(dst, m);
+  for (int s = 128; s > 0; s >>= 1) {
+    if (tid < s && tid + s < n) {
+      unsigned long long w = sh[tid + s];
+      if (w < sh[tid]) sh[tid] = w;
+    }
+    __syncthreads();
   }
+  if (tid == 0) atomicMin(dst, sh[0]);
 }
 
 // ------------------------------------------------------------- barrier ----

@@ -56,7 +56,7 @@ struct FL {
   static constexpr size_t B_ELEM = B_XS + B_VS + B_WS + B_ES + B_DQ + B_GQ + B_FK + B_SCR + B_L2;
   static constexpr size_t B_TAB = al(NQ * P * sizeof(T)) * 2 + al(NQ * K * sizeof(T)) +
                                   al(NQ * K * sizeof(double)) + al(NQ * sizeof(double));
-  static constexpr size_t BYTES = B_TAB + EPB * B_ELEM + 64 * sizeof(unsigned long long);
+  static constexpr size_t BYTES = B_TAB + EPB * B_ELEM + 256 * sizeof(unsigned long long);
 };
 
 struct ForceKParams {
@@ -272,9 +272,17 @@ force_kernel(const ForceKParams prm) {
       }
     }
     const T rho0K = (T)prm.rho0K[el];
-    flags = qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, (T)g.ell0,
-                                   (T)(1.0 / K), sigma, tau);
-    tau_q = (double)tau;
+    if (A.mode == kForceFull) {
+      const T pref = (MIXED && A.p_ref != nullptr) ? (T)(*A.p_ref) : T(0);
+      flags = qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, (T)g.ell0,
+                                     (T)(1.0 / K), pref, sigma, tau);
+      tau_q = (double)tau;
+    } else {
+      // reference pressure only: sigma = -p_ref I
+      const T pref = (T)(*A.p_ref);
+      for (int c = 0; c < DIM; ++c)
+        for (int n = 0; n < DIM; ++n) sigma[c][n] = (c == n) ? -pref : T(0);
+    }
     double alpha = Wd[qx] * Wd[qy] * (DIM == 3 ? Wd[qz] : 1.0);
     T Aj[DIM][DIM];
     adj_of<T, DIM>(J, Aj);
@@ -300,15 +308,17 @@ force_kernel(const ForceKParams prm) {
     }
   }
   // time-step estimate and error flags of the block
-  {
+  if (A.tau_bits != nullptr) {
     unsigned long long* rsh = red;
     block_min_to(tau_to_bits(tau_q), rsh, A.tau_bits);
-    if (flags) atomicOr(A.status, flags);
   }
+  if (flags && A.status != nullptr) atomicOr(A.status, flags);
   __syncthreads();
 
   // ---- transposed contractions ----
   if constexpr (!MIXED) {
+    if (A.F1E == nullptr) goto l2_part;
+    {
     // F.1 rows: F1[c][i] = sum_q sum_m D[c][m](q) d_m w_i(q)
     if constexpr (DIM == 2) {
       T* Y = scr;
@@ -329,7 +339,8 @@ force_kernel(const ForceKParams prm) {
             const T* X = (m == 0) ? Gs : Bs;
             for (int x_ = 0; x_ < NQ; ++x_) s += X[x_ * P + a] * Y[(((c * DIM + m) * P + b) * NQ) + x_];
           }
-          A.F1E[(slot * DIM + c) * ND1 + i] = (double)s;
+          double* o = &A.F1E[(slot * DIM + c) * ND1 + i];
+          *o = A.accumulate ? *o + (double)s : (double)s;
         }
     } else {
       T* Y = scr;
@@ -365,8 +376,10 @@ force_kernel(const ForceKParams prm) {
             for (int x_ = 0; x_ < NQ; ++x_)
               s += X[x_ * P + a] * Z[((((c * DIM + m) * P + cz) * P + b) * NQ) + x_];
           }
-          A.F1E[(slot * DIM + c) * ND1 + i] = (double)s;
+          double* o = &A.F1E[(slot * DIM + c) * ND1 + i];
+          *o = A.accumulate ? *o + (double)s : (double)s;
         }
+    }
     }
   } else {
     // Mixed: F_K[(c,i), j] = sum_q phi_j(q) sum_m D[c][m](q) d_m w_i(q) in FP32
@@ -458,6 +471,7 @@ force_kernel(const ForceKParams prm) {
   }
 
   // ---- L2 contractions (FP64): F^T w (FP64 path) and the energy source ----
+l2_part:
   const bool do_ftv = (!MIXED) && with_w;
   const bool do_src = (A.srcE != nullptr) && DIM == 2;
   if (do_ftv || do_src) {
@@ -479,7 +493,7 @@ force_kernel(const ForceKParams prm) {
           if ((fld == 0 && !do_ftv) || (fld == 1 && !do_src)) continue;
           double s = 0.0;
           for (int y_ = 0; y_ < NQ; ++y_) s += Ld[y_ * K + jy] * R1[(fld * K + jx) * NQ + y_];
-          if (fld == 0) A.FTvE[slot * ND2 + j] = s;
+          if (fld == 0) A.FTvE[slot * ND2 + j] = A.accumulate ? A.FTvE[slot * ND2 + j] + s : s;
           else A.srcE[el * ND2 + j] = s;
         }
     } else {
@@ -510,7 +524,7 @@ force_kernel(const ForceKParams prm) {
           double s = 0.0;
           for (int z_ = 0; z_ < NQ; ++z_)
             s += Ld[z_ * K + jz] * R2[((fld * K + jy) * K + jx) * NQ + z_];
-          if (fld == 0) A.FTvE[slot * ND2 + j] = s;
+          if (fld == 0) A.FTvE[slot * ND2 + j] = A.accumulate ? A.FTvE[slot * ND2 + j] + s : s;
           else A.srcE[el * ND2 + j] = s;
         }
     }
@@ -749,7 +763,8 @@ energy_update_kernel(const EnergyKParams prm) {
       // M_E,K^{-1} = Mref^{-1} / (rho0 |J0|)_K, applied to F^T w + src
       double s = 0.0;
       for (int l = 0; l < ND2; ++l) {
-        double rhs = ftv[l] + (A.srcE ? A.srcE[el * ND2 + l] : 0.0);
+        double rhs = ftv[l] + (A.srcE ? A.srcE[el * ND2 + l] : 0.0) +
+                     (A.prefE ? A.prefE[el * ND2 + l] : 0.0);
         s += Mi[j * ND2 + l] * rhs;
       }
       A.e_out[el * ND2 + j] = A.e_base[el * ND2 + j] + coef * s / prm.rho0K[el];
@@ -792,6 +807,15 @@ static cudaError_t launch_force_dk(const lh_ctx* c, const ForceArgs& fa, cudaStr
 
 cudaError_t launch_force(const lh_ctx* c, const ForceArgs& fa, cudaStream_t s) {
   LAGH_DISPATCH(c->g.dim, c->g.k, launch_force_dk, c, fa, s);
+}
+
+template <int DIM, int K>
+static cudaError_t launch_force64_dk(const lh_ctx* c, const ForceArgs& fa, cudaStream_t s) {
+  return launch_force_t<DIM, K, false>(c, fa, s);
+}
+
+cudaError_t launch_force_fp64(const lh_ctx* c, const ForceArgs& fa, cudaStream_t s) {
+  LAGH_DISPATCH(c->g.dim, c->g.k, launch_force64_dk, c, fa, s);
 }
 
 template <int DIM, int K>
@@ -847,8 +871,9 @@ static cudaError_t prepare_t() {
 
 template <int DIM, int K>
 static cudaError_t prepare_dk(const lh_ctx* c) {
-  if (c->precision == LH_MIXED) return prepare_t<DIM, K, true>();
-  return prepare_t<DIM, K, false>();
+  cudaError_t e = prepare_t<DIM, K, false>();  // FP64 kernels serve the mixed path too
+  if (e != cudaSuccess || c->precision != LH_MIXED) return e;
+  return prepare_t<DIM, K, true>();
 }
 
 cudaError_t prepare_kernels(const lh_ctx* c) { LAGH_DISPATCH(c->g.dim, c->g.k, prepare_dk, c); }

@@ -72,6 +72,7 @@ struct Ctl {
   int cg_last_iters;
   double cg_last_relres;
   double tau_last;  // min estimate over both stages of the last attempt
+  double p_ref;     // mixed path: constant reference pressure split off the FP32 stress
   int fixed;        // replay mode: accept every attempt
 };
 
@@ -149,10 +150,16 @@ struct ForceArgs {
   float* FK;
   double* FTvE;
   double* srcE;
-  unsigned long long* tau_bits;
+  unsigned long long* tau_bits;  // may be NULL (no estimate)
   int* status;
   const Ctl* ctl;     // if non-NULL and ctl->done, the kernel returns at once
+  const double* p_ref;  // device scalar: mixed stress is sigma + p_ref I
+  int mode;           // 0: full physics; 1: only the reference pressure -p_ref I (FP64)
+  int accumulate;     // add to F1E / FTvE instead of overwriting
 };
+enum { kForceFull = 0, kForceRefPressure = 1 };
+// Same force in FP64 whatever the context precision (reference-pressure mode).
+cudaError_t launch_force_fp64(const lh_ctx* c, const ForceArgs& fa, cudaStream_t s);
 cudaError_t launch_force(const lh_ctx* c, const ForceArgs& fa, cudaStream_t s);
 
 // Node gather of an element-local kinematic vector: out = scale * gather(E),
@@ -167,6 +174,7 @@ struct EnergyArgs {
   const double* D;       // FP64 path
   const float* FK;       // mixed path
   const double* srcE;    // may be NULL
+  const double* prefE;   // mixed path: F^T w of the reference pressure (may be NULL)
   const double* e_base;
   double* e_out;
   double frac;

@@ -150,12 +150,14 @@ __device__ __forceinline__ T sigma_min_of(const T (&J)[DIM][DIM], T detJ) {
 }
 
 // Stress and time-step estimate at one point.  J, Gv: reference gradients
-// (row = component, column = reference direction).  Returns the flags
+// (row = component, column = reference direction).  p_ref: a constant
+// reference pressure taken out of the returned stress (sigma + p_ref I is
+// returned; the caller accounts for -p_ref I separately).  Returns the flags
 // kDevTangled / kDevNonFinite (then sigma = 0 and tau = 0).
 template <typename T, int DIM>
 __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&Gv)[DIM][DIM],
                                               T e_q, T rho0K, const Phys& ph,
-                                              const T (&J0inv)[DIM], T ell0, T kinv,
+                                              const T (&J0inv)[DIM], T ell0, T kinv, T p_ref,
                                               T (&sigma)[DIM][DIM], T& tau) {
   const T gam = (T)ph.gamma;
   T detJ = det_of<T, DIM>(J);
@@ -167,7 +169,7 @@ __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&
   T p = (gam - T(1)) * rho * e_q;
   T cs2 = gam * (gam - T(1)) * e_q;
   T cs = t_sqrt(cs2 > T(0) ? cs2 : T(0));
-  for (int c = 0; c < DIM; ++c) sigma[c][c] = -p;
+  for (int c = 0; c < DIM; ++c) sigma[c][c] = p_ref - p;
   T hmin = sigma_min_of<T, DIM>(J, detJ) * kinv;
   T mu = T(0);
   if (ph.visc) {

@@ -458,6 +458,33 @@ static double gresho_pressure(double r) {
   return 3.0 + 4.0 * log(2.0);
 }
 
+// Mixed path: reference pressure (gamma - 1) rho0 min(e), rho0 = 1, clamped at
+// zero.  Any constant is exact (the split is algebraic); a value near the
+// smallest pressure keeps the FP32 stress small relative to its gradients.
+__global__ void pref_kernel(const double* e, int64_t ne, double gm1, Ctl* ctl) {
+  __shared__ double sh[256];
+  double m = 1e300;
+  for (int64_t i = threadIdx.x; i < ne; i += blockDim.x) m = e[i] < m ? e[i] : m;
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s && sh[threadIdx.x + s] < sh[threadIdx.x]) sh[threadIdx.x] = sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double p = gm1 * sh[0];
+    ctl->p_ref = (p > 0.0 && p < 1e300) ? p : 0.0;
+  }
+}
+
+static lh_status set_pref(lh_ctx* c) {
+  if (c->precision != LH_MIXED) return LH_OK;
+  pref_kernel<<<1, 256, 0, c->stream>>>(c->a.e, c->g.ne, c->phys_desc.gamma - 1.0, c->a.ctl);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+  return cuda_check(c, err, "reference pressure");
+}
+
 extern "C" lh_status lh_init_state(lh_ctx* c) {
   if (!c) return LH_EINVAL;
   const Geom& g = c->g;
@@ -540,7 +567,8 @@ extern "C" lh_status lh_init_state(lh_ctx* c) {
   memset(h, 0, sizeof(Ctl));
   err = cudaMemcpyAsync(c->a.ctl, h, sizeof(Ctl), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  return cuda_check(c, err, "init_state ctl");
+  if ((st = cuda_check(c, err, "init_state ctl")) != LH_OK) return st;
+  return set_pref(c);
 }
 
 extern "C" lh_status lh_set_state(lh_ctx* c, const double* v, const double* e, const double* x,
@@ -562,7 +590,8 @@ extern "C" lh_status lh_set_state(lh_ctx* c, const double* v, const double* e, c
   c->ctl_host->done = 0;
   err = cudaMemcpyAsync(c->a.ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
-  return cuda_check(c, err, "set_state ctl");
+  if ((st = cuda_check(c, err, "set_state ctl")) != LH_OK) return st;
+  return set_pref(c);
 }
 
 lh_status lagh::device_status(lh_ctx* c) {

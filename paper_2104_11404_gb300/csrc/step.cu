@@ -172,6 +172,20 @@ static int node_blocks(const lh_ctx* c, int64_t n) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+// Mixed path: F^T w of the constant reference pressure -p_ref I (FP64), the
+// part of the stress the FP32 element matrices leave out.
+static cudaError_t launch_pref_ftv(lh_ctx* c, const double* v, const double* e, const double* x,
+                                   const double* w, double* out, cudaStream_t s) {
+  ForceArgs f = {};
+  f.v = v; f.e = e; f.x = x; f.vtest = w;
+  f.nslots = c->g.nelem;
+  f.FTvE = out;
+  f.ctl = c->a.ctl;
+  f.p_ref = &c->a.ctl->p_ref;
+  f.mode = kForceRefPressure;
+  return launch_force_fp64(c, f, s);
+}
+
 // Enqueue one attempt of the RK2-average step on stream s.
 static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s) {
   Arrays& A = c->a;
@@ -190,14 +204,18 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s) {
   f1.tau_bits = &A.ctl->tau_bits[0];
   f1.status = &A.ctl->status;
   f1.ctl = A.ctl;
+  f1.p_ref = &A.ctl->p_ref;
+  f1.mode = kForceFull;
   if ((e = launch_force(c, f1, s)) != cudaSuccess) return e;
   if ((e = launch_gather(c, A.F1E, A.rhs, -1.0, 1, A.ctl, s)) != cudaSuccess) return e;
   if ((e = launch_cg(c, A.rhs, A.acc, A.ctl, s)) != cudaSuccess) return e;
   stage1_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vh, A.xh, A.ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mixed && (e = launch_pref_ftv(c, A.v, A.e, A.x, A.vh, A.tmpE, s)) != cudaSuccess) return e;
   EnergyArgs e1 = {};
   e1.w = A.vh; e1.D = A.D; e1.FK = A.FK;
   e1.srcE = c->ph.source ? A.srcE : nullptr;
+  e1.prefE = mixed ? A.tmpE : nullptr;
   e1.e_base = A.e; e1.e_out = A.eh; e1.frac = 0.5; e1.dt = 0.0; e1.ctl = A.ctl;
   if ((e = launch_energy_update(c, e1, s)) != cudaSuccess) return e;
   // stage 2: forces of S^{n+1/2}
@@ -210,6 +228,8 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s) {
   stage2_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vn, A.vbar,
                                                              A.xn, A.ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (mixed && (e = launch_pref_ftv(c, A.vh, A.eh, A.xh, A.vbar, A.tmpE, s)) != cudaSuccess)
+    return e;
   EnergyArgs e2 = e1;
   e2.w = A.vbar; e2.e_out = A.en; e2.frac = 1.0;
   if ((e = launch_energy_update(c, e2, s)) != cudaSuccess) return e;
@@ -278,6 +298,7 @@ static cudaError_t estimate_into_aux(lh_ctx* c, cudaStream_t s) {
   f.F1E = c->a.F1E;
   f.tau_bits = bits;
   f.status = flag;
+  f.p_ref = &c->a.ctl->p_ref;
   return launch_force(c, f, s);
 }
 
@@ -401,8 +422,20 @@ extern "C" lh_status lh_force(lh_ctx* c, const double* v, const double* e, const
   f.FTvE = vtest ? FTv : nullptr;
   f.tau_bits = bits;
   f.status = flag;
+  f.p_ref = &c->a.ctl->p_ref;
   lh_status st = cuda_check(c, launch_force(c, f, s), "force");
   if (st != LH_OK) return st;
+  if (c->precision == LH_MIXED && vtest) {
+    // add F^T vtest of the reference pressure left out of the FP32 stress; its
+    // F.1 part vanishes identically after the wall condition on the box
+    ForceArgs r = f;
+    r.F1E = nullptr;
+    r.tau_bits = nullptr;
+    r.status = nullptr;
+    r.mode = kForceRefPressure;
+    r.accumulate = 1;
+    if ((st = cuda_check(c, launch_force_fp64(c, r, s), "force ref")) != LH_OK) return st;
+  }
   st = cuda_check(c, launch_gather(c, c->a.F1E, F1, 1.0, 1, nullptr, s), "gather");
   if (st != LH_OK) return st;
   if (dt_est) {
@@ -441,8 +474,18 @@ extern "C" lh_status lh_force_sampled(lh_ctx* c, const int32_t* elem_ids, int64_
   f.FTvE = vtest ? FTv_local : nullptr;
   f.tau_bits = bits;
   f.status = flag;
+  f.p_ref = &c->a.ctl->p_ref;
   lh_status st = cuda_check(c, launch_force(c, f, s), "force_sampled");
   if (st != LH_OK) return st;
+  if (c->precision == LH_MIXED && n > 0) {
+    // element rows carry no wall condition: add the reference-pressure part
+    ForceArgs r = f;
+    r.tau_bits = nullptr;
+    r.status = nullptr;
+    r.mode = kForceRefPressure;
+    r.accumulate = 1;
+    if ((st = cuda_check(c, launch_force_fp64(c, r, s), "force_sampled ref")) != LH_OK) return st;
+  }
   if (dt_est) {
     double hb[2];
     cudaError_t err = cudaMemcpyAsync(hb, c->a.aux, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -76,8 +76,10 @@ def test_mass_operators(dim, k, n):
     assert max_rel(o.mass_solve_e(b), host(g.mass_solve_e(dev(b)))) <= 1e-13
 
 
-def _replay(cfg, nsteps, precision="fp64", tol=1e-12):
-    """Oracle runs free; the GPU replays the oracle's accepted steps."""
+def _per_step(cfg, nsteps, precision="fp64", tol=1e-12):
+    """Each step from the same state: the oracle advances its own trajectory
+    under step control; the GPU is set to the oracle's state, takes the same
+    step and is compared field by field (eq:relerrors)."""
     o = oracle_for(cfg)
     v, e, x = o.init_state()
     g = gpu_for(cfg, precision=precision)
@@ -86,16 +88,17 @@ def _replay(cfg, nsteps, precision="fp64", tol=1e-12):
     assert max_rel(v, host(vg)) <= 1e-15 and max_rel(e, host(eg)) <= 1e-15
     assert max_rel(x, host(xg)) <= 1e-15
     worst = 0.0
+    dt_next = 0.0
     for _ in range(nsteps):
-        stats, log, st = o.run(1e9, v, e, x, dt=0.0 if _ == 0 else dt_next, max_steps=1)
+        g.set_state(v, e, x, t=0.0, dt=1.0)
+        stats, log, st = o.run(1.0, v, e, x, dt=dt_next, max_steps=1)
         assert st == 0
         dt_next = stats["dt"]
-        tau = g.step_fixed(log[0])
+        tau_g = g.step_fixed(float(log[0]))
         vg, eg, xg, _, _ = g.get_state()
         for a, b in ((v, vg), (e, eg), (x, xg)):
             worst = max(worst, rel_l2(a, host(b)))
     assert worst <= tol, worst
-    return o, g
 
 
 @pytest.mark.parametrize("name,n,steps", [("sedov2d_8", (8, 8), 12), ("tg2d_64", (16, 16), 8),
@@ -103,7 +106,14 @@ def _replay(cfg, nsteps, precision="fp64", tol=1e-12):
                                            ("sedov3d_32", (4, 4, 4), 6)])
 def test_steps_fp64_per_step(name, n, steps):
     cfg = W.scaled(name, n=n)
-    _replay(cfg, steps)
+    _per_step(cfg, steps)
+
+
+@pytest.mark.parametrize("name,n,steps", [("sedov2d_8", (8, 8), 6), ("tg2d_64", (16, 16), 6),
+                                           ("gresho2d_256", (8, 8), 4)])
+def test_steps_mixed_per_step(name, n, steps):
+    cfg = W.scaled(name, n=n)
+    _per_step(cfg, steps, precision="mixed", tol=1e-6)
 
 
 def test_sedov_full_run_replay_fp64():
