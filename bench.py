@@ -1,0 +1,380 @@
+"""Benchmark: Lagrangian step DOF-updates/s of the full-order hydro step.
+
+Workload: the 2D Taylor-Green vortex of Section 6.1.3 on 64x64 Q2/Q1 elements
+(the workload the headline metric is quoted on), synthetic (problem initial
+conditions, no data).  One bench step = CHUNK accepted RK2-average time steps
+of the device-controlled time loop (lh_run_to).  value = (2 N_V + N_E) x
+accepted time steps / device time, for the mixed FP32/FP64 path; the FP64 path
+is measured the same way and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+Under torchrun every rank advances its own instance (independent replicas,
+weak scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CHUNK = 50           # accepted time steps per bench step
+WORKLOAD = "tg2d_64"
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            return out
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for i, n in enumerate(names):
+                if r[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        busy = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        out["sm_mhz"] = statistics.median(busy) if busy else None
+        out["sm_max_mhz"] = max(mx) if mx else None
+        out["reasons"] = sorted(reasons)
+        out["samples"] = len(rows)
+        return out
+
+
+def flops_per_element_force(dim, k, mixed):
+    """Algorithmic flops of one element in the force kernel: the trip counts
+    of the sum-factorised contractions (2 flops per multiply-add) plus a fixed
+    budget for the quadrature-point physics (300 flops per point in 2D, 600 in
+    3D: Jacobian algebra, EOS, sound speed, eigen-direction viscosity, stress,
+    time-step bound)."""
+    P, NQ = k + 1, 2 * k
+    ND1, ND2, NQD = P ** dim, k ** dim, NQ ** dim
+    nf = 2 * dim                       # x and v, dim components each
+    if dim == 2:
+        interp = nf * P * NQ * P * 2 + NQD * nf * P * 3
+    else:
+        interp = nf * P * P * NQ * P * 2 + nf * P * NQ * NQ * P * 3 + NQD * nf * P * 4
+    eq = NQD * ND2 * (dim)             # e at the points
+    phys = NQD * (300 if dim == 2 else 600)
+    if not mixed:
+        if dim == 2:
+            trans = dim * dim * P * NQ * NQ + dim * ND1 * dim * NQ
+        else:
+            trans = dim * dim * P * NQ * NQ * NQ + dim * dim * P * P * NQ * NQ + dim * ND1 * dim * NQ
+    else:
+        PK = P * k
+        if dim == 2:
+            trans = dim * dim * PK * NQ * NQ * 2 + dim * ND1 * ND2 * dim * NQ * 2
+        else:
+            trans = (dim * dim * PK * NQ * NQ * NQ * 2 + dim * dim * PK * PK * NQ * NQ * 2 +
+                     dim * ND1 * ND2 * dim * NQ * 2)
+        trans += dim * ND1 * ND2       # FP64 row sums
+    return 2 * (interp + eq + trans) + phys
+
+
+def _env_info():
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    return peaks
+
+
+def run_native(args):
+    import torch
+    from paper_2104_11404_gb300 import build as libbuild
+    from paper_2104_11404_gb300 import lagh
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.hydro import Hydro
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    libbuild.build()
+    cfg = W.CONFIGS[WORKLOAD]
+    nv, ne, nel = W.sizes(cfg)
+    N = 2 * nv + ne
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        return float(t.item())
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def measure(precision):
+        with torch.cuda.stream(stream):
+            g = Hydro(cfg, precision=precision, stream=stream)
+            g.init_state()
+            for _ in range(args.warmup):
+                g.run_to(cfg["t_final"], max_steps=CHUNK)
+            torch.cuda.synchronize()
+            barrier()
+            torch.cuda.synchronize()
+            dev_ms, steps, cg, rejects = 0.0, 0, 0, 0
+            clk = Clocks(local)
+            clk.start()
+            t_wall = time.time()
+            for _ in range(args.steps):
+                flush.fill_(1.0)            # L2 flushed between timed steps
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = g.run_to(cfg["t_final"], max_steps=CHUNK)
+                e1.record(stream)
+                e1.synchronize()
+                dev_ms += e0.elapsed_time(e1)
+                steps += st["steps"]
+                cg += st["cg_iters"]
+                rejects += st["rejects"]
+            wall = time.time() - t_wall
+            clocks = clk.stop()
+            torch.cuda.synchronize()
+            barrier()
+            # end to end through the C ABI with pinned host buffers
+            hv = torch.empty(nv, dtype=torch.float64, pin_memory=True)
+            he = torch.empty(ne, dtype=torch.float64, pin_memory=True)
+            hx = torch.empty(nv, dtype=torch.float64, pin_memory=True)
+            lagh.lh_get_state(g.ctx, hv, he, hx)
+            e2e_ms, e2e_steps = 0.0, 0
+            for _ in range(max(1, args.steps // 2)):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                t_, dt_ = lagh.lh_get_state(g.ctx, None, None, None)
+                lagh.lh_set_state(g.ctx, hv, he, hx, t_, dt_)
+                st = g.run_to(cfg["t_final"], max_steps=CHUNK)
+                lagh.lh_get_state(g.ctx, hv, he, hx)
+                e1.record(stream)
+                e1.synchronize()
+                e2e_ms += e0.elapsed_time(e1)
+                e2e_steps += st["steps"]
+            # dominant kernel: the force evaluation over all elements, timed
+            # alone with events on the library stream
+            v, e, x, _, _ = g.get_state()
+            ids = torch.arange(nel, dtype=torch.int32, device="cuda")
+            F1 = torch.empty(nel * cfg["dim"] * (cfg["order"] + 1) ** cfg["dim"], dtype=torch.float64,
+                             device="cuda")
+            lagh.lh_force_sampled(g.ctx, ids, nel, v, e, x, F1, want_dt=False)
+            reps = 50
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                lagh.lh_force_sampled(g.ctx, ids, nel, v, e, x, F1, want_dt=False)
+            e1.record(stream)
+            e1.synchronize()
+            force_ms = e0.elapsed_time(e1) / reps
+            g.close()
+        return dict(dev_ms=max_over_ranks(dev_ms), steps=sum_over_ranks(steps), cg=cg,
+                    rejects=rejects, wall=wall, clocks=clocks, e2e_ms=max_over_ranks(e2e_ms),
+                    e2e_steps=sum_over_ranks(e2e_steps), force_ms=force_ms)
+
+    res = {p: measure(p) for p in ("mixed", "fp64")}
+    if rank != 0:
+        return None
+    m, f = res["mixed"], res["fp64"]
+    value = N * m["steps"] / (m["dev_ms"] * 1e-3)
+    value64 = N * f["steps"] / (f["dev_ms"] * 1e-3)
+    peaks = _env_info()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, unit counts x clock
+    fp64_peak = 1.25                                      # TFLOP/s, GB300 nominal FP64 rate
+    fl = flops_per_element_force(cfg["dim"], cfg["order"], True) * nel
+    achieved = fl / (m["force_ms"] * 1e-3) / 1e12
+    fl64 = flops_per_element_force(cfg["dim"], cfg["order"], False) * nel
+    achieved64 = fl64 / (f["force_ms"] * 1e-3) / 1e12
+    # kernels launched per attempt: per stage force, gather, cg reset, dim init
+    # passes, (cg iterations x (3 + dim + 1)), update, energy (+ FP64 reference
+    # pressure term on the mixed path); then control and commit
+    d = cfg["dim"]
+    attempts = m["steps"] + m["rejects"]
+    launches = attempts * (2 * (1 + 1 + 1 + d + 1 + 1 + 1) + 2) + m["cg"] * (3 + d + 1)
+    line = {
+        "metric": "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error",
+        "value": value,
+        "unit": "DOF-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": m["dev_ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "2D Taylor-Green vortex 64x64 Q2/Q1, AV on, CFL 0.1, mixed FP32/FP64",
+                   "dofs_per_instance": N, "time_steps_per_bench_step": CHUNK,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "fp64": {"value": value64, "ms_per_step": f["dev_ms"] / args.steps,
+                 "speedup_mixed_over_fp64": value / value64},
+        "roofline": {"bound": "alu", "kernel": "force_kernel (mixed, FP32 stress + element matrices)",
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
+                     "fp64_kernel": {"achieved": achieved64, "peak": fp64_peak,
+                                     "frac": achieved64 / fp64_peak}},
+        "e2e": {"value": N * m["e2e_steps"] / (m["e2e_ms"] * 1e-3), "unit": "DOF-updates/s",
+                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
+        "gpu_launches": int(launches),
+        "clocks": m["clocks"],
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, bounded_seconds=12.0)
+    return line
+
+
+def cpu_baseline(args, bounded_seconds=12.0, steps=None):
+    """The oracle as it stands (single thread, FP64) on a bounded sample of the
+    same workload: accepted time steps from the initial state."""
+    import oracle as O
+    from paper_2104_11404_gb300 import workloads as W
+    cfg = W.CONFIGS[WORKLOAD]
+    o = O.Oracle(dim=cfg["dim"], nx=cfg["n"][0], ny=cfg["n"][1], nz=cfg["n"][2],
+                 lo=list(cfg["lo"]), hi=list(cfg["hi"]), order=cfg["order"], problem=cfg["problem"],
+                 gamma=cfg["gamma"], visc=cfg["visc"], source=cfg.get("source", 1),
+                 cfl=cfg.get("cfl", 0.5))
+    v, e, x = o.init_state()
+    N = o.nv * 2 + o.ne
+    total, t0 = 0, time.time()
+    dt = 0.0
+    while time.time() - t0 < bounded_seconds and (steps is None or total < steps):
+        stats, log, st = o.run(cfg["t_final"], v, e, x, dt=dt, max_steps=5)
+        dt = stats["dt"]
+        total += stats["steps"]
+    el = time.time() - t0
+    return {"value": N * total / el, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d accepted RK2-average steps of the 64x64 Taylor-Green workload from t = 0, "
+                      "single-thread FP64 C oracle, %.1f s" % (total, el)}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host cores, each bench step a
+    bounded sample (CHUNK_REF accepted time steps) of the same workload."""
+    world, rank, local = _dist()
+    if rank != 0:
+        return None
+    import oracle as O
+    from paper_2104_11404_gb300 import workloads as W
+    O.lib()
+    cfg = W.CONFIGS[WORKLOAD]
+    o = O.Oracle(dim=cfg["dim"], nx=cfg["n"][0], ny=cfg["n"][1], nz=cfg["n"][2],
+                 lo=list(cfg["lo"]), hi=list(cfg["hi"]), order=cfg["order"], problem=cfg["problem"],
+                 gamma=cfg["gamma"], visc=cfg["visc"], source=cfg.get("source", 1),
+                 cfl=cfg.get("cfl", 0.5))
+    v, e, x = o.init_state()
+    N = 2 * o.nv + o.ne
+    chunk = 5
+    dt = 0.0
+    for _ in range(args.warmup):
+        stats, _, _ = o.run(cfg["t_final"], v, e, x, dt=dt, max_steps=chunk)
+        dt = stats["dt"]
+    t0 = time.time()
+    total = 0
+    for _ in range(args.steps):
+        stats, _, _ = o.run(cfg["t_final"], v, e, x, dt=dt, max_steps=chunk)
+        dt = stats["dt"]
+        total += stats["steps"]
+    el = time.time() - t0
+    value = N * total / el
+    return {"metric": "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error",
+            "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "2D Taylor-Green vortex 64x64 Q2/Q1, AV on, CFL 0.1",
+                       "dofs_per_instance": N, "time_steps_per_bench_step": chunk},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d bench steps of %d accepted time steps" % (args.steps, chunk)},
+            "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    line = run_reference(args) if args.impl == "reference" else run_native(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

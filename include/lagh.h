@@ -110,7 +110,18 @@ typedef struct lh_phys_desc {
   double q1, q2;         /* linear and quadratic viscosity coefficients */
   double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2 */
   double dt_min_frac;    /* dt < dt_min_frac * t_final -> LH_EDTMIN */
+  int32_t cg_precond;    /* LH_PRECOND_TENSOR (default) or LH_PRECOND_JACOBI */
+  int32_t direct_launch; /* 0 (default): each step attempt is one CUDA graph launch
+                            (the CG iterations a WHILE node inside it); 1: the same
+                            kernels launched one by one, with a host poll of the CG
+                            between iteration batches (for kernel profilers) */
 } lh_phys_desc;
+
+/* Preconditioners of the velocity CG.  TENSOR: the exact inverse of the
+ * kinematic mass matrix when rho0 |J0| is the same in every element (then
+ * M_V is a Kronecker product of assembled 1D mass matrices), applied by
+ * banded 1D line solves; JACOBI: the inverse diagonal. */
+enum { LH_PRECOND_JACOBI = 0, LH_PRECOND_TENSOR = 1 };
 
 typedef struct lh_layout_info {
   int64_t nv;            /* N_V = dim * nnodes */
@@ -195,8 +206,8 @@ LH_API lh_status lh_force_sampled(lh_ctx* ctx, const int32_t* elem_ids, int64_t 
  * partially assembled, no boundary condition. */
 LH_API lh_status lh_mass_apply_v(lh_ctx* ctx, const double* in, double* out);
 /* Solves M_V out = rhs on the non-essential components (essential entries of
- * out are zero) by Jacobi-preconditioned CG from a zero guess (Section 2.2.1
- * momentum equation).  iters / relres (host, may be NULL) return the
+ * out are zero) by preconditioned CG with the partially assembled M_V, from a
+ * zero guess (momentum equation of eq:fom; preconditioner: cg_precond).  iters / relres (host, may be NULL) return the
  * iteration count and ||r||/||b||; both make the call synchronize.
  * LH_ECG if cg_maxit is reached. */
 LH_API lh_status lh_mass_solve_v(lh_ctx* ctx, const double* rhs, double* out,

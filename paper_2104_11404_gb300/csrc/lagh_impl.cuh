@@ -76,10 +76,28 @@ struct Ctl {
   int fixed;        // replay mode: accept every attempt
 };
 
+// Scalars of one CG solve (device memory).
+constexpr int kMaxPartials = 4096;
+struct CgDev {
+  double bb, rz, alpha, beta;
+  int it, done;
+  unsigned int ticket[8];
+};
+
 // Grid barrier state (cooperative persistent kernels).
 struct Barrier {
   unsigned int count;
   unsigned int gen;
+};
+
+// Tensor-product preconditioner: banded Cholesky factors of the assembled 1D
+// reference mass matrices along each direction, full (variant 0) and without
+// the two end nodes (variant 1, the wall-normal component), L[i][m] = L_{i,i-m}.
+struct TensorPC {
+  int64_t off[3][2];   // offsets into Arrays::lfac (units of double)
+  double scale;        // 1 / (rho0 |J0|), the same for every element
+  // (factors in FP32: L[i][0] holds 1 / L_ii)
+  int enabled;
 };
 
 // Work arrays of one context (all device pointers).
@@ -101,6 +119,8 @@ struct Arrays {
   double *tmpE;                 // N_E scratch
   double *tmpV;                 // N_V scratch
   double *aux;                  // 16 doubles of API scratch (estimates, flags, energy)
+  float *lfac;                  // tensor preconditioner factors (FP32)
+  CgDev* cg;
   Barrier* bar;
   Ctl* ctl;
 };
@@ -117,11 +137,11 @@ struct lh_ctx {
   lagh::Arrays a;
   lagh::Ctl* ctl_host;      // pinned mirror of the control block
   int num_sms;
-  int cg_blocks;            // cooperative grid size of the CG kernel
-  int cg_threads;
   double cg_rtol;
   int cg_maxit;
+  lagh::TensorPC tpc;
   cudaStream_t work;          // stream the step graph is captured and launched on
+  cudaStream_t side;          // second stream, used to capture conditional bodies
   int own_work;               // work stream created by the context
   cudaGraphExec_t step_graph;
   int graph_ready;            // 1: graph built, -1: capture unsupported (eager launches)
@@ -185,15 +205,17 @@ cudaError_t launch_energy_update(const lh_ctx* c, const EnergyArgs& ea, cudaStre
 
 // Mass operations.
 cudaError_t launch_mass_apply(const lh_ctx* c, const double* in, double* out, cudaStream_t s);
-// Jacobi-PCG on M_V out = rhs (non-essential components); iteration count,
-// relative residual and failures are written to c->a.ctl.
-cudaError_t launch_cg(const lh_ctx* c, const double* rhs, double* out, const Ctl* gate,
-                      cudaStream_t s);
+// Preconditioned CG on M_V out = rhs (non-essential components); iteration
+// count, relative residual and failures are written to c->a.ctl.
+cudaError_t cg_solve_eager(const lh_ctx* c, const double* rhs, double* out, cudaStream_t s,
+                           int* done_host);
+cudaError_t cg_solve_capture(const lh_ctx* c, const double* rhs, double* out, const Ctl* gate,
+                             cudaStream_t s, cudaStream_t side);
 cudaError_t launch_mass_solve_e(const lh_ctx* c, const double* rhs, double* out, cudaStream_t s);
 // Total energy 1/2 v.M_V.v + 1.M_E.e into *out (device double).
 cudaError_t launch_total_energy(const lh_ctx* c, const double* v, const double* e, double* out,
                                 cudaStream_t s);
-cudaError_t cg_occupancy(lh_ctx* c);
 cudaError_t prepare_kernels(const lh_ctx* c);
+cudaError_t cg_prepare(const lh_ctx* c);
 
 }  // namespace lagh

@@ -204,6 +204,7 @@ extern "C" void lh_default_phys(lh_phys_desc* p) {
   p->q2 = 2.0;
   p->cg_rtol = 1e-14;
   p->dt_min_frac = 1e-12;
+  p->cg_precond = LH_PRECOND_TENSOR;
 }
 
 extern "C" const char* lh_status_string(lh_status s) {
@@ -235,6 +236,9 @@ static void free_all(lh_ctx* c) {
   if (c->a.FK) { cudaFree(c->a.FK); c->a.FK = nullptr; }
   if (c->a.bar) { cudaFree(c->a.bar); c->a.bar = nullptr; }
   if (c->a.ctl) { cudaFree(c->a.ctl); c->a.ctl = nullptr; }
+  if (c->a.cg) { cudaFree(c->a.cg); c->a.cg = nullptr; }
+  if (c->a.lfac) { cudaFree(c->a.lfac); c->a.lfac = nullptr; }
+  if (c->side) { cudaStreamDestroy(c->side); c->side = nullptr; }
   if (c->ctl_host) { cudaFreeHost(c->ctl_host); c->ctl_host = nullptr; }
   if (c->graph_ready == 1) cudaGraphExecDestroy(c->step_graph);
   c->graph_ready = 0;
@@ -270,6 +274,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   c->graph_ready = 0;
   c->ev0 = c->ev1 = nullptr;
   c->work = nullptr;
+  c->side = nullptr;
   c->own_work = 0;
   c->stream = (cudaStream_t)stream;
   c->precision = precision;
@@ -341,7 +346,6 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   if ((st = cuda_check(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev),
                        "sm count")) != LH_OK)
     return fail(st, c->err);
-  if ((st = cuda_check(c, cg_occupancy(c), "cg occupancy")) != LH_OK) return fail(st, c->err);
   if ((st = cuda_check(c, prepare_kernels(c), "kernel attributes")) != LH_OK) return fail(st, c->err);
 
   Arrays& A = c->a;
@@ -363,14 +367,16 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   }
   if (e == cudaSuccess) e = dalloc(&A.rho0K, nelem);
   if (e == cudaSuccess) e = dalloc(&A.dinv, (size_t)g.nnodes);
-  size_t npart = (size_t)(4 * c->cg_blocks > 1024 ? 4 * c->cg_blocks : 1024);
-  if (e == cudaSuccess) e = dalloc(&A.partials, npart);
+  if (e == cudaSuccess) e = dalloc(&A.partials, (size_t)5 * kMaxPartials);
+  if (e == cudaSuccess) e = dalloc(&A.cg, 1);
+  if (e == cudaSuccess) e = cudaMemset(A.cg, 0, sizeof(CgDev));
   if (e == cudaSuccess) e = dalloc(&A.aux, 16);
   if (e == cudaSuccess) e = dalloc(&A.bar, 1);
   if (e == cudaSuccess) e = dalloc(&A.ctl, 1);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->ctl_host, sizeof(Ctl));
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
   if (e == cudaSuccess) {
     if (c->stream == nullptr) {
       e = cudaStreamCreateWithFlags(&c->work, cudaStreamNonBlocking);
@@ -400,6 +406,62 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     }
     for (auto& x : diag) x = 1.0 / x;
   }
+  // tensor-product preconditioner: exact inverse of M_V when rho0 |J0| is the
+  // same in every element (M_s = rho0|J0| G_x (x) G_y [(x) G_z])
+  std::vector<double> lf;
+  memset(&c->tpc, 0, sizeof(c->tpc));
+  {
+    bool uniform = true;
+    for (int64_t el = 1; el < g.nelem; ++el)
+      if (rho0K[el] != rho0K[0]) uniform = false;
+    const int P = k + 1;
+    for (int dd = 0; dd < d; ++dd)
+      for (int var = 0; var < 2; ++var) {
+        int nfull = g.nn[dd];
+        int N = nfull - 2 * var;
+        c->tpc.off[dd][var] = (int64_t)lf.size();
+        // banded matrix rows of the assembled 1D reference mass matrix
+        auto G = [&](int i, int j) -> double {
+          int gi = i + var, gj = j + var;
+          double s = 0.0;
+          for (int e = 0; e < g.n[dd]; ++e) {
+            int a = gi - e * k, b = gj - e * k;
+            if (a >= 0 && a < P && b >= 0 && b < P) s += c->basis.M1[a][b];
+          }
+          return s;
+        };
+        std::vector<double> L((size_t)N * (k + 1), 0.0);
+        for (int i = 0; i < N; ++i) {
+          for (int m = k; m >= 1; --m) {
+            int j = i - m;
+            if (j < 0) continue;
+            double s = G(i, j);
+            for (int q = 1; q <= k; ++q) {  // sum over columns l < j of L_il L_jl
+              int l = j - q;
+              if (l < 0 || i - l > k) continue;
+              s -= L[(size_t)i * (k + 1) + (i - l)] * L[(size_t)j * (k + 1) + q];
+            }
+            L[(size_t)i * (k + 1) + m] = s / L[(size_t)j * (k + 1)];
+          }
+          double s = G(i, i);
+          for (int m = 1; m <= k; ++m) s -= L[(size_t)i * (k + 1) + m] * L[(size_t)i * (k + 1) + m];
+          L[(size_t)i * (k + 1)] = sqrt(s);
+        }
+        // the device solves multiply by the reciprocal diagonal
+        for (int i = 0; i < N; ++i) L[(size_t)i * (k + 1)] = 1.0 / L[(size_t)i * (k + 1)];
+        lf.insert(lf.end(), L.begin(), L.end());
+      }
+    c->tpc.scale = 1.0 / rho0K[0];
+    c->tpc.enabled = (phys->cg_precond == LH_PRECOND_TENSOR) && uniform;
+  }
+  // the line solves run in FP32 (a preconditioner only needs to be close to
+  // the inverse; the CG residuals and iterates stay FP64)
+  std::vector<float> lff(lf.begin(), lf.end());
+  e = dalloc(&A.lfac, lff.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpy(A.lfac, lff.data(), lff.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if ((st = cuda_check(c, e, "preconditioner")) != LH_OK) return fail(st, c->err);
+  if ((st = cuda_check(c, cg_prepare(c), "cg attributes")) != LH_OK) return fail(st, c->err);
   Ctl ctl0;
   memset(&ctl0, 0, sizeof(ctl0));
   e = cudaMemcpy(A.rho0K, rho0K.data(), nelem * sizeof(double), cudaMemcpyHostToDevice);

@@ -9,6 +9,7 @@
 // sequence is captured once as a CUDA graph and relaunched without host
 // synchronisation; the host only polls the control block between batches.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include "device_util.cuh"
@@ -186,8 +187,15 @@ static cudaError_t launch_pref_ftv(lh_ctx* c, const double* v, const double* e, 
   return launch_force_fp64(c, f, s);
 }
 
+// CG of one stage: a WHILE graph node when capturing, else an eager loop.
+static cudaError_t stage_cg(lh_ctx* c, cudaStream_t s, bool capturing) {
+  if (capturing) return cg_solve_capture(c, c->a.rhs, c->a.acc, c->a.ctl, s, c->side);
+  int done = 0;
+  return cg_solve_eager(c, c->a.rhs, c->a.acc, s, &done);
+}
+
 // Enqueue one attempt of the RK2-average step on stream s.
-static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s) {
+static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   Arrays& A = c->a;
   const Geom& g = c->g;
   const bool mixed = c->precision == LH_MIXED;
@@ -208,7 +216,7 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s) {
   f1.mode = kForceFull;
   if ((e = launch_force(c, f1, s)) != cudaSuccess) return e;
   if ((e = launch_gather(c, A.F1E, A.rhs, -1.0, 1, A.ctl, s)) != cudaSuccess) return e;
-  if ((e = launch_cg(c, A.rhs, A.acc, A.ctl, s)) != cudaSuccess) return e;
+  if ((e = stage_cg(c, s, capturing)) != cudaSuccess) return e;
   stage1_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vh, A.xh, A.ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (mixed && (e = launch_pref_ftv(c, A.v, A.e, A.x, A.vh, A.tmpE, s)) != cudaSuccess) return e;
@@ -224,7 +232,7 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s) {
   f2.tau_bits = &A.ctl->tau_bits[1];
   if ((e = launch_force(c, f2, s)) != cudaSuccess) return e;
   if ((e = launch_gather(c, A.F1E, A.rhs, -1.0, 1, A.ctl, s)) != cudaSuccess) return e;
-  if ((e = launch_cg(c, A.rhs, A.acc, A.ctl, s)) != cudaSuccess) return e;
+  if ((e = stage_cg(c, s, capturing)) != cudaSuccess) return e;
   stage2_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vn, A.vbar,
                                                              A.xn, A.ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -246,27 +254,39 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s) {
 
 static lh_status build_graph(lh_ctx* c) {
   if (c->graph_ready != 0) return LH_OK;
+  if (c->phys_desc.direct_launch) {
+    c->graph_ready = -1;
+    return LH_OK;
+  }
   cudaGraph_t graph = nullptr;
+  const char* where = "begin capture";
   cudaError_t e = cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaError_t e2 = enqueue_attempt(c, c->work);
+    cudaError_t e2 = enqueue_attempt(c, c->work, true);
+    where = "enqueue";
     e = cudaStreamEndCapture(c->work, &graph);
     if (e2 != cudaSuccess) e = e2;
+    else where = "end capture";
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->step_graph, graph, 0);
+  if (e == cudaSuccess) {
+    where = "instantiate";
+    e = cudaGraphInstantiate(&c->step_graph, graph, 0);
+  }
   if (graph) cudaGraphDestroy(graph);
   if (e == cudaSuccess) {
     c->graph_ready = 1;
   } else {
     cudaGetLastError();  // capture not available: launch the sequence eagerly
     c->graph_ready = -1;
+    fprintf(stderr, "lagh: step graph not built at %s (%s); launching kernels directly\n",
+            where, cudaGetErrorString(e));
   }
   return LH_OK;
 }
 
 static cudaError_t launch_attempt(lh_ctx* c) {
   if (c->graph_ready == 1) return cudaGraphLaunch(c->step_graph, c->work);
-  return enqueue_attempt(c, c->work);
+  return enqueue_attempt(c, c->work, false);
 }
 
 // Orders the work stream after the user stream (and back at the end).
@@ -340,6 +360,9 @@ static lh_status run_attempts(lh_ctx* c, double t_final, int64_t max_steps, int 
     if (!fixed && h.dt > 0.0) {
       double rem = (h.t_final - h.t) / h.dt;
       batch = rem > 64.0 ? 64 : (int64_t)rem + 1;
+      // a few attempts beyond the remaining step budget absorb redone steps
+      int64_t left = h.max_steps - h.steps + 2;
+      if (left < batch) batch = left > 1 ? left : 1;
     }
     if (batch > max_attempts - attempts) batch = max_attempts - attempts;
     for (int64_t i = 0; i < batch; ++i) {
@@ -510,7 +533,8 @@ extern "C" lh_status lh_mass_apply_v(lh_ctx* c, const double* in, double* out) {
 extern "C" lh_status lh_mass_solve_v(lh_ctx* c, const double* rhs, double* out, int32_t* iters,
                                      double* relres) {
   if (!c || !rhs || !out) return LH_EINVAL;
-  lh_status st = cuda_check(c, launch_cg(c, rhs, out, nullptr, c->stream), "cg");
+  int done = 0;
+  lh_status st = cuda_check(c, cg_solve_eager(c, rhs, out, c->stream, &done), "cg");
   if (st != LH_OK) return st;
   if (iters || relres) {
     if ((st = read_ctl(c, c->stream)) != LH_OK) return st;

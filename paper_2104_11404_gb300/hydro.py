@@ -27,6 +27,7 @@ class Hydro:
         phys.source = int(cfg.get("source", 1))
         phys.blast_energy = float(cfg.get("blast_energy", 0.25))
         phys.e_uniform = float(cfg.get("e_uniform", 1.0))
+        phys.cfl = float(cfg.get("cfl", 0.5))
         if cg_rtol is not None:
             phys.cg_rtol = cg_rtol
         if cg_maxit is not None:

@@ -16,6 +16,7 @@ LH_OK, LH_EINVAL, LH_ENOMEM, LH_ECUDA, LH_ETANGLED, LH_ENONFINITE, LH_EDTMIN, LH
     LH_ETIMEOUT, LH_EUNSUPPORTED = range(10)
 LH_FP64, LH_MIXED = 0, 1
 LH_SEDOV, LH_TAYLOR_GREEN, LH_GRESHO, LH_UNIFORM = 1, 2, 3, 4
+LH_PRECOND_JACOBI, LH_PRECOND_TENSOR = 0, 1
 
 # every entry point declared in include/lagh.h
 API_NAMES = [
@@ -42,7 +43,8 @@ class lh_phys_desc(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("cfl_mu", ctypes.c_double),
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("gamma_dt", ctypes.c_double), ("q1", ctypes.c_double), ("q2", ctypes.c_double),
-                ("cg_rtol", ctypes.c_double), ("dt_min_frac", ctypes.c_double)]
+                ("cg_rtol", ctypes.c_double), ("dt_min_frac", ctypes.c_double),
+                ("cg_precond", ctypes.c_int32), ("direct_launch", ctypes.c_int32)]
 
 
 class lh_layout_info(ctypes.Structure):

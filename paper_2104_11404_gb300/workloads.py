@@ -19,9 +19,11 @@ CONFIGS = {
     "sedov2d_8": dict(dim=2, n=(8, 8, 1), order=2, problem=SEDOV, gamma=1.4,
                       lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), visc=1, blast_energy=0.25,
                       t_final=0.8),
-    # 2D Taylor-Green vortex with its manufactured energy source, 64x64 Q2/Q1, t_f = 0.5
+    # 2D Taylor-Green vortex with its manufactured energy source, 64x64 Q2/Q1, t_f = 0.5,
+    # CFL 0.1 as for the Taylor-Green runs of Table tab:fom
     "tg2d_64": dict(dim=2, n=(64, 64, 1), order=2, problem=TAYLOR_GREEN, gamma=5.0 / 3.0,
-                    lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), visc=1, source=1, t_final=0.5),
+                    lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), visc=1, source=1, cfl=0.1,
+                    t_final=0.5),
     # 3D point blast, [0,1]^3, 32^3 Q2/Q1, t_f = 0.6
     "sedov3d_32": dict(dim=3, n=(32, 32, 32), order=2, problem=SEDOV, gamma=1.4,
                        lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), visc=1, blast_energy=0.25,
