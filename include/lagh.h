@@ -60,7 +60,9 @@ typedef enum lh_status {
   LH_EDTMIN = 6,       /* step size collapsed below dt_min_frac * t_final */
   LH_ECG = 7,          /* CG did not reach cg_rtol within cg_maxit iterations */
   LH_ETIMEOUT = 8,     /* a device-wide barrier waited longer than its limit */
-  LH_EUNSUPPORTED = 9  /* valid but not built (order/dimension/quadrature) */
+  LH_EUNSUPPORTED = 9, /* valid but not built (order/dimension/quadrature) */
+  LH_ETOOLARGE = 10    /* the mesh does not fit the fixed working memory of
+                          lh_force_static */
 } lh_status;
 
 typedef enum lh_precision {
@@ -232,6 +234,35 @@ LH_API lh_status lh_step(lh_ctx* ctx, double t_final, int32_t* accepted, double*
  * accepted step sizes in order, at most dt_log_cap of them. */
 LH_API lh_status lh_run_to(lh_ctx* ctx, double t_final, int64_t max_steps,
                     lh_run_stats* stats, double* dt_log, int64_t dt_log_cap);
+
+/* F.1 of a state without allocating memory and without a context.  This entry
+ * point is a service of the library, not a step of the paper: the paper has no
+ * counterpart.  It is for callers that cannot call cudaMalloc (their device
+ * memory is owned by a framework pool or budgeted up front, or they cannot
+ * afford an allocation inside a latency-critical loop); lh_create would
+ * allocate, this does not.
+ * Computes what lh_force computes for F1 and dt_est, in FP64: F1 (device, N_V)
+ * = F.1 of the state (v, e, x: device pointers, layouts as above) with the
+ * essential components set to zero, and dt_est (host, may be NULL) = the
+ * minimum of eq:adaptive-timestep over all quadrature points.  rho0 = 1 as in
+ * every problem of Section 6.1.
+ * Working memory: one file-scope device array of 4 Mi doubles (32 MiB) that
+ * every GPU which loads the library holds until the process exits.  A mesh
+ * fits when 16 + n_e (1 + dim (k+1)^dim) <= 4194304 doubles (for example
+ * 2D Q2 up to 220,000 elements, 3D Q2 up to 51,000); larger meshes return
+ * LH_ETOOLARGE before any GPU work.  The first call on a device looks up the
+ * array's device address and sets kernel attributes for that device (with the
+ * device current); make that first call before any stream capture.
+ * Every call shares the array and the array keeps the last call's contents
+ * (the estimate and flag slots are reset at the start of each call); calls
+ * whose work overlaps on the GPU (different streams, or threads) race on it:
+ * order them on one stream.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  Synchronizes stream when dt_est != NULL.  Errors:
+ * LH_EINVAL / LH_EUNSUPPORTED (descriptors), LH_ETOOLARGE, LH_ECUDA,
+ * LH_ETANGLED, LH_ENONFINITE. */
+LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* disc,
+                                 const lh_phys_desc* phys, const double* v, const double* e,
+                                 const double* x, double* F1, double* dt_est, void* stream);
 
 #ifdef __cplusplus
 }

@@ -219,6 +219,7 @@ extern "C" const char* lh_status_string(lh_status s) {
     case LH_ECG: return "CG did not converge";
     case LH_ETIMEOUT: return "device barrier timed out";
     case LH_EUNSUPPORTED: return "unsupported configuration";
+    case LH_ETOOLARGE: return "mesh exceeds the fixed working memory";
   }
   return "unknown status";
 }

@@ -13,7 +13,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "_lib", "liblagh.so")
 
 LH_OK, LH_EINVAL, LH_ENOMEM, LH_ECUDA, LH_ETANGLED, LH_ENONFINITE, LH_EDTMIN, LH_ECG, \
-    LH_ETIMEOUT, LH_EUNSUPPORTED = range(10)
+    LH_ETIMEOUT, LH_EUNSUPPORTED, LH_ETOOLARGE = range(11)
 LH_FP64, LH_MIXED = 0, 1
 LH_SEDOV, LH_TAYLOR_GREEN, LH_GRESHO, LH_UNIFORM = 1, 2, 3, 4
 LH_PRECOND_JACOBI, LH_PRECOND_TENSOR = 0, 1
@@ -23,7 +23,7 @@ API_NAMES = [
     "lh_default_phys", "lh_status_string", "lh_create", "lh_destroy", "lh_last_error",
     "lh_layout", "lh_init_state", "lh_set_state", "lh_get_state", "lh_force",
     "lh_force_sampled", "lh_mass_apply_v", "lh_mass_solve_v", "lh_mass_solve_e",
-    "lh_total_energy", "lh_step_fixed", "lh_step", "lh_run_to",
+    "lh_total_energy", "lh_step_fixed", "lh_step", "lh_run_to", "lh_force_static",
 ]
 
 
@@ -105,6 +105,9 @@ def load():
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.lh_run_to.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, ctypes.POINTER(lh_run_stats),
                             _dp, ctypes.c_int64]
+    L.lh_force_static.argtypes = [ctypes.POINTER(lh_mesh_desc), ctypes.POINTER(lh_disc_desc),
+                                  ctypes.POINTER(lh_phys_desc), _dp, _dp, _dp, _dp,
+                                  ctypes.POINTER(ctypes.c_double), _vp]
     for name in API_NAMES:
         if name not in ("lh_default_phys", "lh_status_string", "lh_last_error"):
             getattr(L, name).restype = S
@@ -240,3 +243,15 @@ def lh_run_to(ctx, t_final, max_steps=2 ** 62, dt_log=None, dt_log_cap=0):
                           int(dt_log_cap))
     _check(ctx, st)
     return {k: getattr(stats, k) for k, _ in lh_run_stats._fields_}
+
+
+def lh_force_static(mesh, disc, phys, v, e, x, F1, stream=None, want_dt=True):
+    """F.1 of a state with no device allocation (see include/lagh.h); returns
+    the time-step estimate.  Raises LaghError on a non-zero status."""
+    dt = ctypes.c_double()
+    st = load().lh_force_static(ctypes.byref(mesh), ctypes.byref(disc), ctypes.byref(phys),
+                                _ptr(v), _ptr(e), _ptr(x), _ptr(F1),
+                                ctypes.byref(dt) if want_dt else None, stream)
+    if st != LH_OK:
+        raise LaghError(st, "lh_force_static failed")
+    return dt.value if want_dt else None
