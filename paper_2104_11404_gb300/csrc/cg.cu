@@ -18,7 +18,9 @@
 
 namespace lagh {
 
-constexpr int kLineThreads = 32;
+constexpr int kLineThreads = 256;  // one CTA per tile of 32 lines x 32 positions
+// band half-width of the truncated 1D inverses, by H1 order (must match setup)
+template <int K> struct PB { static constexpr int B = K == 1 ? 14 : (K == 2 ? 22 : 30); };
 constexpr int kNodeThreads = 256;
 enum { kTicketPass0 = 0, kTicketPassL = 1, kTicketA = 2, kTicketB = 3, kTicketJ = 4 };
 
@@ -45,8 +47,18 @@ __device__ __forceinline__ bool gated(const CgArgs& a) {
   return (a.gate != nullptr && a.gate->done) || a.cg->done;
 }
 
-// Block partial -> last block adds all partials in block order.  Returns true
-// in every thread of the last block; *total is valid there.
+// Sum of the per-block partials by the whole (last) block, in a fixed order:
+// thread t adds partials t, t + blockDim, ... in sequence, then a fixed tree.
+// All threads must call it; the result is valid in thread 0.
+__device__ __forceinline__ double sum_partials(const double* part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (unsigned int i = threadIdx.x; i < gridDim.x; i += blockDim.x) acc += __ldcg(&part[i]);
+  return block_sum(acc, sh);
+}
+
+// Block partial -> the last block to finish adds all partials (sum_partials).
+// Returns true in every thread of the last block; *total is valid in thread 0.
 __device__ __forceinline__ bool reduce_last(double v, double* part, unsigned int* ticket,
                                             double* total) {
   __shared__ double sh[32];
@@ -60,11 +72,10 @@ __device__ __forceinline__ bool reduce_last(double v, double* part, unsigned int
   }
   __syncthreads();
   if (!last) return false;
+  __threadfence();
+  const double tot = sum_partials(part);
   if (threadIdx.x == 0) {
-    __threadfence();
-    double acc = 0.0;
-    for (unsigned int i = 0; i < gridDim.x; ++i) acc += __ldcg(&part[i]);
-    *total = acc;
+    *total = tot;
     *ticket = 0u;
   }
   __syncthreads();
@@ -81,12 +92,6 @@ __device__ __forceinline__ void write_partial(double v, double* part) {
   }
 }
 
-__device__ __forceinline__ double sum_partials(const double* part) {
-  double acc = 0.0;
-  for (unsigned int i = 0; i < gridDim.x; ++i) acc += __ldcg(&part[i]);
-  return acc;
-}
-
 __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
   CgDev* cg = a.cg;
   a.ctl->cg_last_iters = cg->it;
@@ -97,137 +102,119 @@ __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
 
 // ---------------------------------------------------- tensor line passes --
 
-// One warp owns 32 node lines of one direction (consecutive line numbers): it
-// stages them in shared memory with coalesced loads, each lane runs the banded
-// forward/backward substitution of its line from shared memory in FP32, and
-// the warp writes the lines back with coalesced stores.
+// One pass of the tensor-product preconditioner along direction d: every
+// node line of every component is multiplied by the banded inverse of the 1D
+// mass matrix.  A CTA owns a tile of 32 lines x 32 positions: it stages the
+// tile and its +-B halo along the line in shared memory (coalesced: along x
+// the lines are contiguous rows, along y / z neighbouring lines are
+// neighbouring nodes), then each thread forms 4 outputs in FP32.
 //
 // mode: 0 = first pass of the initial preconditioning (reads rhs, writes r = b
 // on free components and x = 0, sums b.b), 1 = first pass inside the loop
-// (reads r), 2 = later pass (in place on z).  last: the pass along the last
-// direction (sums r.z; init also writes p = z).
+// (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
+// last: the pass along the last direction (sums r.z; init also writes p = z).
 template <int DIM, int K>
 __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, int d, int mode,
-                                                              int last, int init) {
+                                                              int last, int init,
+                                                              const double* src_in,
+                                                              double* dst) {
   if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) return;
   if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
     a.cg->done = 0;
     a.cg->it = 0;
   }
-  extern __shared__ float lines[];  // [32][ld], ld odd: conflict-free lane rows
+  constexpr int B = PB<K>::B;
+  constexpr int W = 2 * B + 1;
+  constexpr int TP = 32;
+  constexpr int ldt = TP + 2 * B + 1;  // odd row length
+  __shared__ float tile[32 * ldt];     // 32 lines x (32 positions + halo)
+  __shared__ float wrows[TP * W];      // band rows of the 32 positions
   const Geom& g = a.g;
   const int nd = g.nn[d];
-  const int ld = nd | 1;
   const int64_t nlines = g.nnodes / nd;
+  const int64_t lgroups = (nlines + 31) / 32;
+  const int pblocks = (nd + TP - 1) / TP;
   const int64_t stride = d == 0 ? 1 : (d == 1 ? (int64_t)g.nn[0] : (int64_t)g.nn[0] * g.nn[1]);
-  const int lane = threadIdx.x;
-  const int64_t task = (int64_t)blockIdx.x * 32 + lane;
-  const bool active = task < DIM * nlines;
-  int c = 0;
-  int I[3] = {0, 0, 0};
-  int64_t base = 0;
-  bool wall_line = true;
-  if (active) {
-    c = (int)(task / nlines);
-    const int64_t line = task - (int64_t)c * nlines;
+  // block -> (component, line group, position block)
+  int64_t bid = blockIdx.x;
+  const int pb = (int)(bid % pblocks);
+  bid /= pblocks;
+  const int64_t lg = bid % lgroups;
+  const int c = (int)(bid / lgroups);
+  const int p0 = pb * TP;
+  const int var = (c == d) ? 1 : 0;
+  const float* Wt = a.lfac + a.tpc.off[d][var];
+  const int tid = threadIdx.x;
+  // line l of the tile: its base node and whether it is a wall-normal line
+  auto line_info = [&](int l, int64_t& base, bool& wall) -> bool {
+    const int64_t line = lg * 32 + l;
+    if (line >= nlines) return false;
+    int I[3] = {0, 0, 0};
     if (d == 0) { I[1] = (int)(line % g.nn[1]); I[2] = (int)(line / g.nn[1]); }
     else if (d == 1) { I[0] = (int)(line % g.nn[0]); I[2] = (int)(line / g.nn[0]); }
     else { I[0] = (int)(line % g.nn[0]); I[1] = (int)(line / g.nn[0]); }
     base = (int64_t)c * g.nnodes + node_index(g, I[0], I[1], I[2]);
-    wall_line = (c != d) && (I[c] == 0 || I[c] == g.nn[c] - 1);
-  }
-  const double* src = mode == 0 ? a.rhs : (mode == 1 ? a.r : a.z);
-  float* my = lines + lane * ld;
-  double l_bb = 0.0, l_rz = 0.0;
+    wall = (c != d) && (I[c] == 0 || I[c] == g.nn[c] - 1);
+    return true;
+  };
+  const double* src = mode == 0 ? a.rhs : src_in;
   const float scl = (mode == 2) ? 1.0f : (float)a.tpc.scale;
-
-  // ---- load: entry i of the line of lane l ----
-  auto load_entry = [&](int l, int64_t bl, int cl, bool wl, int i) {
-    const int64_t k = bl + i * stride;
-    const bool ess = wl || (cl == d && (i == 0 || i == nd - 1));
-    double v = ess ? 0.0 : src[k];
+  double l_bb = 0.0, l_rz = 0.0;
+  // stage the tile with its halo: positions [p0 - B, p0 + TP + B)
+  const int span = TP + 2 * B;
+  for (int idx = tid; idx < 32 * span; idx += kLineThreads) {
+    // along x (d == 0) walk a line, otherwise walk across lines
+    const int l = d == 0 ? idx / span : idx % 32;
+    const int q = d == 0 ? idx - l * span : idx / 32;
+    const int pos = p0 - B + q;
+    float val = 0.0f;
+    int64_t base;
+    bool wall;
+    if (pos >= var && pos < nd - var && line_info(l, base, wall) && !wall) {
+      const double v = src[base + pos * stride];
+      val = (float)v * scl;
+    }
+    tile[l * ldt + q] = val;
+  }
+  {
+    const int nrow = nd - 2 * var;  // rows of the band (interior positions)
+    for (int idx = tid; idx < TP * W; idx += kLineThreads) {
+      const int q = idx / W, m = idx - q * W;
+      const int row = p0 + q - var;
+      wrows[idx] = (row >= 0 && row < nrow) ? Wt[(int64_t)row * W + m] : 0.0f;
+    }
+  }
+  __syncthreads();
+  // outputs: thread -> (line, 4 positions)
+  for (int o = tid; o < 32 * TP; o += kLineThreads) {
+    const int l = d == 0 ? o / TP : o % 32;
+    const int q = d == 0 ? o - l * TP : o / 32;
+    const int pos = p0 + q;
+    int64_t base;
+    bool wall;
+    if (pos >= nd || !line_info(l, base, wall)) continue;
+    const int64_t kk = base + pos * stride;
+    double zv = 0.0;
+    if (!wall && pos >= var && pos < nd - var) {
+      const float* wr = wrows + q * W;
+      const float* tr = tile + l * ldt + q;  // tile position of offset -B
+      float acc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < W; ++m) acc += wr[m] * tr[m];
+      zv = (double)acc;
+    }
     if (mode == 0) {
-      a.r[k] = v;
-      a.x[k] = 0.0;
-      l_bb += v * v;
+      const bool ess = wall || pos < var || pos >= nd - var;
+      const double bv = ess ? 0.0 : a.rhs[kk];
+      a.r[kk] = bv;
+      a.x[kk] = 0.0;
+      l_bb += bv * bv;
     }
-    lines[l * ld + i] = (float)v * scl;
-  };
-  if (d == 0) {
-    // lines are contiguous rows: the warp loads row after row
-    for (int l = 0; l < 32; ++l) {
-      const int64_t bl = __shfl_sync(0xffffffffu, base, l);
-      const int cl = __shfl_sync(0xffffffffu, c, l);
-      const int wl = __shfl_sync(0xffffffffu, (int)wall_line, l);
-      const int al = __shfl_sync(0xffffffffu, (int)active, l);
-      if (!al) continue;
-      for (int i = lane; i < nd; i += 32) load_entry(l, bl, cl, wl != 0, i);
-    }
-  } else if (active) {
-    // neighbouring lanes hold neighbouring lines: every load is coalesced
-    for (int i = 0; i < nd; ++i) load_entry(lane, base, c, wall_line, i);
-  }
-  __syncwarp();
-
-  // ---- banded Cholesky solve of this lane's line (FP32, shared memory) ----
-  if (active && !wall_line) {
-    const int var = (c == d) ? 1 : 0;
-    const int N = nd - 2 * var;
-    const float* L = a.lfac + a.tpc.off[d][var];  // L[i][0] holds 1 / L_ii
-    float* z = my + var;
-    float win[K];
-#pragma unroll
-    for (int m = 0; m < K; ++m) win[m] = 0.0f;
-    for (int i = 0; i < N; ++i) {
-      const float* Li = L + i * (K + 1);
-      float zz = z[i];
-#pragma unroll
-      for (int m = 1; m <= K; ++m) zz -= Li[m] * win[m - 1];
-      const float y = zz * Li[0];
-#pragma unroll
-      for (int m = K - 1; m > 0; --m) win[m] = win[m - 1];
-      win[0] = y;
-      z[i] = y;
-    }
-#pragma unroll
-    for (int m = 0; m < K; ++m) win[m] = 0.0f;
-    for (int i = N - 1; i >= 0; --i) {
-      float yy = z[i];
-#pragma unroll
-      for (int m = 1; m <= K; ++m)
-        if (i + m < N) yy -= L[(i + m) * (K + 1) + m] * win[m - 1];
-      const float xv = yy * L[i * (K + 1)];
-#pragma unroll
-      for (int m = K - 1; m > 0; --m) win[m] = win[m - 1];
-      win[0] = xv;
-      z[i] = xv;
-    }
-    if (var) {
-      my[0] = 0.0f;
-      my[nd - 1] = 0.0f;
-    }
-  }
-  __syncwarp();
-
-  // ---- store z (and p = z, r.z on the last pass) ----
-  auto store_entry = [&](int l, int64_t bl, int i) {
-    const int64_t k = bl + i * stride;
-    const double zv = (double)lines[l * ld + i];
-    a.z[k] = zv;
+    dst[kk] = zv;
     if (last) {
-      l_rz += a.r[k] * zv;
-      if (init) a.p[k] = zv;
+      l_rz += a.r[kk] * zv;
+      if (init) a.p[kk] = zv;
     }
-  };
-  if (d == 0) {
-    for (int l = 0; l < 32; ++l) {
-      const int64_t bl = __shfl_sync(0xffffffffu, base, l);
-      const int al = __shfl_sync(0xffffffffu, (int)active, l);
-      if (!al) continue;
-      for (int i = lane; i < nd; i += 32) store_entry(l, bl, i);
-    }
-  } else if (active) {
-    for (int i = 0; i < nd; ++i) store_entry(lane, base, i);
   }
 
   double tot;
@@ -242,6 +229,7 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
       if (init) {
         cg->rz = tot;
         cg->it = 0;
+        cg->beta = 0.0;
         if (!(cg->bb > 0.0)) {  // zero right-hand side: x = 0 is the solution
           cg->done = 1;
           report(a, true, 0.0);
@@ -280,12 +268,14 @@ __global__ void __launch_bounds__(kNodeThreads) cg_jacobi_init_kernel(const CgAr
   }
   write_partial(l_bb, a.part);
   double rz;
-  if (reduce_last(l_rz, a.part + kMaxPartials, &a.cg->ticket[kTicketJ], &rz) &&
-      threadIdx.x == 0) {
+  if (reduce_last(l_rz, a.part + kMaxPartials, &a.cg->ticket[kTicketJ], &rz)) {
+    const double bb = sum_partials(a.part);
+    if (threadIdx.x != 0) return;
     CgDev* cg = a.cg;
-    cg->bb = sum_partials(a.part);
+    cg->bb = bb;
     cg->rz = rz;
     cg->it = 0;
+    cg->beta = 0.0;
     if (!(cg->bb > 0.0)) {
       cg->done = 1;
       report(a, true, 0.0);
@@ -295,6 +285,8 @@ __global__ void __launch_bounds__(kNodeThreads) cg_jacobi_init_kernel(const CgAr
 
 // ------------------------------------------------------ loop kernels ----
 
+// Element phase of M p with the search direction formed on the fly,
+// p = z + beta p_old (beta = 0 on the first iteration, where p_old = z).
 template <int DIM, int K>
 __global__ void __launch_bounds__(256) cg_elem_kernel(const CgArgs a) {
   using L = ML<DIM, K>;
@@ -302,18 +294,33 @@ __global__ void __launch_bounds__(256) cg_elem_kernel(const CgArgs a) {
   if (gated(a)) return;
   __shared__ double M1s[P * P];
   __shared__ double u[EPB * DIM * ND1], t[EPB * DIM * ND1], y[EPB * DIM * ND1];
-  (void)M1s;
   const Geom& g = a.g;
   for (int i = threadIdx.x; i < P * P; i += blockDim.x) M1s[i] = a.M1[(i / P) * (kMaxOrder + 1) + i % P];
+  const double beta = a.cg->beta;
   const int64_t el0 = (int64_t)blockIdx.x * EPB;
   const int nel = (int)((g.nelem - el0) < EPB ? (g.nelem - el0) : EPB);
-  mass_elements<DIM, K>(g, M1s, a.p, a.rho0K, a.ApE, el0, nel, u, t, y);
+  const int items = nel * DIM * ND1;
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int i = w % ND1, r = w / ND1, c = r % DIM, le = r / DIM;
+    int E[3] = {0, 0, 0};
+    elem_ijk(g, el0 + le, E);
+    int aa = i % P, b = (i / P) % P, cz = DIM == 3 ? i / (P * P) : 0;
+    const int64_t k = c * g.nnodes + elem_node<K>(g, E, aa, b, cz);
+    u[w] = a.z[k] + beta * a.p[k];
+  }
+  __syncthreads();
+  kron_mass<DIM, K>(M1s, u, t, y, nel);
+  for (int w = threadIdx.x; w < items; w += blockDim.x) {
+    int le = w / (DIM * ND1);
+    a.ApE[el0 * DIM * ND1 + w] = a.rho0K[el0 + le] * y[w];
+  }
 }
 
 template <int DIM, int K>
 __global__ void __launch_bounds__(kNodeThreads) cg_gather_kernel(const CgArgs a) {
   if (gated(a)) return;
   const Geom& g = a.g;
+  const double beta = a.cg->beta;
   double l = 0.0;
   for (int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; node < g.nnodes;
        node += (int64_t)gridDim.x * blockDim.x) {
@@ -322,8 +329,10 @@ __global__ void __launch_bounds__(kNodeThreads) cg_gather_kernel(const CgArgs a)
     for (int c = 0; c < DIM; ++c) {
       const int64_t k = c * g.nnodes + node;
       const double ap = essential(g, I, c) ? 0.0 : gather_node<DIM, K>(g, a.ApE, I, c);
+      const double pv = a.z[k] + beta * a.p[k];  // the p the element phase used
+      a.p[k] = pv;
       a.Ap[k] = ap;
-      l += a.p[k] * ap;
+      l += pv * ap;
     }
   }
   double tot;
@@ -359,11 +368,11 @@ __global__ void __launch_bounds__(kNodeThreads) cg_update_kernel(const CgArgs a,
   }
   if (jacobi) write_partial(l_rz, a.part + 3 * kMaxPartials);
   double rr;
-  if (reduce_last(l_rr, a.part + 4 * kMaxPartials, &a.cg->ticket[kTicketB], &rr) &&
-      threadIdx.x == 0) {
-    CgDev* cg = a.cg;
+  if (reduce_last(l_rr, a.part + 4 * kMaxPartials, &a.cg->ticket[kTicketB], &rr)) {
     // every block wrote its r.z partial before taking its rr ticket
     const double rz_new = jacobi ? sum_partials(a.part + 3 * kMaxPartials) : 0.0;
+    if (threadIdx.x != 0) return;
+    CgDev* cg = a.cg;
     cg->it += 1;
     const bool conv = rr <= a.rtol * a.rtol * cg->bb;
     const bool bad = !(rr == rr);
@@ -376,16 +385,6 @@ __global__ void __launch_bounds__(kNodeThreads) cg_update_kernel(const CgArgs a,
       cg->rz = rz_new;
     }
   }
-}
-
-template <int DIM, int K>
-__global__ void __launch_bounds__(kNodeThreads) cg_pupdate_kernel(const CgArgs a) {
-  if (gated(a)) return;
-  const double beta = a.cg->beta;
-  const int64_t n = (int64_t)DIM * a.g.nnodes;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x)
-    a.p[k] = a.z[k] + beta * a.p[k];
 }
 
 __global__ void cg_reset_kernel(CgDev* cg, const Ctl* gate) {
@@ -433,13 +432,19 @@ static CgArgs make_args(const lh_ctx* c, const double* rhs, double* out, const C
 
 template <int DIM, int K>
 static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, cudaStream_t s) {
+  // out of place: r -> z (d = 0), then alternate between Ap (free here) and z
+  // so that the last direction writes z
+  const double* src = a.r;
+  double* bufs[2] = {a.z, a.Ap};
   for (int d = 0; d < DIM; ++d) {
-    const int64_t tasks = (int64_t)DIM * (c->g.nnodes / c->g.nn[d]);
-    const int blocks = (int)((tasks + kLineThreads - 1) / kLineThreads);
+    const int nd = c->g.nn[d];
+    const int64_t nlines = c->g.nnodes / nd;
+    const int64_t blocks = (int64_t)DIM * ((nlines + 31) / 32) * ((nd + 31) / 32);
     const int mode = d == 0 ? (init ? 0 : 1) : 2;
-    const size_t smem = (size_t)32 * (c->g.nn[d] | 1) * sizeof(float);
-    cg_pass_kernel<DIM, K><<<blocks, kLineThreads, smem, s>>>(a, d, mode, d == DIM - 1,
-                                                              init ? 1 : 0);
+    double* dst = bufs[(DIM - 1 - d) & 1];
+    cg_pass_kernel<DIM, K><<<(unsigned)blocks, kLineThreads, 0, s>>>(a, d, mode, d == DIM - 1,
+                                                                    init ? 1 : 0, src, dst);
+    src = dst;
   }
   return cudaGetLastError();
 }
@@ -464,7 +469,6 @@ static cudaError_t cg_body_dk(const lh_ctx* c, const CgArgs& a, cudaStream_t s) 
   if (c->tpc.enabled) {
     if ((e = precond_passes<DIM, K>(c, a, false, s)) != cudaSuccess) return e;
   }
-  cg_pupdate_kernel<DIM, K><<<node_grid(c), kNodeThreads, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -489,11 +493,7 @@ static cudaError_t cg_body(const lh_ctx* c, const CgArgs& a, cudaStream_t s) {
 
 template <int DIM, int K>
 static cudaError_t cg_prepare_dk(const lh_ctx* c) {
-  int most = 0;
-  for (int d = 0; d < DIM; ++d) most = c->g.nn[d] > most ? c->g.nn[d] : most;
-  const int bytes = 32 * (most | 1) * (int)sizeof(float);
-  return cudaFuncSetAttribute(cg_pass_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              bytes);
+  return c->tpc.B[0] == PB<K>::B ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Shared memory of the line passes, set before any stream capture.

@@ -77,7 +77,7 @@ struct Ctl {
 };
 
 // Scalars of one CG solve (device memory).
-constexpr int kMaxPartials = 4096;
+constexpr int kMaxPartials = 16384;
 struct CgDev {
   double bb, rz, alpha, beta;
   int it, done;
@@ -90,13 +90,15 @@ struct Barrier {
   unsigned int gen;
 };
 
-// Tensor-product preconditioner: banded Cholesky factors of the assembled 1D
-// reference mass matrices along each direction, full (variant 0) and without
-// the two end nodes (variant 1, the wall-normal component), L[i][m] = L_{i,i-m}.
+// Tensor-product preconditioner: the inverses of the assembled 1D reference
+// mass matrices along each direction, full (variant 0) and without the two end
+// nodes (variant 1, the wall-normal component), truncated to the band
+// |i - j| <= B[d] and stored in FP32 as rows [i][j - i + B].
 struct TensorPC {
-  int64_t off[3][2];   // offsets into Arrays::lfac (units of double)
+  int64_t off[3][2];   // offsets into Arrays::lfac (units of float)
+  int B[3];            // band half-width per direction
+  int Bmax;
   double scale;        // 1 / (rho0 |J0|), the same for every element
-  // (factors in FP32: L[i][0] holds 1 / L_ii)
   int enabled;
 };
 
@@ -119,7 +121,7 @@ struct Arrays {
   double *tmpE;                 // N_E scratch
   double *tmpV;                 // N_V scratch
   double *aux;                  // 16 doubles of API scratch (estimates, flags, energy)
-  float *lfac;                  // tensor preconditioner factors (FP32)
+  float *lfac;                  // tensor preconditioner bands (FP32)
   CgDev* cg;
   Barrier* bar;
   Ctl* ctl;
