@@ -214,6 +214,12 @@ LH_API lh_status lh_mass_apply_v(lh_ctx* ctx, const double* in, double* out);
  * LH_ECG if cg_maxit is reached. */
 LH_API lh_status lh_mass_solve_v(lh_ctx* ctx, const double* rhs, double* out,
                           int32_t* iters, double* relres);
+/* out = P^{-1} in (device pointers, N_V): one application of the velocity CG's
+ * tensor-product preconditioner, the banded inverses of the 1D mass matrices
+ * along every direction (an FP32 approximation of M_V^{-1} on the
+ * non-essential components; essential entries of out are zero).
+ * LH_EUNSUPPORTED if the context uses the Jacobi preconditioner. */
+LH_API lh_status lh_precond_apply(lh_ctx* ctx, const double* in, double* out);
 /* out = M_E^{-1} rhs (device pointers, N_E), block diagonal per element. */
 LH_API lh_status lh_mass_solve_e(lh_ctx* ctx, const double* rhs, double* out);
 /* Total energy 1/2 v.M_V.v + 1.M_E.e of the context state (host double). */

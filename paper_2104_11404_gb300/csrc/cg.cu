@@ -499,6 +499,23 @@ static cudaError_t cg_prepare_dk(const lh_ctx* c) {
 // Shared memory of the line passes, set before any stream capture.
 cudaError_t cg_prepare(const lh_ctx* c) { LAGH_DISPATCH_CG(cg_prepare_dk, c); }
 
+// One application of the tensor preconditioner on a caller vector: the loop
+// passes of the solve (mode 1 reads `in` through CgArgs::r, out through z).
+template <int DIM, int K>
+static cudaError_t precond_apply_dk(const lh_ctx* c, const double* in, double* out,
+                                    cudaStream_t s) {
+  CgArgs a = make_args(c, nullptr, nullptr, nullptr);
+  a.r = const_cast<double*>(in);
+  a.z = out;
+  cudaError_t e = cudaMemsetAsync(&c->a.cg->done, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  return precond_passes<DIM, K>(c, a, false, s);
+}
+
+cudaError_t precond_apply(const lh_ctx* c, const double* in, double* out, cudaStream_t s) {
+  LAGH_DISPATCH_CG(precond_apply_dk, c, in, out, s);
+}
+
 // Eager solve (API): the body is launched in batches and the host polls the
 // done flag between batches.
 cudaError_t cg_solve_eager(const lh_ctx* c, const double* rhs, double* out, cudaStream_t s,

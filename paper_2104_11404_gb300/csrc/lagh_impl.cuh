@@ -211,6 +211,7 @@ cudaError_t launch_mass_apply(const lh_ctx* c, const double* in, double* out, cu
 // count, relative residual and failures are written to c->a.ctl.
 cudaError_t cg_solve_eager(const lh_ctx* c, const double* rhs, double* out, cudaStream_t s,
                            int* done_host);
+cudaError_t precond_apply(const lh_ctx* c, const double* in, double* out, cudaStream_t s);
 cudaError_t cg_solve_capture(const lh_ctx* c, const double* rhs, double* out, const Ctl* gate,
                              cudaStream_t s, cudaStream_t side);
 cudaError_t launch_mass_solve_e(const lh_ctx* c, const double* rhs, double* out, cudaStream_t s);

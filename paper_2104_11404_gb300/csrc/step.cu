@@ -552,6 +552,12 @@ extern "C" lh_status lh_mass_solve_v(lh_ctx* c, const double* rhs, double* out, 
   return LH_OK;
 }
 
+extern "C" lh_status lh_precond_apply(lh_ctx* c, const double* in, double* out) {
+  if (!c || !in || !out) return LH_EINVAL;
+  if (!c->tpc.enabled) return set_error(c, LH_EUNSUPPORTED, "context uses the Jacobi preconditioner");
+  return cuda_check(c, precond_apply(c, in, out, c->stream), "precond apply");
+}
+
 extern "C" lh_status lh_mass_solve_e(lh_ctx* c, const double* rhs, double* out) {
   if (!c || !rhs || !out) return LH_EINVAL;
   return cuda_check(c, launch_mass_solve_e(c, rhs, out, c->stream), "mass solve e");

@@ -24,6 +24,7 @@ API_NAMES = [
     "lh_layout", "lh_init_state", "lh_set_state", "lh_get_state", "lh_force",
     "lh_force_sampled", "lh_mass_apply_v", "lh_mass_solve_v", "lh_mass_solve_e",
     "lh_total_energy", "lh_step_fixed", "lh_step", "lh_run_to", "lh_force_static",
+    "lh_precond_apply",
 ]
 
 
@@ -99,6 +100,7 @@ def load():
     L.lh_mass_solve_v.argtypes = [_vp, _dp, _dp, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double)]
     L.lh_mass_solve_e.argtypes = [_vp, _dp, _dp]
+    L.lh_precond_apply.argtypes = [_vp, _dp, _dp]
     L.lh_total_energy.argtypes = [_vp, ctypes.POINTER(ctypes.c_double)]
     L.lh_step_fixed.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     L.lh_step.argtypes = [_vp, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
@@ -210,6 +212,10 @@ def lh_mass_solve_v(ctx, rhs, out):
     _check(ctx, load().lh_mass_solve_v(ctx, _ptr(rhs), _ptr(out), ctypes.byref(it),
                                        ctypes.byref(rr)))
     return it.value, rr.value
+
+
+def lh_precond_apply(ctx, a, out):
+    _check(ctx, load().lh_precond_apply(ctx, _ptr(a), _ptr(out)))
 
 
 def lh_mass_solve_e(ctx, rhs, out):

@@ -93,6 +93,22 @@ def test_cg_preconditioners_agree(dim, k, n):
     assert it_t <= 3 < it_j
 
 
+@pytest.mark.parametrize("dim,k,n", SMALL)
+def test_precond_apply_approximates_mass_inverse(dim, k, n):
+    cfg = _cfg(dim, k, n)
+    o = oracle_for(cfg)
+    g = gpu_for(cfg)
+    b = np.random.default_rng(11 + dim + k).normal(size=o.nv)
+    xo, _, _, _ = o.mass_solve_v(b)
+    out = g.zeros_v()
+    from paper_2104_11404_gb300 import lagh
+    lagh.lh_precond_apply(g.ctx, dev(b), out)
+    z = host(out)
+    assert np.all(z[W.essential_mask(cfg)] == 0.0)
+    # FP32 banded inverse: close to M_V^{-1} b, not equal
+    assert 1e-12 < rel_l2(xo, z) <= 1e-6
+
+
 def _per_step(cfg, nsteps, precision="fp64", tol=1e-12):
     """Each step from the same state: the oracle advances its own trajectory
     under step control; the GPU is set to the oracle's state, takes the same
