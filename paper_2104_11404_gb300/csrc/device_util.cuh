@@ -121,14 +121,14 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 // Block minimum of the ordered bits, then one atomicMin per block (min is
 // exact and order-independent, so the result is deterministic).  Works for
 // any block size (a shared-memory tree, no partial-warp shuffles).
-// sh: >= 256 entries; blockDim.x <= 256.
+// sh: >= blockDim.x entries; blockDim.x <= 1024.
 __device__ __forceinline__ void block_min_to(unsigned long long v, unsigned long long* sh,
                                              unsigned long long* dst) {
   const int tid = threadIdx.x, n = blockDim.x;
   __syncthreads();
   sh[tid] = v;
   __syncthreads();
-  for (int s = 128; s > 0; s >>= 1) {
+  for (int s = 512; s > 0; s >>= 1) {
     if (tid < s && tid + s < n) {
       unsigned long long w = sh[tid + s];
       if (w < sh[tid]) sh[tid] = w;

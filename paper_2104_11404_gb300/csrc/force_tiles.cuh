@@ -1,0 +1,779 @@
+// Tile-level device functions of the force and energy kernels (shared by the
+// grid kernels of force.cu and the batched stage kernel of batch.cu).
+#pragma once
+
+#include <type_traits>
+
+#include "device_util.cuh"
+#include "qpoint.cuh"
+
+namespace lagh {
+
+
+template <int DIM, int K, bool MIXED, int NTT = 256>
+struct FL {
+  using T = typename std::conditional<MIXED, float, double>::type;
+  static constexpr int P = K + 1, NQ = 2 * K;
+  static constexpr int ND1 = ipow(P, DIM), ND2 = ipow(K, DIM), NQD = ipow(NQ, DIM);
+  static constexpr int EPB = (NTT / NQD) > 0 ? NTT / NQD : 1;
+  static constexpr int NT = EPB * NQD;
+  static constexpr int PK = P * K;
+  // interpolated nodal fields: x, v and (FP64 path) the test vector
+  static constexpr int NF = MIXED ? 2 * DIM : 3 * DIM;
+  static constexpr int S_INTERP =
+      DIM == 2 ? 2 * NF * P * NQ : 2 * NF * P * P * NQ + 3 * NF * P * NQ * NQ;
+  static constexpr int S_F1 =
+      DIM == 2 ? DIM * DIM * P * NQ : DIM * DIM * P * NQ * NQ + DIM * DIM * P * P * NQ;
+  static constexpr int S_FK =
+      !MIXED ? 0 : (DIM == 2 ? DIM * DIM * PK * NQ : DIM * DIM * PK * NQ * NQ + DIM * DIM * PK * PK * NQ);
+  static constexpr int SCR = S_INTERP > S_F1 ? (S_INTERP > S_FK ? S_INTERP : S_FK)
+                                             : (S_F1 > S_FK ? S_F1 : S_FK);
+  static constexpr int S_L2 = DIM == 2 ? 2 * K * NQ : 2 * (K * NQ * NQ + K * K * NQ);
+  static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
+  // per-element byte sizes
+  static constexpr size_t B_XS = al(DIM * ND1 * sizeof(T));
+  static constexpr size_t B_VS = B_XS;
+  static constexpr size_t B_WS = al(DIM * ND1 * sizeof(double));
+  static constexpr size_t B_ES = al(ND2 * sizeof(T));
+  static constexpr size_t B_DQ = al(DIM * DIM * NQD * sizeof(T));
+  static constexpr size_t B_GQ = al(2 * NQD * sizeof(double));  // FTv and source integrands
+  static constexpr size_t B_FK = MIXED ? al(DIM * ND1 * ND2 * sizeof(float)) : 0;
+  static constexpr size_t B_SCR = al(SCR * sizeof(T));
+  static constexpr size_t B_L2 = al(S_L2 * sizeof(double));
+  static constexpr size_t B_ELEM = B_XS + B_VS + B_WS + B_ES + B_DQ + B_GQ + B_FK + B_SCR + B_L2;
+  static constexpr size_t B_TAB = al(NQ * P * sizeof(T)) * 2 + al(NQ * K * sizeof(T)) +
+                                  al(NQ * K * sizeof(double)) + al(NQ * sizeof(double));
+  static constexpr size_t BYTES = B_TAB + EPB * B_ELEM + NTT * sizeof(unsigned long long);
+};
+
+struct ForceKParams {
+  Geom g;
+  Phys ph;
+  Basis1D b;
+  ForceArgs a;
+  const double* rho0K;
+};
+
+template <typename T>
+__device__ __forceinline__ T tab(const double& d, const float& f);
+template <>
+__device__ __forceinline__ double tab<double>(const double& d, const float&) { return d; }
+template <>
+__device__ __forceinline__ float tab<float>(const double&, const float& f) { return f; }
+
+// 2D Taylor-Green manufactured source e_src = v.grad(e) of the steady exact
+// solution: (pi / (4 (gamma-1))) (cos 3pi x cos pi y - cos pi x cos 3pi y).
+__device__ __forceinline__ double tg_source(double X, double Y, double gam) {
+  const double pi = 3.141592653589793238462643383279502884;
+  return 0.25 * pi / (gam - 1.0) *
+         (cos(3.0 * pi * X) * cos(pi * Y) - cos(pi * X) * cos(3.0 * pi * Y));
+}
+
+// One tile of EPB element slots [slot0, slot0 + EPB) of the force evaluation,
+// by all NTT threads of the block (the grid kernel below uses one tile per
+// block; the batched stage kernel loops over the tiles of an instance).
+template <int DIM, int K, bool MIXED, int NTT>
+__device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const Basis1D& bas,
+                                           const ForceArgs& A, const double* rho0Kp,
+                                           unsigned char* smem, int64_t slot0) {
+  using F = FL<DIM, K, MIXED, NTT>;
+  using T = typename F::T;
+  constexpr int P = F::P, NQ = F::NQ, ND1 = F::ND1, ND2 = F::ND2, NQD = F::NQD;
+  constexpr int NF = F::NF;
+  struct Prm { const Phys& ph; const Basis1D& b; const double* rho0K; } prm{ph, bas, rho0Kp};
+  unsigned char* sp = smem;
+  T* Bs = reinterpret_cast<T*>(sp); sp += F::al(NQ * P * sizeof(T));
+  T* Gs = reinterpret_cast<T*>(sp); sp += F::al(NQ * P * sizeof(T));
+  T* Ls = reinterpret_cast<T*>(sp); sp += F::al(NQ * K * sizeof(T));
+  double* Ld = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * sizeof(double));
+  double* Wd = reinterpret_cast<double*>(sp); sp += F::al(NQ * sizeof(double));
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + F::B_TAB + F::EPB * F::B_ELEM);
+
+  const int tid = threadIdx.x;
+  const int le = tid / NQD;       // element of this thread's team
+  const int tq = tid - le * NQD;  // quadrature point / team rank
+  unsigned char* ep = sp + le * F::B_ELEM;
+  T* xs = reinterpret_cast<T*>(ep); ep += F::B_XS;
+  T* vs = reinterpret_cast<T*>(ep); ep += F::B_VS;
+  double* ws = reinterpret_cast<double*>(ep); ep += F::B_WS;
+  T* es = reinterpret_cast<T*>(ep); ep += F::B_ES;
+  T* dq = reinterpret_cast<T*>(ep); ep += F::B_DQ;
+  double* gq = reinterpret_cast<double*>(ep); ep += F::B_GQ;  // [2][NQD]
+  float* fk = reinterpret_cast<float*>(ep); ep += F::B_FK;
+  T* scr = reinterpret_cast<T*>(ep); ep += F::B_SCR;
+  double* l2s = reinterpret_cast<double*>(ep);
+
+  for (int i = tid; i < NQ * P; i += blockDim.x) {
+    int q = i / P, a = i - q * P;
+    Bs[i] = tab<T>(prm.b.B[q][a], prm.b.Bf[q][a]);
+    Gs[i] = tab<T>(prm.b.G[q][a], prm.b.Gf[q][a]);
+  }
+  for (int i = tid; i < NQ * K; i += blockDim.x) {
+    int q = i / K, j = i - q * K;
+    Ls[i] = tab<T>(prm.b.L[q][j], prm.b.Lf[q][j]);
+    Ld[i] = prm.b.L[q][j];
+  }
+  for (int i = tid; i < NQ; i += blockDim.x) Wd[i] = prm.b.W[i];
+
+  const int64_t slot = slot0 + le;
+  const bool active = le < F::EPB && slot < A.nslots;
+  const int64_t el = active ? (A.list ? (int64_t)A.list[slot] : slot) : 0;
+  int E[3] = {0, 0, 0};
+  elem_ijk(g, el, E);
+  const bool with_w = A.vtest != nullptr;
+
+  // ---- stage element data ----
+  double x0[DIM];  // element origin (mixed path subtracts it before rounding)
+  {
+    int64_t n0 = elem_node<K>(g, E, 0, 0, 0);
+    for (int c = 0; c < DIM; ++c) x0[c] = MIXED ? A.x[c * g.nnodes + n0] : 0.0;
+  }
+  if (active) {
+    for (int w = tq; w < DIM * ND1; w += NQD) {
+      int c = w / ND1, i = w - c * ND1;
+      int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+      int64_t node = elem_node<K>(g, E, a, b, cc);
+      xs[w] = (T)(A.x[c * g.nnodes + node] - x0[c]);
+      vs[w] = (T)A.v[c * g.nnodes + node];
+      if (with_w) ws[w] = A.vtest[c * g.nnodes + node];
+    }
+    for (int j = tq; j < ND2; j += NQD) es[j] = (T)A.e[el * ND2 + j];
+  }
+  __syncthreads();
+
+  // ---- reference gradients at the quadrature points (sum factorisation) ----
+  // fields f: [0, DIM) x, [DIM, 2 DIM) v, [2 DIM, 3 DIM) test vector (FP64 path)
+  const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
+  T grad[NF][DIM];
+  T xval[DIM];
+  auto field = [&](int f, int i) -> T {
+    if (f < DIM) return xs[f * ND1 + i];
+    if (f < 2 * DIM) return vs[(f - DIM) * ND1 + i];
+    return (T)ws[(f - 2 * DIM) * ND1 + i];
+  };
+  const int nf = (MIXED || !with_w) ? 2 * DIM : 3 * DIM;
+  if constexpr (DIM == 2) {
+    T* TB = scr;
+    T* TG = scr + NF * P * NQ;
+    if (active)
+      for (int w = tq; w < nf * P * NQ; w += NQD) {
+        int x_ = w % NQ, b = (w / NQ) % P, f = w / (NQ * P);
+        T sb = T(0), sg = T(0);
+        for (int a = 0; a < P; ++a) {
+          T u = field(f, b * P + a);
+          sb += Bs[x_ * P + a] * u;
+          sg += Gs[x_ * P + a] * u;
+        }
+        TB[(f * P + b) * NQ + x_] = sb;
+        TG[(f * P + b) * NQ + x_] = sg;
+      }
+    __syncthreads();
+    if (active)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (f >= nf) break;
+        T d0 = T(0), d1 = T(0), vv = T(0);
+        for (int b = 0; b < P; ++b) {
+          T tb = TB[(f * P + b) * NQ + qx], tg = TG[(f * P + b) * NQ + qx];
+          d0 += Bs[qy * P + b] * tg;
+          d1 += Gs[qy * P + b] * tb;
+          vv += Bs[qy * P + b] * tb;
+        }
+        grad[f][0] = d0;
+        grad[f][1] = d1;
+        if (f < DIM) xval[f] = vv;
+      }
+  } else {
+    T* TB = scr;
+    T* TG = TB + NF * P * P * NQ;
+    T* PBB = TG + NF * P * P * NQ;
+    T* PGB = PBB + NF * P * NQ * NQ;
+    T* PBG = PGB + NF * P * NQ * NQ;
+    if (active)
+      for (int w = tq; w < nf * P * P * NQ; w += NQD) {
+        int x_ = w % NQ, r = w / NQ;  // r = (f * P + cz) * P + b
+        int b = r % P, fz = r / P;    // fz = f * P + cz
+        T sb = T(0), sg = T(0);
+        int f = fz / P, cz = fz - f * P;
+        for (int a = 0; a < P; ++a) {
+          T u = field(f, (cz * P + b) * P + a);
+          sb += Bs[x_ * P + a] * u;
+          sg += Gs[x_ * P + a] * u;
+        }
+        TB[r * NQ + x_] = sb;
+        TG[r * NQ + x_] = sg;
+      }
+    __syncthreads();
+    if (active)
+      for (int w = tq; w < nf * P * NQ * NQ; w += NQD) {
+        int x_ = w % NQ, y_ = (w / NQ) % NQ, fz = w / (NQ * NQ);
+        T bb = T(0), gb = T(0), bg = T(0);
+        for (int b = 0; b < P; ++b) {
+          T tb = TB[(fz * P + b) * NQ + x_], tg = TG[(fz * P + b) * NQ + x_];
+          bb += Bs[y_ * P + b] * tb;
+          gb += Bs[y_ * P + b] * tg;
+          bg += Gs[y_ * P + b] * tb;
+        }
+        PBB[w] = bb;
+        PGB[w] = gb;
+        PBG[w] = bg;
+      }
+    __syncthreads();
+    if (active)
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        if (f >= nf) break;
+        T d0 = T(0), d1 = T(0), d2 = T(0), vv = T(0);
+        for (int cz = 0; cz < P; ++cz) {
+          int idx = ((f * P + cz) * NQ + qy) * NQ + qx;
+          d0 += Bs[qz * P + cz] * PGB[idx];
+          d1 += Bs[qz * P + cz] * PBG[idx];
+          d2 += Gs[qz * P + cz] * PBB[idx];
+          vv += Bs[qz * P + cz] * PBB[idx];
+        }
+        grad[f][0] = d0;
+        grad[f][1] = d1;
+        grad[f][2] = d2;
+        if (f < DIM) xval[f] = vv;
+      }
+  }
+  __syncthreads();  // scratch is reused below
+
+  // ---- quadrature-point physics ----
+  double tau_q = t_inf<double>();
+  int flags = 0;
+  if (active) {
+    T e_q = T(0);
+    for (int j = 0; j < ND2; ++j) {
+      int jx = j % K, jy = (j / K) % K, jz = DIM == 3 ? j / (K * K) : 0;
+      T phi = Ls[qx * K + jx] * Ls[qy * K + jy];
+      if (DIM == 3) phi *= Ls[qz * K + jz];
+      e_q += es[j] * phi;
+    }
+    T J[DIM][DIM], Gv[DIM][DIM], J0i[DIM], sigma[DIM][DIM], tau;
+    for (int c = 0; c < DIM; ++c) {
+      J0i[c] = (T)g.J0inv[c];
+      for (int m = 0; m < DIM; ++m) {
+        J[c][m] = grad[c][m];
+        Gv[c][m] = grad[DIM + c][m];
+      }
+    }
+    const T rho0K = (T)prm.rho0K[el];
+    if (A.mode == kForceFull) {
+      const T pref = (MIXED && A.p_ref != nullptr) ? (T)(*A.p_ref) : T(0);
+      flags = qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, (T)g.ell0,
+                                     (T)(1.0 / K), pref, sigma, tau);
+      tau_q = (double)tau;
+    } else {
+      // reference pressure only: sigma = -p_ref I
+      const T pref = (T)(*A.p_ref);
+      for (int c = 0; c < DIM; ++c)
+        for (int n = 0; n < DIM; ++n) sigma[c][n] = (c == n) ? -pref : T(0);
+    }
+    double alpha = Wd[qx] * Wd[qy] * (DIM == 3 ? Wd[qz] : 1.0);
+    T Aj[DIM][DIM];
+    adj_of<T, DIM>(J, Aj);
+    for (int c = 0; c < DIM; ++c)
+      for (int m = 0; m < DIM; ++m) {
+        T acc = T(0);
+        for (int n = 0; n < DIM; ++n) acc += sigma[c][n] * Aj[m][n];
+        dq[(c * DIM + m) * NQD + tq] = (T)alpha * acc;
+      }
+    if (!MIXED && A.D != nullptr)
+      for (int cm = 0; cm < DIM * DIM; ++cm)
+        A.D[(el * DIM * DIM + cm) * NQD + tq] = (double)dq[cm * NQD + tq];
+    if (!MIXED && with_w) {
+      double gsum = 0.0;
+      for (int c = 0; c < DIM; ++c)
+        for (int m = 0; m < DIM; ++m)
+          gsum += (double)dq[(c * DIM + m) * NQD + tq] * (double)grad[2 * DIM + c][m];
+      gq[tq] = gsum;
+    }
+    if (A.srcE != nullptr && DIM == 2) {
+      double X = x0[0] + (double)xval[0], Y = x0[1] + (double)xval[1];
+      gq[NQD + tq] = alpha * prm.rho0K[el] * tg_source(X, Y, prm.ph.gamma);
+    }
+  }
+  // time-step estimate and error flags of the block
+  if (A.tau_bits != nullptr) {
+    unsigned long long* rsh = red;
+    block_min_to(tau_to_bits(tau_q), rsh, A.tau_bits);
+  }
+  if (flags && A.status != nullptr) atomicOr(A.status, flags);
+  __syncthreads();
+
+  // ---- transposed contractions ----
+  if constexpr (!MIXED) {
+    if (A.F1E == nullptr) goto l2_part;
+    {
+    // F.1 rows: F1[c][i] = sum_q sum_m D[c][m](q) d_m w_i(q)
+    if constexpr (DIM == 2) {
+      T* Y = scr;
+      if (active)
+        for (int w = tq; w < DIM * DIM * P * NQ; w += NQD) {
+          int x_ = w % NQ, b = (w / NQ) % P, cm = w / (NQ * P), m = cm % DIM;
+          const T* X = (m == 1) ? Gs : Bs;
+          T s = T(0);
+          for (int y_ = 0; y_ < NQ; ++y_) s += X[y_ * P + b] * dq[cm * NQD + y_ * NQ + x_];
+          Y[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < DIM * ND1; w += NQD) {
+          int c = w / ND1, i = w - c * ND1, a = i % P, b = i / P;
+          T s = T(0);
+          for (int m = 0; m < DIM; ++m) {
+            const T* X = (m == 0) ? Gs : Bs;
+            for (int x_ = 0; x_ < NQ; ++x_) s += X[x_ * P + a] * Y[(((c * DIM + m) * P + b) * NQ) + x_];
+          }
+          double* o = &A.F1E[(slot * DIM + c) * ND1 + i];
+          *o = A.accumulate ? *o + (double)s : (double)s;
+        }
+    } else {
+      T* Y = scr;
+      T* Z = scr + DIM * DIM * P * NQ * NQ;
+      if (active)
+        for (int w = tq; w < DIM * DIM * P * NQ * NQ; w += NQD) {
+          int x_ = w % NQ, y_ = (w / NQ) % NQ, cz = (w / (NQ * NQ)) % P, cm = w / (NQ * NQ * P);
+          int m = cm % DIM;
+          const T* X = (m == 2) ? Gs : Bs;
+          T s = T(0);
+          for (int z_ = 0; z_ < NQ; ++z_)
+            s += X[z_ * P + cz] * dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
+          Y[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < DIM * DIM * P * P * NQ; w += NQD) {
+          int x_ = w % NQ, b = (w / NQ) % P, cz = (w / (NQ * P)) % P, cm = w / (NQ * P * P);
+          int m = cm % DIM;
+          const T* X = (m == 1) ? Gs : Bs;
+          T s = T(0);
+          for (int y_ = 0; y_ < NQ; ++y_)
+            s += X[y_ * P + b] * Y[((cm * P + cz) * NQ + y_) * NQ + x_];
+          Z[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < DIM * ND1; w += NQD) {
+          int c = w / ND1, i = w - c * ND1, a = i % P, b = (i / P) % P, cz = i / (P * P);
+          T s = T(0);
+          for (int m = 0; m < DIM; ++m) {
+            const T* X = (m == 0) ? Gs : Bs;
+            for (int x_ = 0; x_ < NQ; ++x_)
+              s += X[x_ * P + a] * Z[((((c * DIM + m) * P + cz) * P + b) * NQ) + x_];
+          }
+          double* o = &A.F1E[(slot * DIM + c) * ND1 + i];
+          *o = A.accumulate ? *o + (double)s : (double)s;
+        }
+    }
+    }
+  } else {
+    // Mixed: F_K[(c,i), j] = sum_q phi_j(q) sum_m D[c][m](q) d_m w_i(q) in FP32
+    constexpr int PK = F::PK;
+    if constexpr (DIM == 2) {
+      T* Y = scr;
+      if (active)
+        for (int w = tq; w < DIM * DIM * PK * NQ; w += NQD) {
+          int x_ = w % NQ, u = (w / NQ) % PK, cm = w / (NQ * PK), m = cm % DIM;
+          int b = u / K, jy = u - b * K;
+          const T* X = (m == 1) ? Gs : Bs;
+          T s = T(0);
+          for (int y_ = 0; y_ < NQ; ++y_)
+            s += X[y_ * P + b] * Ls[y_ * K + jy] * dq[cm * NQD + y_ * NQ + x_];
+          Y[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < DIM * ND1 * ND2; w += NQD) {
+          int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
+          int a = i % P, b = i / P, jx = j % K, jy = j / K;
+          T s = T(0);
+          for (int m = 0; m < DIM; ++m) {
+            const T* X = (m == 0) ? Gs : Bs;
+            for (int x_ = 0; x_ < NQ; ++x_)
+              s += X[x_ * P + a] * Ls[x_ * K + jx] * Y[(((c * DIM + m) * PK + b * K + jy) * NQ) + x_];
+          }
+          fk[w] = s;
+        }
+    } else {
+      T* Y = scr;
+      T* Z = scr + DIM * DIM * PK * NQ * NQ;
+      if (active)
+        for (int w = tq; w < DIM * DIM * PK * NQ * NQ; w += NQD) {
+          int x_ = w % NQ, y_ = (w / NQ) % NQ, u = (w / (NQ * NQ)) % PK, cm = w / (NQ * NQ * PK);
+          int m = cm % DIM, cz = u / K, jz = u - cz * K;
+          const T* X = (m == 2) ? Gs : Bs;
+          T s = T(0);
+          for (int z_ = 0; z_ < NQ; ++z_)
+            s += X[z_ * P + cz] * Ls[z_ * K + jz] * dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
+          Y[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < DIM * DIM * PK * PK * NQ; w += NQD) {
+          int x_ = w % NQ, uy = (w / NQ) % PK, uz = (w / (NQ * PK)) % PK, cm = w / (NQ * PK * PK);
+          int m = cm % DIM, b = uy / K, jy = uy - b * K;
+          const T* X = (m == 1) ? Gs : Bs;
+          T s = T(0);
+          for (int y_ = 0; y_ < NQ; ++y_)
+            s += X[y_ * P + b] * Ls[y_ * K + jy] * Y[((cm * PK + uz) * NQ + y_) * NQ + x_];
+          Z[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < DIM * ND1 * ND2; w += NQD) {
+          int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
+          int a = i % P, b = (i / P) % P, cz = i / (P * P);
+          int jx = j % K, jy = (j / K) % K, jz = j / (K * K);
+          int uy = b * K + jy, uz = cz * K + jz;
+          T s = T(0);
+          for (int m = 0; m < DIM; ++m) {
+            const T* X = (m == 0) ? Gs : Bs;
+            for (int x_ = 0; x_ < NQ; ++x_)
+              s += X[x_ * P + a] * Ls[x_ * K + jx] *
+                   Z[((((c * DIM + m) * PK + uz) * PK + uy) * NQ) + x_];
+          }
+          fk[w] = s;
+        }
+    }
+    __syncthreads();
+    if (active) {
+      if (A.FK != nullptr)
+        for (int w = tq; w < DIM * ND1 * ND2; w += NQD) A.FK[el * (DIM * ND1 * ND2) + w] = fk[w];
+      // F.1 = row sums in FP64
+      for (int w = tq; w < DIM * ND1; w += NQD) {
+        double s = 0.0;
+        for (int j = 0; j < ND2; ++j) s += (double)fk[w * ND2 + j];
+        A.F1E[slot * DIM * ND1 + w] = s;
+      }
+      // F^T w in FP64
+      if (with_w)
+        for (int j = tq; j < ND2; j += NQD) {
+          double s = 0.0;
+          for (int ci = 0; ci < DIM * ND1; ++ci) s += (double)fk[ci * ND2 + j] * ws[ci];
+          A.FTvE[slot * ND2 + j] = s;
+        }
+    }
+  }
+
+  // ---- L2 contractions (FP64): F^T w (FP64 path) and the energy source ----
+l2_part:
+  const bool do_ftv = (!MIXED) && with_w;
+  const bool do_src = (A.srcE != nullptr) && DIM == 2;
+  if (do_ftv || do_src) {
+    __syncthreads();
+    // field 0: F^T w integrand, field 1: source integrand
+    if constexpr (DIM == 2) {
+      double* R1 = l2s;  // [2][K][NQ]
+      if (active)
+        for (int w = tq; w < 2 * K * NQ; w += NQD) {
+          int y_ = w % NQ, jx = (w / NQ) % K, fld = w / (NQ * K);
+          double s = 0.0;
+          for (int x_ = 0; x_ < NQ; ++x_) s += Ld[x_ * K + jx] * gq[fld * NQD + y_ * NQ + x_];
+          R1[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < 2 * ND2; w += NQD) {
+          int fld = w / ND2, j = w - fld * ND2, jx = j % K, jy = j / K;
+          if ((fld == 0 && !do_ftv) || (fld == 1 && !do_src)) continue;
+          double s = 0.0;
+          for (int y_ = 0; y_ < NQ; ++y_) s += Ld[y_ * K + jy] * R1[(fld * K + jx) * NQ + y_];
+          if (fld == 0) A.FTvE[slot * ND2 + j] = A.accumulate ? A.FTvE[slot * ND2 + j] + s : s;
+          else A.srcE[el * ND2 + j] = s;
+        }
+    } else {
+      double* R1 = l2s;                 // [2][K][NQ][NQ]
+      double* R2 = l2s + 2 * K * NQ * NQ;  // [2][K][K][NQ]
+      if (active)
+        for (int w = tq; w < 2 * K * NQ * NQ; w += NQD) {
+          int y_ = w % NQ, z_ = (w / NQ) % NQ, jx = (w / (NQ * NQ)) % K, fld = w / (NQ * NQ * K);
+          double s = 0.0;
+          for (int x_ = 0; x_ < NQ; ++x_)
+            s += Ld[x_ * K + jx] * gq[fld * NQD + (z_ * NQ + y_) * NQ + x_];
+          R1[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < 2 * K * K * NQ; w += NQD) {
+          int z_ = w % NQ, jx = (w / NQ) % K, jy = (w / (NQ * K)) % K, fld = w / (NQ * K * K);
+          double s = 0.0;
+          for (int y_ = 0; y_ < NQ; ++y_)
+            s += Ld[y_ * K + jy] * R1[((fld * K + jx) * NQ + z_) * NQ + y_];
+          R2[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < 2 * ND2; w += NQD) {
+          int fld = w / ND2, j = w - fld * ND2, jx = j % K, jy = (j / K) % K, jz = j / (K * K);
+          if ((fld == 0 && !do_ftv) || (fld == 1 && !do_src)) continue;
+          double s = 0.0;
+          for (int z_ = 0; z_ < NQ; ++z_)
+            s += Ld[z_ * K + jz] * R2[((fld * K + jy) * K + jx) * NQ + z_];
+          if (fld == 0) A.FTvE[slot * ND2 + j] = A.accumulate ? A.FTvE[slot * ND2 + j] + s : s;
+          else A.srcE[el * ND2 + j] = s;
+        }
+    }
+  }
+}
+
+template <int DIM, int K, bool MIXED>
+__global__ void __launch_bounds__(FL<DIM, K, MIXED>::NT)
+force_kernel(const ForceKParams prm) {
+  using F = FL<DIM, K, MIXED>;
+  if (prm.a.ctl != nullptr && prm.a.ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  force_tile<DIM, K, MIXED, F::NT>(prm.g, prm.ph, prm.b, prm.a, prm.rho0K, smem,
+                                   (int64_t)blockIdx.x * F::EPB);
+}
+
+// ------------------------------------------------------------- gather ----
+
+template <int DIM, int K>
+__global__ void gather_kernel(Geom g, const double* __restrict__ E, double* __restrict__ out,
+                              double scale, int apply_bc, const Ctl* ctl) {
+  if (ctl != nullptr && ctl->done) return;
+  int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (node >= g.nnodes) return;
+  int I[3];
+  node_ijk(g, node, I);
+  for (int c = 0; c < DIM; ++c) {
+    double val = (apply_bc && essential(g, I, c)) ? 0.0 : scale * gather_node<DIM, K>(g, E, I, c);
+    out[c * g.nnodes + node] = val;
+  }
+}
+
+// ------------------------------------------------------- energy update ----
+
+// e_out = e_base + coef * M_E^{-1} (F^T w + src) per element.  One team of
+// NQ^DIM threads per element (same mapping as the force kernel).
+template <int DIM, int K, bool MIXED, int NTT = 256>
+struct EL {
+  static constexpr int P = K + 1, NQ = 2 * K;
+  static constexpr int ND1 = ipow(P, DIM), ND2 = ipow(K, DIM), NQD = ipow(NQ, DIM);
+  static constexpr int EPB = (NTT / NQD) > 0 ? NTT / NQD : 1;
+  static constexpr int NT = EPB * NQD;
+  static constexpr int S_INTERP = DIM == 2 ? 2 * DIM * P * NQ
+                                           : 2 * DIM * P * P * NQ + 3 * DIM * P * NQ * NQ;
+  static constexpr int S_L2 = DIM == 2 ? K * NQ : K * NQ * NQ + K * K * NQ;
+  static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
+  static constexpr size_t B_ELEM = al(DIM * ND1 * 8) + al(S_INTERP * 8) + al(NQD * 8) +
+                                   al(S_L2 * 8) + al(ND2 * 8);
+  static constexpr size_t B_TAB = 3 * al(NQ * P * 8) + al(NQ * K * 8) + al(81 * 8);
+  static constexpr size_t BYTES = B_TAB + EPB * B_ELEM;
+};
+
+struct EnergyKParams {
+  Geom g;
+  Basis1D b;
+  EnergyArgs a;
+  const double* rho0K;
+};
+
+// One tile of EPB elements [el0, el0 + EPB) of the energy update.
+template <int DIM, int K, bool MIXED, int NTT>
+__device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, const EnergyArgs& A,
+                                            const double* rho0Kp, unsigned char* smem,
+                                            int64_t el0) {
+  using F = EL<DIM, K, MIXED, NTT>;
+  constexpr int P = F::P, NQ = F::NQ, ND1 = F::ND1, ND2 = F::ND2, NQD = F::NQD;
+  struct Prm { const Basis1D& b; const double* rho0K; } prm{bas, rho0Kp};
+  const double coef = A.frac * (A.ctl != nullptr ? A.ctl->dt_use : A.dt);
+  unsigned char* sp = smem;
+  double* Bs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
+  double* Gs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
+  sp += F::al(NQ * P * 8);
+  double* Ls = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * 8);
+  double* Mi = reinterpret_cast<double*>(sp); sp += F::al(81 * 8);
+  const int tid = threadIdx.x, le = tid / NQD, tq = tid - le * NQD;
+  unsigned char* ep = sp + le * F::B_ELEM;
+  double* ws = reinterpret_cast<double*>(ep); ep += F::al(DIM * ND1 * 8);
+  double* scr = reinterpret_cast<double*>(ep); ep += F::al(F::S_INTERP * 8);
+  double* gq = reinterpret_cast<double*>(ep); ep += F::al(NQD * 8);
+  double* l2s = reinterpret_cast<double*>(ep); ep += F::al(F::S_L2 * 8);
+  double* ftv = reinterpret_cast<double*>(ep);
+
+  for (int i = tid; i < NQ * P; i += blockDim.x) {
+    Bs[i] = prm.b.B[i / P][i % P];
+    Gs[i] = prm.b.G[i / P][i % P];
+  }
+  for (int i = tid; i < NQ * K; i += blockDim.x) Ls[i] = prm.b.L[i / K][i % K];
+  for (int i = tid; i < ND2 * ND2; i += blockDim.x) Mi[i] = prm.b.MEinv[i];
+
+  const int64_t el = el0 + le;
+  const bool active = le < F::EPB && el < g.nelem;
+  int E[3] = {0, 0, 0};
+  elem_ijk(g, active ? el : 0, E);
+  if (active)
+    for (int w = tq; w < DIM * ND1; w += NQD) {
+      int c = w / ND1, i = w - c * ND1;
+      int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+      ws[w] = A.w[c * g.nnodes + elem_node<K>(g, E, a, b, cc)];
+    }
+  __syncthreads();
+
+  if constexpr (MIXED) {
+    // F^T w from the stored FP32 element matrix, FP64 accumulation
+    if (active)
+      for (int j = tq; j < ND2; j += NQD) {
+        const float* fk = A.FK + el * (DIM * ND1 * ND2);
+        double s = 0.0;
+        for (int ci = 0; ci < DIM * ND1; ++ci) s += (double)fk[ci * ND2 + j] * ws[ci];
+        ftv[j] = s;
+      }
+  } else {
+    const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
+    double gw[DIM][DIM];
+    if constexpr (DIM == 2) {
+      double* TB = scr;
+      double* TG = scr + DIM * P * NQ;
+      if (active)
+        for (int w = tq; w < DIM * P * NQ; w += NQD) {
+          int x_ = w % NQ, b = (w / NQ) % P, f = w / (NQ * P);
+          double sb = 0.0, sg = 0.0;
+          for (int a = 0; a < P; ++a) {
+            double u = ws[f * ND1 + b * P + a];
+            sb += Bs[x_ * P + a] * u;
+            sg += Gs[x_ * P + a] * u;
+          }
+          TB[w] = sb;
+          TG[w] = sg;
+        }
+      __syncthreads();
+      if (active)
+        for (int f = 0; f < DIM; ++f) {
+          double d0 = 0.0, d1 = 0.0;
+          for (int b = 0; b < P; ++b) {
+            d0 += Bs[qy * P + b] * TG[(f * P + b) * NQ + qx];
+            d1 += Gs[qy * P + b] * TB[(f * P + b) * NQ + qx];
+          }
+          gw[f][0] = d0;
+          gw[f][1] = d1;
+        }
+    } else {
+      double* TB = scr;
+      double* TG = TB + DIM * P * P * NQ;
+      double* PBB = TG + DIM * P * P * NQ;
+      double* PGB = PBB + DIM * P * NQ * NQ;
+      double* PBG = PGB + DIM * P * NQ * NQ;
+      if (active)
+        for (int w = tq; w < DIM * P * P * NQ; w += NQD) {
+          int x_ = w % NQ, r = w / NQ, b = r % P, fz = r / P;
+          int f = fz / P, cz = fz - f * P;
+          double sb = 0.0, sg = 0.0;
+          for (int a = 0; a < P; ++a) {
+            double u = ws[f * ND1 + (cz * P + b) * P + a];
+            sb += Bs[x_ * P + a] * u;
+            sg += Gs[x_ * P + a] * u;
+          }
+          TB[w] = sb;
+          TG[w] = sg;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < DIM * P * NQ * NQ; w += NQD) {
+          int x_ = w % NQ, y_ = (w / NQ) % NQ, fz = w / (NQ * NQ);
+          double bb = 0.0, gb = 0.0, bg = 0.0;
+          for (int b = 0; b < P; ++b) {
+            double tb = TB[(fz * P + b) * NQ + x_], tg = TG[(fz * P + b) * NQ + x_];
+            bb += Bs[y_ * P + b] * tb;
+            gb += Bs[y_ * P + b] * tg;
+            bg += Gs[y_ * P + b] * tb;
+          }
+          PBB[w] = bb;
+          PGB[w] = gb;
+          PBG[w] = bg;
+        }
+      __syncthreads();
+      if (active)
+        for (int f = 0; f < DIM; ++f) {
+          double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+          for (int cz = 0; cz < P; ++cz) {
+            int idx = ((f * P + cz) * NQ + qy) * NQ + qx;
+            d0 += Bs[qz * P + cz] * PGB[idx];
+            d1 += Bs[qz * P + cz] * PBG[idx];
+            d2 += Gs[qz * P + cz] * PBB[idx];
+          }
+          gw[f][0] = d0;
+          gw[f][1] = d1;
+          gw[f][2] = d2;
+        }
+    }
+    if (active) {
+      const double* D = A.D + el * DIM * DIM * NQD;
+      double s = 0.0;
+      for (int c = 0; c < DIM; ++c)
+        for (int m = 0; m < DIM; ++m) s += D[(c * DIM + m) * NQD + tq] * gw[c][m];
+      gq[tq] = s;
+    }
+    __syncthreads();
+    if constexpr (DIM == 2) {
+      if (active)
+        for (int w = tq; w < K * NQ; w += NQD) {
+          int y_ = w % NQ, jx = w / NQ;
+          double s = 0.0;
+          for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[y_ * NQ + x_];
+          l2s[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int j = tq; j < ND2; j += NQD) {
+          int jx = j % K, jy = j / K;
+          double s = 0.0;
+          for (int y_ = 0; y_ < NQ; ++y_) s += Ls[y_ * K + jy] * l2s[jx * NQ + y_];
+          ftv[j] = s;
+        }
+    } else {
+      double* R1 = l2s;
+      double* R2 = l2s + K * NQ * NQ;
+      if (active)
+        for (int w = tq; w < K * NQ * NQ; w += NQD) {
+          int y_ = w % NQ, z_ = (w / NQ) % NQ, jx = w / (NQ * NQ);
+          double s = 0.0;
+          for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[(z_ * NQ + y_) * NQ + x_];
+          R1[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int w = tq; w < K * K * NQ; w += NQD) {
+          int z_ = w % NQ, jx = (w / NQ) % K, jy = w / (NQ * K);
+          double s = 0.0;
+          for (int y_ = 0; y_ < NQ; ++y_) s += Ls[y_ * K + jy] * R1[(jx * NQ + z_) * NQ + y_];
+          R2[w] = s;
+        }
+      __syncthreads();
+      if (active)
+        for (int j = tq; j < ND2; j += NQD) {
+          int jx = j % K, jy = (j / K) % K, jz = j / (K * K);
+          double s = 0.0;
+          for (int z_ = 0; z_ < NQ; ++z_) s += Ls[z_ * K + jz] * R2[(jy * K + jx) * NQ + z_];
+          ftv[j] = s;
+        }
+    }
+  }
+  __syncthreads();
+  if (active)
+    for (int j = tq; j < ND2; j += NQD) {
+      // M_E,K^{-1} = Mref^{-1} / (rho0 |J0|)_K, applied to F^T w + src
+      double s = 0.0;
+      for (int l = 0; l < ND2; ++l) {
+        double rhs = ftv[l] + (A.srcE ? A.srcE[el * ND2 + l] : 0.0) +
+                     (A.prefE ? A.prefE[el * ND2 + l] : 0.0);
+        s += Mi[j * ND2 + l] * rhs;
+      }
+      A.e_out[el * ND2 + j] = A.e_base[el * ND2 + j] + coef * s / prm.rho0K[el];
+    }
+}
+
+template <int DIM, int K, bool MIXED>
+__global__ void __launch_bounds__(EL<DIM, K, MIXED>::NT)
+energy_update_kernel(const EnergyKParams prm) {
+  using F = EL<DIM, K, MIXED>;
+  if (prm.a.ctl != nullptr && prm.a.ctl->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  energy_tile<DIM, K, MIXED, F::NT>(prm.g, prm.b, prm.a, prm.rho0K, smem,
+                                    (int64_t)blockIdx.x * F::EPB);
+}
+
+}  // namespace lagh
