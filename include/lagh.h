@@ -150,6 +150,30 @@ typedef struct lh_run_stats {
   double wall_ms;        /* time-loop wall clock (CUDA events on the stream) */
 } lh_run_stats;
 
+/* Aggregate statistics of a batched run (sums over instances). */
+typedef struct lh_batch_stats {
+  int64_t steps;           /* accepted steps */
+  int64_t rejects;         /* repeated attempts */
+  int64_t cg_iters;        /* CG iterations */
+  int64_t attempts;        /* step attempts of unfinished instances */
+  int64_t instances_done;  /* instances that reached t_final (or max_steps) */
+  int64_t dof_updates;     /* sum of (2 N_V + N_E) x accepted steps */
+  int64_t graph_launches;  /* attempt graphs launched */
+  double wall_ms;          /* time-loop wall clock (CUDA events on the stream) */
+} lh_batch_stats;
+
+/* Launch shape of the batched kernels.  threads: 256, 512 or 1024 (2D only)
+ * threads per CTA; with one thread per quadrature point, the force and energy
+ * tiles hold threads / nq^dim elements and the mass tiles threads /
+ * (dim (k+1)^dim).  ctas_per_sm: 0 = as many as fit.  smem_lines: 1 = the
+ * node lines of the velocity solve are staged in shared memory (needs
+ * 8 x nodes of the largest instance), 0 = solved in place in device memory. */
+typedef struct lh_batch_tuning {
+  int32_t threads;
+  int32_t ctas_per_sm;
+  int32_t smem_lines;
+} lh_batch_tuning;
+
 typedef struct lh_ctx lh_ctx;
 typedef struct lh_batch lh_batch;
 
@@ -269,6 +293,97 @@ LH_API lh_status lh_run_to(lh_ctx* ctx, double t_final, int64_t max_steps,
 LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* disc,
                                  const lh_phys_desc* phys, const double* v, const double* e,
                                  const double* x, double* F1, double* dt_est, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched form: n independent instances of the time step, each on its own
+ * Cartesian box mesh with its own physics (a parameter sweep such as the
+ * snapshot runs of the offline stage, Section 4 and Section 6).  Every
+ * instance follows exactly the step of a context with the same descriptors:
+ * RK2-average (eq:RK2-avg), the step control of Section 2.2.3 with its own
+ * dt, the velocity solve by CG on the partially assembled M_V.  The library
+ * runs one persistent kernel per RK stage over all instances (one CTA per
+ * instance at a time, largest instances first), the two stage kernels of an
+ * attempt captured as one CUDA graph.
+ *
+ * Layout: every state array is the concatenation of the instances' arrays in
+ * instance order (offsets from lh_batch_layout); within an instance the
+ * layout of lh_layout.  Differences from a context: the mixed path keeps the
+ * whole stress in FP32 (no reference-pressure split, exact for problems with
+ * zero background pressure such as the point blast); the velocity CG is
+ * preconditioned by the exact inverse of M_V (banded Cholesky solves along
+ * node lines, FP64), so it stops after one iteration.
+ * ------------------------------------------------------------------------ */
+
+/* Creates a batch.  meshes[n] and phys[n]: one descriptor per instance (all
+ * of the same dimension); disc: shared order and quadrature.  cg_rtol and
+ * cg_maxit are taken from phys[0].  precision: lh_precision for every
+ * instance.  stream: cudaStream_t as void* (NULL: the library creates a work
+ * stream).  tuning: NULL (or threads == 0) for the default launch shape, to be
+ * replaced by lh_batch_autotune; otherwise a fixed shape.  Allocates every
+ * array, including per-CTA scratch sized by the largest instance.  Errors:
+ * LH_EINVAL, LH_EUNSUPPORTED, LH_ENOMEM, LH_ECUDA.  *out is NULL on failure. */
+LH_API lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
+                                 const lh_disc_desc* disc, const lh_phys_desc* phys,
+                                 int32_t precision, void* stream,
+                                 const lh_batch_tuning* tuning, lh_batch** out);
+LH_API lh_status lh_batch_destroy(lh_batch* b);
+LH_API const char* lh_batch_last_error(const lh_batch* b);
+/* Offsets of each instance in the packed arrays (host, n + 1 entries each:
+ * off_v for N_V-sized arrays, off_e for N_E-sized ones; may be NULL) and the
+ * per-instance layouts (host, n entries, may be NULL). */
+LH_API lh_status lh_batch_layout(const lh_batch* b, int64_t* off_v, int64_t* off_e,
+                                 lh_layout_info* info);
+/* Initial conditions of every instance (as lh_init_state); t = 0, dt to be
+ * estimated. */
+LH_API lh_status lh_batch_init_state(lh_batch* b);
+/* Copies packed states in (host or device pointers).  t, dt: host arrays of n
+ * (NULL: 0); dt <= 0 asks for a fresh estimate. */
+LH_API lh_status lh_batch_set_state(lh_batch* b, const double* v, const double* e,
+                                    const double* x, const double* t, const double* dt);
+/* Copies packed states out (host or device pointers, any may be NULL) and
+ * synchronizes. */
+LH_API lh_status lh_batch_get_state(lh_batch* b, double* v, double* e, double* x);
+/* Per-instance scalars (host arrays of n, any may be NULL): time, next step
+ * size, accepted steps, rejected attempts and CG iterations of the last run,
+ * and the instance's lh_status (LH_OK, LH_ENONFINITE, LH_ECG, LH_EDTMIN). */
+LH_API lh_status lh_batch_query(lh_batch* b, double* t, double* dt, int64_t* steps,
+                                int64_t* rejects, int64_t* cg_iters, int32_t* status);
+/* Advances every instance to t_final (or max_steps accepted steps each) under
+ * its own step control; attempt graphs are launched in growing batches and
+ * the host polls the count of finished instances between batches.  stats
+ * (host, may be NULL).  Returns the first instance error (LH_ENONFINITE,
+ * LH_ECG, LH_EDTMIN; the failed instance stops, the others run on). */
+LH_API lh_status lh_batch_run_to(lh_batch* b, double t_final, int64_t max_steps,
+                                 lh_batch_stats* stats);
+/* One RK2-average step of every instance with the given step sizes (host
+ * array of n, each > 0), every attempt accepted: the replay of a recorded dt
+ * sequence, as lh_step_fixed. */
+LH_API lh_status lh_batch_step_fixed(lh_batch* b, const double* dt, lh_batch_stats* stats);
+/* Total energy 1/2 v.M_V.v + 1.M_E.e of every instance (host array of n);
+ * synchronizes. */
+LH_API lh_status lh_batch_total_energy(lh_batch* b, double* energy);
+/* Restricted force of every instance (Section 3.3, eq:rom-hr), as
+ * lh_force_sampled: list_off (device, n + 1 int64) delimits each instance's
+ * element ids in elem_ids (device int32, ids within the instance).  v, e, x:
+ * packed device states (NULL: the batch's current state); vtest: packed
+ * device test vectors or NULL.  Outputs (device) in list order:
+ * F1_local[list_off[n]][dim][ndof_h1] and, with vtest, FTv_local
+ * [list_off[n]][ndof_l2]; dt_est (host, n, may be NULL) = the estimate over
+ * each instance's listed elements (0 if one is inverted); synchronizes when
+ * dt_est != NULL. */
+LH_API lh_status lh_batch_force_sampled(lh_batch* b, const int64_t* list_off,
+                                        const int32_t* elem_ids, const double* v,
+                                        const double* e, const double* x,
+                                        const double* vtest, double* F1_local,
+                                        double* FTv_local, double* dt_est);
+/* Autotuner (not a step of the paper): times the stage kernel on the current
+ * states for every launch shape that fits the device (threads per CTA, CTAs
+ * per SM, node-line staging), reps launches each, keeps the fastest and
+ * returns it in *chosen (may be NULL).  The states and control blocks are
+ * left as they were. */
+LH_API lh_status lh_batch_autotune(lh_batch* b, int32_t reps, lh_batch_tuning* chosen);
+/* The launch shape in use. */
+LH_API lh_status lh_batch_tuning_get(const lh_batch* b, lh_batch_tuning* t);
 
 #ifdef __cplusplus
 }

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "lagh.h"
 
@@ -157,6 +158,15 @@ namespace lagh {
 lh_status set_error(lh_ctx* c, lh_status s, const std::string& msg);
 lh_status cuda_check(lh_ctx* c, cudaError_t e, const char* what);
 void build_basis(int k, int nq, int dim, Basis1D* b);
+// Geometry of a Cartesian box mesh (validates the descriptors; *why = reason).
+lh_status make_geom(const lh_mesh_desc* mesh, const lh_disc_desc* disc, Geom* g,
+                    std::string* why);
+// Initial condition of the problem at the nodes (host arrays, resized).
+void initial_state(const Geom& g, const lh_phys_desc& ph, std::vector<double>& v,
+                   std::vector<double>& e, std::vector<double>& x);
+// Banded Cholesky factor of the assembled 1D reference mass matrix of nel
+// elements (var = 1: without its two end nodes): L[i][m] = L_{i,i-m}, m <= k.
+void banded_cholesky_1d(const Basis1D& b, int k, int nel, int var, std::vector<double>& L);
 lh_status device_status(lh_ctx* c);  // reads ctl->status (synchronizes)
 
 // ---- kernel launchers (force.cu, mass.cu, step.cu) ----

@@ -186,6 +186,83 @@ using namespace lagh;
 
 // ------------------------------------------------------------- C ABI ----
 
+lh_status lagh::make_geom(const lh_mesh_desc* mesh, const lh_disc_desc* disc, Geom* out,
+                    std::string* why) {
+  auto bad = [&](lh_status st, const char* m) {
+    if (why) *why = m;
+    return st;
+  };
+  const int d = mesh->dim;
+  if (d != 2 && d != 3) return bad(LH_EINVAL, "dim must be 2 or 3");
+  const int k = disc->order;
+  if (k < 1 || k > 3 || (d == 3 && k > 2)) return bad(LH_EUNSUPPORTED, "order not built");
+  if (disc->nq != 2 * k) return bad(LH_EUNSUPPORTED, "only nq = 2k is built");
+  int nel[3] = {mesh->nx, mesh->ny, d == 3 ? mesh->nz : 1};
+  for (int i = 0; i < d; ++i) {
+    if (nel[i] < 1) return bad(LH_EINVAL, "element counts must be positive");
+    if (!(mesh->hi[i] > mesh->lo[i])) return bad(LH_EINVAL, "empty box");
+  }
+  Geom g;
+  memset(&g, 0, sizeof(g));
+  g.dim = d;
+  g.k = k;
+  g.nq = disc->nq;
+  g.nnodes = 1;
+  g.nelem = 1;
+  double vol = 1.0;
+  for (int i = 0; i < 3; ++i) {
+    g.n[i] = i < d ? nel[i] : 1;
+    g.nn[i] = i < d ? nel[i] * k + 1 : 1;
+    g.nnodes *= g.nn[i];
+    g.nelem *= g.n[i];
+    double h = i < d ? (mesh->hi[i] - mesh->lo[i]) / nel[i] : 1.0;
+    if (i < d) vol *= h;
+    g.lo[i] = i < d ? mesh->lo[i] : 0.0;
+    g.h[i] = h;
+    g.J0inv[i] = 1.0 / h;
+  }
+  int nd2 = 1;
+  for (int i = 0; i < d; ++i) nd2 *= k;
+  g.nv = (int64_t)d * g.nnodes;
+  g.ne = g.nelem * nd2;
+  g.detJ0 = vol;
+  g.ell0 = pow(vol, 1.0 / d) / k;
+  if (g.nelem > (int64_t)1 << 31) return bad(LH_EINVAL, "mesh too large");
+  *out = g;
+  return LH_OK;
+}
+
+void lagh::banded_cholesky_1d(const Basis1D& b, int k, int nel, int var, std::vector<double>& L) {
+  const int P = k + 1;
+  const int N = nel * k + 1 - 2 * var;
+  L.assign((size_t)(N > 0 ? N : 0) * (k + 1), 0.0);
+  auto G = [&](int i, int j) -> double {
+    int gi = i + var, gj = j + var;
+    double s = 0.0;
+    for (int e = 0; e < nel; ++e) {
+      int a = gi - e * k, c = gj - e * k;
+      if (a >= 0 && a < P && c >= 0 && c < P) s += b.M1[a][c];
+    }
+    return s;
+  };
+  for (int i = 0; i < N; ++i) {
+    for (int m = k; m >= 1; --m) {
+      int j = i - m;
+      if (j < 0) continue;
+      double s = G(i, j);
+      for (int q = 1; q <= k; ++q) {
+        int l = j - q;
+        if (l < 0 || i - l > k) continue;
+        s -= L[(size_t)i * (k + 1) + (i - l)] * L[(size_t)j * (k + 1) + q];
+      }
+      L[(size_t)i * (k + 1) + m] = s / L[(size_t)j * (k + 1)];
+    }
+    double s = G(i, i);
+    for (int m = 1; m <= k; ++m) s -= L[(size_t)i * (k + 1) + m] * L[(size_t)i * (k + 1) + m];
+    L[(size_t)i * (k + 1)] = sqrt(s);
+  }
+}
+
 extern "C" void lh_default_phys(lh_phys_desc* p) {
   memset(p, 0, sizeof(*p));
   p->problem = LH_SEDOV;
@@ -286,47 +363,21 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     delete c;
     return s;
   };
-  const int d = mesh->dim;
-  if (d != 2 && d != 3) return fail(LH_EINVAL, "dim must be 2 or 3");
   if (precision != LH_FP64 && precision != LH_MIXED) return fail(LH_EINVAL, "bad precision");
-  int k = disc->order;
-  if (k < 1 || k > 3 || (d == 3 && k > 2)) return fail(LH_EUNSUPPORTED, "order not built");
-  if (disc->nq != 2 * k) return fail(LH_EUNSUPPORTED, "only nq = 2k is built");
-  int nel[3] = {mesh->nx, mesh->ny, d == 3 ? mesh->nz : 1};
-  for (int i = 0; i < d; ++i) {
-    if (nel[i] < 1) return fail(LH_EINVAL, "element counts must be positive");
-    if (!(mesh->hi[i] > mesh->lo[i])) return fail(LH_EINVAL, "empty box");
+  {
+    std::string why;
+    lh_status gs = make_geom(mesh, disc, &c->g, &why);
+    if (gs != LH_OK) return fail(gs, why);
   }
   if (!(phys->gamma > 1.0)) return fail(LH_EINVAL, "gamma must exceed 1");
   if (phys->problem < LH_SEDOV || phys->problem > LH_UNIFORM)
     return fail(LH_EINVAL, "unknown problem");
   if (!(phys->cg_rtol > 0.0) || phys->cg_maxit < 1) return fail(LH_EINVAL, "bad CG settings");
-
   Geom& g = c->g;
-  g.dim = d;
-  g.k = k;
-  g.nq = disc->nq;
-  g.nnodes = 1;
-  g.nelem = 1;
-  double vol = 1.0;
-  for (int i = 0; i < 3; ++i) {
-    g.n[i] = i < d ? nel[i] : 1;
-    g.nn[i] = i < d ? nel[i] * k + 1 : 1;
-    g.nnodes *= g.nn[i];
-    g.nelem *= g.n[i];
-    double h = i < d ? (mesh->hi[i] - mesh->lo[i]) / nel[i] : 1.0;
-    if (i < d) vol *= h;
-    g.lo[i] = i < d ? mesh->lo[i] : 0.0;
-    g.h[i] = h;
-    g.J0inv[i] = 1.0 / h;
-  }
+  const int d = g.dim, k = g.k;
   int nd1 = 1, nd2 = 1, nqe = 1;
   for (int i = 0; i < d; ++i) { nd1 *= k + 1; nd2 *= k; nqe *= 2 * k; }
-  g.nv = (int64_t)d * g.nnodes;
-  g.ne = g.nelem * nd2;
-  g.detJ0 = vol;
-  g.ell0 = pow(vol, 1.0 / d) / k;
-  if (g.nelem > (int64_t)1 << 31) return fail(LH_EINVAL, "mesh too large");
+  const double vol = g.detJ0;
 
   Phys& ph = c->ph;
   ph.gamma = phys->gamma;
@@ -419,7 +470,6 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     bool uniform = true;
     for (int64_t el = 1; el < g.nelem; ++el)
       if (rho0K[el] != rho0K[0]) uniform = false;
-    const int P = k + 1;
     const int Btab[4] = {0, 14, 22, 30};
     int Bmax = 0;
     for (int dd = 0; dd < d; ++dd) {
@@ -431,33 +481,8 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
         const int N = nfull - 2 * var;
         c->tpc.off[dd][var] = (int64_t)lf.size();
         if (N <= 0) continue;
-        // banded assembled matrix and its Cholesky factor (host, FP64)
-        auto G = [&](int i, int j) -> double {
-          int gi = i + var, gj = j + var;
-          double s = 0.0;
-          for (int e = 0; e < g.n[dd]; ++e) {
-            int a = gi - e * k, b = gj - e * k;
-            if (a >= 0 && a < P && b >= 0 && b < P) s += c->basis.M1[a][b];
-          }
-          return s;
-        };
-        std::vector<double> L((size_t)N * (k + 1), 0.0);  // L[i][m] = L_{i,i-m}
-        for (int i = 0; i < N; ++i) {
-          for (int m = k; m >= 1; --m) {
-            int j = i - m;
-            if (j < 0) continue;
-            double s = G(i, j);
-            for (int q = 1; q <= k; ++q) {
-              int l = j - q;
-              if (l < 0 || i - l > k) continue;
-              s -= L[(size_t)i * (k + 1) + (i - l)] * L[(size_t)j * (k + 1) + q];
-            }
-            L[(size_t)i * (k + 1) + m] = s / L[(size_t)j * (k + 1)];
-          }
-          double s = G(i, i);
-          for (int m = 1; m <= k; ++m) s -= L[(size_t)i * (k + 1) + m] * L[(size_t)i * (k + 1) + m];
-          L[(size_t)i * (k + 1)] = sqrt(s);
-        }
+        std::vector<double> L;  // L[i][m] = L_{i,i-m}
+        banded_cholesky_1d(c->basis, k, g.n[dd], var, L);
         // columns of the inverse by banded solves; keep |i - j| <= B
         const int W = 2 * B + 1;
         std::vector<double> band((size_t)N * W, 0.0), col(N);
@@ -573,16 +598,16 @@ static lh_status set_pref(lh_ctx* c) {
   return cuda_check(c, err, "reference pressure");
 }
 
-extern "C" lh_status lh_init_state(lh_ctx* c) {
-  if (!c) return LH_EINVAL;
-  const Geom& g = c->g;
+void lagh::initial_state(const Geom& g, const lh_phys_desc& ph, std::vector<double>& v,
+                   std::vector<double>& e, std::vector<double>& x) {
   const int d = g.dim, k = g.k;
   const double pi = 3.14159265358979323846;
-  const lh_phys_desc& ph = c->phys_desc;
   double xn[kMaxOrder + 1], l2x[kMaxOrder], l2w[kMaxOrder];
   gll_nodes(k, xn);
   gl_rule(k, l2x, l2w);
-  std::vector<double> v(g.nv, 0.0), x(g.nv), e(g.ne, 0.0);
+  v.assign(g.nv, 0.0);
+  x.assign(g.nv, 0.0);
+  e.assign(g.ne, 0.0);
   // nodes: coordinate lo + (element + GLL node) h along each direction
   for (int64_t node = 0; node < g.nnodes; ++node) {
     int64_t r = node;
@@ -644,6 +669,13 @@ extern "C" lh_status lh_init_state(lh_ctx* c) {
       e[el * nd2 + j] = ev;
     }
   }
+}
+
+extern "C" lh_status lh_init_state(lh_ctx* c) {
+  if (!c) return LH_EINVAL;
+  const Geom& g = c->g;
+  std::vector<double> v, e, x;
+  initial_state(g, c->phys_desc, v, e, x);
   cudaStream_t s = c->stream;
   cudaError_t err = cudaMemcpyAsync(c->a.v, v.data(), g.nv * 8, cudaMemcpyHostToDevice, s);
   if (err == cudaSuccess) err = cudaMemcpyAsync(c->a.x, x.data(), g.nv * 8, cudaMemcpyHostToDevice, s);

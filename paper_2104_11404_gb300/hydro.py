@@ -6,34 +6,41 @@ import torch
 from . import lagh
 
 
+def descriptors(cfg, cg_rtol=None, cg_maxit=None, phys_overrides=None):
+    """(mesh, disc, phys) descriptors of a configuration dict."""
+    L = lagh
+    mesh = L.lh_mesh_desc()
+    mesh.dim = cfg["dim"]
+    mesh.nx, mesh.ny, mesh.nz = [int(v) for v in cfg["n"]]
+    for i in range(3):
+        mesh.lo[i] = float(cfg["lo"][i])
+        mesh.hi[i] = float(cfg["hi"][i])
+    disc = L.lh_disc_desc()
+    disc.order = cfg["order"]
+    disc.nq = cfg.get("nq", 2 * cfg["order"])
+    phys = L.lh_default_phys()
+    phys.problem = cfg["problem"]
+    phys.gamma = float(cfg["gamma"])
+    phys.visc = int(cfg.get("visc", 1))
+    phys.source = int(cfg.get("source", 1))
+    phys.blast_energy = float(cfg.get("blast_energy", 0.25))
+    phys.e_uniform = float(cfg.get("e_uniform", 1.0))
+    phys.cfl = float(cfg.get("cfl", 0.5))
+    if cg_rtol is not None:
+        phys.cg_rtol = cg_rtol
+    if cg_maxit is not None:
+        phys.cg_maxit = cg_maxit
+    for k, v in (phys_overrides or {}).items():
+        setattr(phys, k, v)
+    return mesh, disc, phys
+
+
 class Hydro:
     def __init__(self, cfg, precision="fp64", stream=None, cg_rtol=None, cg_maxit=None,
                  phys_overrides=None):
         L = lagh
         self.cfg = dict(cfg)
-        mesh = L.lh_mesh_desc()
-        mesh.dim = cfg["dim"]
-        mesh.nx, mesh.ny, mesh.nz = [int(v) for v in cfg["n"]]
-        for i in range(3):
-            mesh.lo[i] = float(cfg["lo"][i])
-            mesh.hi[i] = float(cfg["hi"][i])
-        disc = L.lh_disc_desc()
-        disc.order = cfg["order"]
-        disc.nq = cfg.get("nq", 2 * cfg["order"])
-        phys = L.lh_default_phys()
-        phys.problem = cfg["problem"]
-        phys.gamma = float(cfg["gamma"])
-        phys.visc = int(cfg.get("visc", 1))
-        phys.source = int(cfg.get("source", 1))
-        phys.blast_energy = float(cfg.get("blast_energy", 0.25))
-        phys.e_uniform = float(cfg.get("e_uniform", 1.0))
-        phys.cfl = float(cfg.get("cfl", 0.5))
-        if cg_rtol is not None:
-            phys.cg_rtol = cg_rtol
-        if cg_maxit is not None:
-            phys.cg_maxit = cg_maxit
-        for k, v in (phys_overrides or {}).items():
-            setattr(phys, k, v)
+        mesh, disc, phys = descriptors(cfg, cg_rtol, cg_maxit, phys_overrides)
         self.precision = L.LH_MIXED if precision == "mixed" else L.LH_FP64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = L.lh_create(mesh, disc, phys, self.precision, self.stream.cuda_stream)

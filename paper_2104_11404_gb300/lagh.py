@@ -24,7 +24,10 @@ API_NAMES = [
     "lh_layout", "lh_init_state", "lh_set_state", "lh_get_state", "lh_force",
     "lh_force_sampled", "lh_mass_apply_v", "lh_mass_solve_v", "lh_mass_solve_e",
     "lh_total_energy", "lh_step_fixed", "lh_step", "lh_run_to", "lh_force_static",
-    "lh_precond_apply",
+    "lh_precond_apply", "lh_batch_create", "lh_batch_destroy", "lh_batch_last_error",
+    "lh_batch_layout", "lh_batch_init_state", "lh_batch_set_state", "lh_batch_get_state",
+    "lh_batch_query", "lh_batch_run_to", "lh_batch_step_fixed", "lh_batch_total_energy",
+    "lh_batch_force_sampled", "lh_batch_autotune", "lh_batch_tuning_get",
 ]
 
 
@@ -62,6 +65,18 @@ class lh_run_stats(ctypes.Structure):
                 ("cg_iters", ctypes.c_int64), ("t", ctypes.c_double), ("dt", ctypes.c_double),
                 ("energy0", ctypes.c_double), ("energy", ctypes.c_double),
                 ("wall_ms", ctypes.c_double)]
+
+
+class lh_batch_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("rejects", ctypes.c_int64),
+                ("cg_iters", ctypes.c_int64), ("attempts", ctypes.c_int64),
+                ("instances_done", ctypes.c_int64), ("dof_updates", ctypes.c_int64),
+                ("graph_launches", ctypes.c_int64), ("wall_ms", ctypes.c_double)]
+
+
+class lh_batch_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("smem_lines", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -110,8 +125,27 @@ def load():
     L.lh_force_static.argtypes = [ctypes.POINTER(lh_mesh_desc), ctypes.POINTER(lh_disc_desc),
                                   ctypes.POINTER(lh_phys_desc), _dp, _dp, _dp, _dp,
                                   ctypes.POINTER(ctypes.c_double), _vp]
+    P = ctypes.POINTER
+    L.lh_batch_create.argtypes = [ctypes.c_int32, P(lh_mesh_desc), P(lh_disc_desc),
+                                  P(lh_phys_desc), ctypes.c_int32, _vp, P(lh_batch_tuning),
+                                  P(_vp)]
+    L.lh_batch_destroy.argtypes = [_vp]
+    L.lh_batch_last_error.argtypes = [_vp]
+    L.lh_batch_last_error.restype = ctypes.c_char_p
+    L.lh_batch_layout.argtypes = [_vp, _vp, _vp, _vp]
+    L.lh_batch_init_state.argtypes = [_vp]
+    L.lh_batch_set_state.argtypes = [_vp, _dp, _dp, _dp, _dp, _dp]
+    L.lh_batch_get_state.argtypes = [_vp, _dp, _dp, _dp]
+    L.lh_batch_query.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.lh_batch_run_to.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, P(lh_batch_stats)]
+    L.lh_batch_step_fixed.argtypes = [_vp, _dp, P(lh_batch_stats)]
+    L.lh_batch_total_energy.argtypes = [_vp, _dp]
+    L.lh_batch_force_sampled.argtypes = [_vp, _vp, _vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+    L.lh_batch_autotune.argtypes = [_vp, ctypes.c_int32, P(lh_batch_tuning)]
+    L.lh_batch_tuning_get.argtypes = [_vp, P(lh_batch_tuning)]
     for name in API_NAMES:
-        if name not in ("lh_default_phys", "lh_status_string", "lh_last_error"):
+        if name not in ("lh_default_phys", "lh_status_string", "lh_last_error",
+                        "lh_batch_last_error"):
             getattr(L, name).restype = S
     _lib = L
     return L
@@ -261,3 +295,100 @@ def lh_force_static(mesh, disc, phys, v, e, x, F1, stream=None, want_dt=True):
     if st != LH_OK:
         raise LaghError(st, "lh_force_static failed")
     return dt.value if want_dt else None
+
+
+# ---- batched form ----------------------------------------------------------
+
+def _bcheck(b, st):
+    if st != LH_OK:
+        raise LaghError(st, load().lh_batch_last_error(b).decode())
+
+
+def lh_batch_create(meshes, disc, physs, precision, stream=None, tuning=None):
+    """meshes, physs: sequences of lh_mesh_desc / lh_phys_desc (one per
+    instance).  tuning: lh_batch_tuning or None."""
+    n = len(meshes)
+    if len(physs) != n:
+        raise ValueError("one physics descriptor per mesh")
+    M = (lh_mesh_desc * n)(*meshes)
+    Ph = (lh_phys_desc * n)(*physs)
+    h = _vp()
+    st = load().lh_batch_create(n, M, ctypes.byref(disc), Ph, int(precision), stream,
+                                ctypes.byref(tuning) if tuning is not None else None,
+                                ctypes.byref(h))
+    if st != LH_OK:
+        raise LaghError(st, "lh_batch_create failed")
+    return h
+
+
+def lh_batch_destroy(b):
+    load().lh_batch_destroy(b)
+
+
+def lh_batch_last_error(b):
+    return load().lh_batch_last_error(b).decode()
+
+
+def lh_batch_layout(b, n):
+    off_v = (ctypes.c_int64 * (n + 1))()
+    off_e = (ctypes.c_int64 * (n + 1))()
+    info = (lh_layout_info * n)()
+    _bcheck(b, load().lh_batch_layout(b, ctypes.addressof(off_v), ctypes.addressof(off_e),
+                                      ctypes.addressof(info)))
+    return list(off_v), list(off_e), list(info)
+
+
+def lh_batch_init_state(b):
+    _bcheck(b, load().lh_batch_init_state(b))
+
+
+def lh_batch_set_state(b, v, e, x, t=None, dt=None):
+    """t, dt: host float64 arrays (numpy) of n, or None."""
+    _bcheck(b, load().lh_batch_set_state(b, _ptr(v), _ptr(e), _ptr(x), _ptr(t), _ptr(dt)))
+
+
+def lh_batch_get_state(b, v=None, e=None, x=None):
+    _bcheck(b, load().lh_batch_get_state(b, _ptr(v), _ptr(e), _ptr(x)))
+
+
+def lh_batch_query(b, t=None, dt=None, steps=None, rejects=None, cg_iters=None, status=None):
+    """Host numpy arrays of n (float64, float64, int64, int64, int64, int32)."""
+    _bcheck(b, load().lh_batch_query(b, _ptr(t), _ptr(dt), _ptr(steps), _ptr(rejects),
+                                     _ptr(cg_iters), _ptr(status)))
+
+
+def lh_batch_run_to(b, t_final, max_steps=2 ** 62):
+    stats = lh_batch_stats()
+    _bcheck(b, load().lh_batch_run_to(b, float(t_final), int(max_steps), ctypes.byref(stats)))
+    return {k: getattr(stats, k) for k, _ in lh_batch_stats._fields_}
+
+
+def lh_batch_step_fixed(b, dt):
+    """dt: host float64 numpy array of n."""
+    stats = lh_batch_stats()
+    _bcheck(b, load().lh_batch_step_fixed(b, _ptr(dt), ctypes.byref(stats)))
+    return {k: getattr(stats, k) for k, _ in lh_batch_stats._fields_}
+
+
+def lh_batch_total_energy(b, out):
+    """out: host float64 numpy array of n."""
+    _bcheck(b, load().lh_batch_total_energy(b, _ptr(out)))
+
+
+def lh_batch_force_sampled(b, list_off, elem_ids, F1_local, v=None, e=None, x=None, vtest=None,
+                           FTv_local=None, dt_est=None):
+    _bcheck(b, load().lh_batch_force_sampled(b, _ptr(list_off), _ptr(elem_ids), _ptr(v), _ptr(e),
+                                             _ptr(x), _ptr(vtest), _ptr(F1_local),
+                                             _ptr(FTv_local), _ptr(dt_est)))
+
+
+def lh_batch_autotune(b, reps=2):
+    t = lh_batch_tuning()
+    _bcheck(b, load().lh_batch_autotune(b, int(reps), ctypes.byref(t)))
+    return t
+
+
+def lh_batch_tuning_get(b):
+    t = lh_batch_tuning()
+    _bcheck(b, load().lh_batch_tuning_get(b, ctypes.byref(t)))
+    return t
