@@ -27,6 +27,7 @@ sys.path.insert(0, ROOT)
 
 CHUNK = 50           # accepted time steps per bench step
 WORKLOAD = "tg2d_64"
+BATCH_CHUNK = 20     # accepted time steps of every instance per batched bench step
 
 
 def _dist():
@@ -255,6 +256,8 @@ def run_native(args):
                     e2e_steps=sum_over_ranks(e2e_steps), force_ms=force_ms, pass_ms=pass_ms)
 
     res = {p: measure(p) for p in ("mixed", "fp64")}
+    batched = None if args.no_batch else measure_batched(args, stream, flush, max_over_ranks,
+                                                         sum_over_ranks)
     if rank != 0:
         return None
     m, f = res["mixed"], res["fp64"]
@@ -313,9 +316,163 @@ def run_native(args):
         "gpu_launches": int(launches),
         "clocks": m["clocks"],
     }
+    if batched is not None:
+        batched["config"] = ("512 independent 2D point-blast instances, E0 U[0.1,1], gamma "
+                             "U[1.3,1.67], n x n quads with n from {16,24,32,48}, Q2/Q1, mixed, "
+                             "splitmix64 seed 2104114040")
+        line["batched"] = batched
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, bounded_seconds=12.0)
     return line
+
+
+def batch_fp64_flops(cfgs):
+    """Algorithmic FP64 flops of one attempt (two stages) of the batched
+    mixed step, summed over instances, with n_e elements and N_V velocity
+    unknowns each (2D Q2/Q1): per element F.1 row sums 72, node gather 18,
+    mass apply (two 3x3 contractions per component, scale) 234 and its gather
+    18, energy update (F^T w 144, M_E^-1 32, update 4) 180; per velocity
+    unknown the line solves 21 (forward and backward substitution along both
+    directions, k = 2, and the scale), CG dots and updates 12, stage update 4."""
+    tot = 0
+    for c in cfgs:
+        n = c["n"][0] * c["n"][1]
+        nn = (2 * c["n"][0] + 1) * (2 * c["n"][1] + 1)
+        nv = 2 * nn
+        tot += 522 * n + 37 * nv
+    return 2 * tot
+
+
+def measure_batched(args, stream, flush, max_over_ranks, sum_over_ranks, sizes_fp64=True):
+    """The 512-instance point-blast sweep (mixed), one bench step = BATCH_CHUNK
+    accepted time steps of every instance (lh_batch_run_to); plus the restricted
+    force on a seeded 5% element sample of every instance, and the plain
+    single-problem paths on the same instance mix for the speed-up."""
+    import numpy as np
+    import torch
+    from paper_2104_11404_gb300 import lagh
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.batch import Batch
+    from paper_2104_11404_gb300.hydro import Hydro
+    cfgs = W.batch_instances()
+    out = {}
+    with torch.cuda.stream(stream):
+        b = Batch(cfgs, precision="mixed", stream=stream)
+        b.init_state()
+        t0 = time.time()
+        tune = b.autotune(reps=2)
+        tune_s = time.time() - t0
+        dofs = b.dofs()
+        for _ in range(args.warmup):
+            b.run_to(0.8, max_steps=BATCH_CHUNK)
+        torch.cuda.synchronize()
+        dev_ms, dof_upd, steps, rejects, launches = 0.0, 0, 0, 0, 0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = b.run_to(0.8, max_steps=BATCH_CHUNK)
+            e1.record(stream)
+            e1.synchronize()
+            dev_ms += e0.elapsed_time(e1)
+            dof_upd += st["dof_updates"]
+            steps += st["steps"]
+            rejects += st["rejects"]
+            launches += st["graph_launches"]
+        # replicas: every rank advances its own copy of the sweep
+        value = sum_over_ranks(dof_upd) / (max_over_ranks(dev_ms) * 1e-3)
+        value_rank = dof_upd / (dev_ms * 1e-3)
+        attempt_ms = dev_ms / max(1, launches)
+        # end to end: pinned host state in, run, state out
+        hv = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
+        he = torch.empty(b.ne, dtype=torch.float64, pin_memory=True)
+        hx = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
+        lagh.lh_batch_get_state(b.b, hv, he, hx)
+        q = b.query()
+        e2e_ms, e2e_upd = 0.0, 0
+        for _ in range(max(1, args.steps // 2)):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.set_state(hv, he, hx, q["t"], q["dt"])
+            st = b.run_to(0.8, max_steps=BATCH_CHUNK)
+            lagh.lh_batch_get_state(b.b, hv, he, hx)
+            q = b.query()
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms += e0.elapsed_time(e1)
+            e2e_upd += st["dof_updates"]
+        # restricted force on 5% of every instance's elements
+        lists = [W.element_sample(c["n"][0] * c["n"][1], frac=0.05, stream=i)
+                 for i, c in enumerate(cfgs)]
+        nsamp = int(sum(len(l) for l in lists))
+        b.force_sampled(lists)
+        reps = 20
+        F1, _, off, _ = b.force_sampled(lists)
+        d_off = torch.from_numpy(off).to("cuda")
+        d_ids = torch.from_numpy(np.concatenate(lists).astype(np.int32)).to("cuda")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            lagh.lh_batch_force_sampled(b.b, d_off, d_ids, F1)
+        e1.record(stream)
+        e1.synchronize()
+        hr_ms = e0.elapsed_time(e1) / reps
+        E_all = b.total_energy()
+        b.close()
+        # plain single-problem paths (one context per problem) on the same mix
+        rates = {}
+        if sizes_fp64:
+            for prec in ("fp64", "mixed"):
+                for n in W.BATCH_SIZES:
+                    c = dict(cfgs[0], n=(n, n, 1), gamma=1.4, blast_energy=0.5)
+                    g = Hydro(c, precision=prec, stream=stream)
+                    g.init_state()
+                    g.run_to(0.8, max_steps=3)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    stg = g.run_to(0.8, max_steps=BATCH_CHUNK)
+                    e1.record(stream)
+                    e1.synchronize()
+                    N = 2 * g.nv + g.ne
+                    rates[(prec, n)] = N * stg["steps"] / (e0.elapsed_time(e1) * 1e-3)
+                    g.close()
+    per_inst_steps = steps / len(cfgs)
+    out = {"value": value, "unit": "DOF-updates/s", "instances": len(cfgs),
+           "dofs_total": int(dofs.sum()), "ms_per_step": dev_ms / args.steps,
+           "time_steps_per_bench_step": BATCH_CHUNK, "accepted_steps": steps, "rejects": rejects,
+           "attempt_graphs": launches, "attempt_ms": attempt_ms, "tuning": tune,
+           "autotune_s": tune_s,
+           "e2e": {"value": e2e_upd / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
+                   "h2d_bytes_per_step": 8 * (2 * b.nv + b.ne) + 16 * len(cfgs),
+                   "d2h_bytes_per_step": 8 * (2 * b.nv + b.ne)},
+           "hyper_reduced_force": {"sampled_elements": nsamp, "launch_us": hr_ms * 1e3,
+                                   "elements_per_s": nsamp / (hr_ms * 1e-3),
+                                   "sample": "ceil(0.05 n_e) elements per instance, seeded "
+                                             "Fisher-Yates, sorted"},
+           "energy_min": float(np.min(E_all))}
+    fl = batch_fp64_flops(cfgs)
+    out["roofline"] = {"bound": "alu", "kernel": "batch_stage_kernel (both stages of an attempt)",
+                       "achieved": fl / (attempt_ms * 1e-3) / 1e12, "peak": 1.25,
+                       "unit": "TFLOP/s (FP64)",
+                       "frac": fl / (attempt_ms * 1e-3) / 1e12 / 1.25,
+                       "algorithmic_fp64_flops_per_attempt": fl,
+                       "peak_source": "GB300 nominal FP64 rate (1.25 TFLOP/s)"}
+    if rates:
+        # time the same accepted steps would take through one context per problem
+        def seq_time(prec):
+            return sum(dofs[i] * per_inst_steps / rates[(prec, c["n"][0])] for i, c in enumerate(cfgs))
+        out["single_problem_fp64"] = {"value": dofs.sum() * per_inst_steps / seq_time("fp64"),
+                                      "rates_by_size": {str(n): rates[("fp64", n)] for n in W.BATCH_SIZES}}
+        out["single_problem_mixed"] = {"value": dofs.sum() * per_inst_steps / seq_time("mixed"),
+                                       "rates_by_size": {str(n): rates[("mixed", n)] for n in W.BATCH_SIZES}}
+        out["speedup_over_fp64_single_problem"] = value_rank / out["single_problem_fp64"]["value"]
+        out["speedup_over_mixed_single_problem"] = value_rank / out["single_problem_mixed"]["value"]
+    return out
 
 
 def cpu_baseline(args, bounded_seconds=12.0, steps=None):
@@ -391,6 +548,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep")
     ap.add_argument("--direct-launch", action="store_true",
                     help="launch the step's kernels one by one instead of one CUDA graph per "
                          "attempt (kernel profilers cannot see kernels inside graphs with "

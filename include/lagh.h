@@ -294,6 +294,16 @@ LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* d
                                  const lh_phys_desc* phys, const double* v, const double* e,
                                  const double* x, double* F1, double* dt_est, void* stream);
 
+/* Self-check of the library's FP32 <-> FP64 conversions (a service of the
+ * library, not a step of the paper; the FP32 paths convert on the integer
+ * pipes because the FP64 pipe of this GPU is narrow): f_out[i] = in[i] rounded
+ * to FP32 (nearest, ties to even; results below the normal FP32 range flush
+ * to zero) and d_out[i] = f_out[i] widened back to FP64 exactly.  Device
+ * pointers, n entries, on stream (cudaStream_t as void*).  Errors: LH_EINVAL,
+ * LH_ECUDA. */
+LH_API lh_status lh_check_conversions(const double* in, int64_t n, float* f_out, double* d_out,
+                                      void* stream);
+
 /* ---------------------------------------------------------------------------
  * Batched form: n independent instances of the time step, each on its own
  * Cartesian box mesh with its own physics (a parameter sweep such as the

@@ -254,10 +254,15 @@ static lh_status begin_run(lh_batch* b, double t_final, int64_t max_steps, int f
                         b->work);
     if ((st = bcheck(b, e, "step sizes")) != LH_OK) return st;
   } else {
-    BatchArgs a = bargs(b);
-    a.out = b->aux;
-    if ((st = launch_aux(b, b->ops.estimate, b->stage_smem, a, nullptr, b->work)) != LH_OK)
-      return st;
+    if ((st = read_ctl(b)) != LH_OK) return st;
+    bool need = false;
+    for (int i = 0; i < b->n && !need; ++i) need = !(b->ctl_host[i].dt > 0.0);
+    if (need) {
+      BatchArgs a = bargs(b);
+      a.out = b->aux;
+      if ((st = launch_aux(b, b->ops.estimate, b->stage_smem, a, nullptr, b->work)) != LH_OK)
+        return st;
+    }
   }
   // per-instance dt_min fractions live after the estimates
   double* frac = b->aux + b->n;
@@ -273,12 +278,16 @@ static lh_status begin_run(lh_batch* b, double t_final, int64_t max_steps, int f
   return bcheck(b, e == cudaSuccess ? cudaGetLastError() : e, "begin");
 }
 
-static lh_status run_loop(lh_batch* b, int64_t max_attempts, float* wall_ms, int64_t* launched) {
+// Launches attempt graphs until every instance is done: first a batch sized
+// by the step budget (a run of a few steps needs no poll in between), then
+// growing batches with a poll of the finished count before each.
+static lh_status run_loop(lh_batch* b, int64_t max_attempts, int64_t first_batch, float* wall_ms,
+                          int64_t* launched) {
   lh_status st;
   if ((st = build_graph(b)) != LH_OK) return st;
   cudaEventRecord(b->ev0, b->work);
   int64_t att = 0;
-  int64_t batch = 4;
+  int64_t batch = first_batch > 0 ? first_batch : 4;
   cudaError_t e = cudaSuccess;
   while (att < max_attempts) {
     e = cudaMemcpyAsync(b->ndone_host, b->ndone, sizeof(int), cudaMemcpyDeviceToHost, b->work);
@@ -289,7 +298,9 @@ static lh_status run_loop(lh_batch* b, int64_t max_attempts, float* wall_ms, int
     for (int64_t i = 0; i < nb && e == cudaSuccess; ++i) e = cudaGraphLaunch(b->graph, b->work);
     if ((st = bcheck(b, e, "attempt launch")) != LH_OK) return st;
     att += nb;
-    if (batch < 64) batch *= 2;
+    // after the first batch: small, then doubling (the few instances that
+    // redid steps finish within a few attempts)
+    batch = (nb == first_batch && att == nb) ? 4 : (batch < 64 ? 2 * batch : 64);
   }
   cudaEventRecord(b->ev1, b->work);
   e = cudaEventSynchronize(b->ev1);
@@ -373,6 +384,7 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
     I.ph.visc = p.visc;
     I.ph.problem = p.problem;
     I.ph.source = (p.source && p.problem == LH_TAYLOR_GREEN && g.dim == 2) ? 1 : 0;
+    set_phys_floats(I.ph);
     b->has_source |= I.ph.source;
     I.kc.beta1 = p.beta1;
     I.kc.beta2 = p.beta2;
@@ -657,7 +669,8 @@ static lh_status batch_run(lh_batch* b, double t_final, int64_t max_steps, int f
   // every attempt of an unfinished instance is accepted, rejected or ends it;
   // 60 rejections in a row take dt below any dt_min fraction above 1e-5
   const int64_t max_att = fixed ? 1 : (max_steps > INT64_MAX / 64 ? INT64_MAX : 61 * (max_steps + 1));
-  if ((st = run_loop(b, max_att, &ms, &launched)) != LH_OK) return st;
+  const int64_t first = fixed ? 1 : (max_steps < 63 ? max_steps + 1 : 64);
+  if ((st = run_loop(b, max_att, first, &ms, &launched)) != LH_OK) return st;
   if ((st = read_ctl(b)) != LH_OK) return st;
   if ((st = bcheck(b, join(b, false), "stream join")) != LH_OK) return st;
   if (stats) {

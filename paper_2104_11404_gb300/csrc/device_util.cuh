@@ -81,6 +81,70 @@ __device__ __forceinline__ double gather_node(const Geom& g, const double* __res
   return s;
 }
 
+// ------------------------------------------------ precision conversions ----
+// On this GPU FP64 arithmetic issues at 1/64 of the FP32 rate, and the FP64
+// pipe also executes conversions between FP32 and FP64.  The FP32 paths
+// therefore convert with integer operations (IEEE 754 bit layouts: FP32 has an
+// 8-bit exponent biased by 127 and a 23-bit fraction, FP64 an 11-bit exponent
+// biased by 1023 and a 52-bit fraction).
+
+// Exact FP32 -> FP64 (every float is a double): rebias the exponent, widen the
+// fraction; subnormal floats are normalised, inf / NaN keep their class.
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned ex = (u >> 23) & 0xffu;
+  const unsigned m = u & 0x7fffffu;
+  unsigned long long bits;
+  if (ex == 0u) {
+    if (m == 0u) {
+      bits = s;
+    } else {  // m 2^-149 with its leading bit at position p
+      const int p = 31 - __clz((int)m);
+      bits = s | ((unsigned long long)(p + 874) << 52) |
+             (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+    }
+  } else if (ex == 0xffu) {
+    bits = s | 0x7ff0000000000000ull | ((unsigned long long)m << 29);
+  } else {
+    bits = s | ((unsigned long long)(ex + 896u) << 52) | ((unsigned long long)m << 29);
+  }
+  return __longlong_as_double((long long)bits);
+}
+
+// FP64 -> FP32 rounded to nearest, ties to even (as a C cast), for results in
+// the normal FP32 range; results below it flush to a signed zero, above it
+// round to infinity, NaN stays NaN.
+__device__ __forceinline__ float d2f_rn(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned s = (unsigned)(b >> 32) & 0x80000000u;
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  const unsigned long long m = b & 0xfffffffffffffull;
+  if (ex == 0x7ff) return __uint_as_float(s | 0x7f800000u | (m ? 0x400000u : 0u));
+  int fe = ex - 896;  // FP32 biased exponent
+  if (fe <= 0) return __uint_as_float(s);
+  unsigned r = (unsigned)(m >> 29);
+  const unsigned rem = (unsigned)(m & 0x1fffffffull);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) {
+    if (++r == 0x800000u) {  // the fraction carried into the exponent
+      r = 0u;
+      ++fe;
+    }
+  }
+  if (fe >= 0xff) return __uint_as_float(s | 0x7f800000u);
+  return __uint_as_float(s | ((unsigned)fe << 23) | r);
+}
+
+template <typename T>
+__device__ __forceinline__ T from_double(double d);
+template <>
+__device__ __forceinline__ double from_double<double>(double d) { return d; }
+template <>
+__device__ __forceinline__ float from_double<float>(double d) { return d2f_rn(d); }
+
+__device__ __forceinline__ double to_double(double d) { return d; }
+__device__ __forceinline__ double to_double(float f) { return f2d_exact(f); }
+
 // ---------------------------------------------------------- reductions ----
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -42,7 +42,8 @@ struct FL {
   static constexpr size_t B_L2 = al(S_L2 * sizeof(double));
   static constexpr size_t B_ELEM = B_XS + B_VS + B_WS + B_ES + B_DQ + B_GQ + B_FK + B_SCR + B_L2;
   static constexpr size_t B_TAB = al(NQ * P * sizeof(T)) * 2 + al(NQ * K * sizeof(T)) +
-                                  al(NQ * K * sizeof(double)) + al(NQ * sizeof(double));
+                                  al(NQ * K * sizeof(double)) + al(NQ * sizeof(double)) +
+                                  al(NQ * sizeof(T));
   static constexpr size_t BYTES = B_TAB + EPB * B_ELEM + NTT * sizeof(unsigned long long);
 };
 
@@ -87,6 +88,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
   T* Ls = reinterpret_cast<T*>(sp); sp += F::al(NQ * K * sizeof(T));
   double* Ld = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * sizeof(double));
   double* Wd = reinterpret_cast<double*>(sp); sp += F::al(NQ * sizeof(double));
+  T* Wt = reinterpret_cast<T*>(sp); sp += F::al(NQ * sizeof(T));
   unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + F::B_TAB + F::EPB * F::B_ELEM);
 
   const int tid = threadIdx.x;
@@ -113,7 +115,10 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     Ls[i] = tab<T>(prm.b.L[q][j], prm.b.Lf[q][j]);
     Ld[i] = prm.b.L[q][j];
   }
-  for (int i = tid; i < NQ; i += blockDim.x) Wd[i] = prm.b.W[i];
+  for (int i = tid; i < NQ; i += blockDim.x) {
+    Wd[i] = prm.b.W[i];
+    Wt[i] = tab<T>(prm.b.W[i], prm.b.Wf[i]);
+  }
 
   const int64_t slot = slot0 + le;
   const bool active = le < F::EPB && slot < A.nslots;
@@ -133,11 +138,11 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
       int c = w / ND1, i = w - c * ND1;
       int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
       int64_t node = elem_node<K>(g, E, a, b, cc);
-      xs[w] = (T)(A.x[c * g.nnodes + node] - x0[c]);
-      vs[w] = (T)A.v[c * g.nnodes + node];
+      xs[w] = from_double<T>(A.x[c * g.nnodes + node] - x0[c]);
+      vs[w] = from_double<T>(A.v[c * g.nnodes + node]);
       if (with_w) ws[w] = A.vtest[c * g.nnodes + node];
     }
-    for (int j = tq; j < ND2; j += NQD) es[j] = (T)A.e[el * ND2 + j];
+    for (int j = tq; j < ND2; j += NQD) es[j] = from_double<T>(A.e[el * ND2 + j]);
   }
   __syncthreads();
 
@@ -252,32 +257,32 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     }
     T J[DIM][DIM], Gv[DIM][DIM], J0i[DIM], sigma[DIM][DIM], tau;
     for (int c = 0; c < DIM; ++c) {
-      J0i[c] = (T)g.J0inv[c];
+      J0i[c] = tab<T>(g.J0inv[c], g.J0invf[c]);
       for (int m = 0; m < DIM; ++m) {
         J[c][m] = grad[c][m];
         Gv[c][m] = grad[DIM + c][m];
       }
     }
-    const T rho0K = (T)prm.rho0K[el];
+    const T rho0K = from_double<T>(prm.rho0K[el]);
     if (A.mode == kForceFull) {
-      const T pref = (MIXED && A.p_ref != nullptr) ? (T)(*A.p_ref) : T(0);
-      flags = qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, (T)g.ell0,
-                                     (T)(1.0 / K), pref, sigma, tau);
-      tau_q = (double)tau;
+      const T pref = (MIXED && A.p_ref != nullptr) ? from_double<T>(*A.p_ref) : T(0);
+      flags = qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, tab<T>(g.ell0, g.ell0f),
+                                     T(1) / T(K), pref, sigma, tau);
+      tau_q = to_double(tau);
     } else {
       // reference pressure only: sigma = -p_ref I
-      const T pref = (T)(*A.p_ref);
+      const T pref = from_double<T>(*A.p_ref);
       for (int c = 0; c < DIM; ++c)
         for (int n = 0; n < DIM; ++n) sigma[c][n] = (c == n) ? -pref : T(0);
     }
-    double alpha = Wd[qx] * Wd[qy] * (DIM == 3 ? Wd[qz] : 1.0);
+    const T alphaT = DIM == 3 ? Wt[qx] * Wt[qy] * Wt[qz] : Wt[qx] * Wt[qy];
     T Aj[DIM][DIM];
     adj_of<T, DIM>(J, Aj);
     for (int c = 0; c < DIM; ++c)
       for (int m = 0; m < DIM; ++m) {
         T acc = T(0);
         for (int n = 0; n < DIM; ++n) acc += sigma[c][n] * Aj[m][n];
-        dq[(c * DIM + m) * NQD + tq] = (T)alpha * acc;
+        dq[(c * DIM + m) * NQD + tq] = alphaT * acc;
       }
     if (!MIXED && A.D != nullptr)
       for (int cm = 0; cm < DIM * DIM; ++cm)
@@ -290,7 +295,8 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
       gq[tq] = gsum;
     }
     if (A.srcE != nullptr && DIM == 2) {
-      double X = x0[0] + (double)xval[0], Y = x0[1] + (double)xval[1];
+      const double alpha = Wd[qx] * Wd[qy];
+      double X = x0[0] + to_double(xval[0]), Y = x0[1] + to_double(xval[1]);
       gq[NQD + tq] = alpha * prm.rho0K[el] * tg_source(X, Y, prm.ph.gamma);
     }
   }
@@ -443,15 +449,15 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         for (int w = tq; w < DIM * ND1 * ND2; w += NQD) A.FK[el * (DIM * ND1 * ND2) + w] = fk[w];
       // F.1 = row sums in FP64
       for (int w = tq; w < DIM * ND1; w += NQD) {
-        double s = 0.0;
-        for (int j = 0; j < ND2; ++j) s += (double)fk[w * ND2 + j];
+        double s = f2d_exact(fk[w * ND2]);
+        for (int j = 1; j < ND2; ++j) s += f2d_exact(fk[w * ND2 + j]);
         A.F1E[slot * DIM * ND1 + w] = s;
       }
       // F^T w in FP64
       if (with_w)
         for (int j = tq; j < ND2; j += NQD) {
           double s = 0.0;
-          for (int ci = 0; ci < DIM * ND1; ++ci) s += (double)fk[ci * ND2 + j] * ws[ci];
+          for (int ci = 0; ci < DIM * ND1; ++ci) s = fma(f2d_exact(fk[ci * ND2 + j]), ws[ci], s);
           A.FTvE[slot * ND2 + j] = s;
         }
     }
@@ -559,7 +565,7 @@ struct EL {
   static constexpr int S_L2 = DIM == 2 ? K * NQ : K * NQ * NQ + K * K * NQ;
   static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
   static constexpr size_t B_ELEM = al(DIM * ND1 * 8) + al(S_INTERP * 8) + al(NQD * 8) +
-                                   al(S_L2 * 8) + al(ND2 * 8);
+                                   al(S_L2 * 8) + al(ND2 * 8) + al(8);
   static constexpr size_t B_TAB = 3 * al(NQ * P * 8) + al(NQ * K * 8) + al(81 * 8);
   static constexpr size_t BYTES = B_TAB + EPB * B_ELEM;
 };
@@ -592,7 +598,8 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   double* scr = reinterpret_cast<double*>(ep); ep += F::al(F::S_INTERP * 8);
   double* gq = reinterpret_cast<double*>(ep); ep += F::al(NQD * 8);
   double* l2s = reinterpret_cast<double*>(ep); ep += F::al(F::S_L2 * 8);
-  double* ftv = reinterpret_cast<double*>(ep);
+  double* ftv = reinterpret_cast<double*>(ep); ep += F::al(ND2 * 8);
+  double* crs = reinterpret_cast<double*>(ep);  // coef / (rho0 |J0|) of the element
 
   for (int i = tid; i < NQ * P; i += blockDim.x) {
     Bs[i] = prm.b.B[i / P][i % P];
@@ -619,7 +626,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
       for (int j = tq; j < ND2; j += NQD) {
         const float* fk = A.FK + el * (DIM * ND1 * ND2);
         double s = 0.0;
-        for (int ci = 0; ci < DIM * ND1; ++ci) s += (double)fk[ci * ND2 + j] * ws[ci];
+        for (int ci = 0; ci < DIM * ND1; ++ci) s = fma(f2d_exact(fk[ci * ND2 + j]), ws[ci], s);
         ftv[j] = s;
       }
   } else {
@@ -752,17 +759,19 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
         }
     }
   }
+  if (active && tq == 0) crs[0] = coef / prm.rho0K[el];
   __syncthreads();
   if (active)
     for (int j = tq; j < ND2; j += NQD) {
       // M_E,K^{-1} = Mref^{-1} / (rho0 |J0|)_K, applied to F^T w + src
       double s = 0.0;
       for (int l = 0; l < ND2; ++l) {
-        double rhs = ftv[l] + (A.srcE ? A.srcE[el * ND2 + l] : 0.0) +
-                     (A.prefE ? A.prefE[el * ND2 + l] : 0.0);
-        s += Mi[j * ND2 + l] * rhs;
+        double rhs = ftv[l];
+        if (A.srcE) rhs += A.srcE[el * ND2 + l];
+        if (A.prefE) rhs += A.prefE[el * ND2 + l];
+        s = fma(Mi[j * ND2 + l], rhs, s);
       }
-      A.e_out[el * ND2 + j] = A.e_base[el * ND2 + j] + coef * s / prm.rho0K[el];
+      A.e_out[el * ND2 + j] = fma(crs[0], s, A.e_base[el * ND2 + j]);
     }
 }
 

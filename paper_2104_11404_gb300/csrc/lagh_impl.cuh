@@ -52,12 +52,24 @@ struct Geom {
   double J0inv[3]; // diagonal of the initial Jacobian inverse (Cartesian mesh)
   double ell0;     // initial length scale |K_0|^{1/d} / k
   double detJ0;    // |K_0|
+  float J0invf[3]; // FP32 copies for the FP32 path (rounded once on the host)
+  float ell0f;
 };
 
 struct Phys {
   double gamma, cfl, cfl_mu, q1, q2;
   int visc, source, problem;
+  float gammaf, cflf, cfl_muf, q1f, q2f;  // FP32 copies (set_phys_floats)
 };
+
+// Fills the FP32 copies of the constants of ph.
+inline void set_phys_floats(Phys& ph) {
+  ph.gammaf = (float)ph.gamma;
+  ph.cflf = (float)ph.cfl;
+  ph.cfl_muf = (float)ph.cfl_mu;
+  ph.q1f = (float)ph.q1;
+  ph.q2f = (float)ph.q2;
+}
 
 // Device control block of the time loop (one per context).
 struct Ctl {

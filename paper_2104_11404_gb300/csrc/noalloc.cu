@@ -51,44 +51,21 @@ extern "C" lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_des
                                      const lh_phys_desc* phys, const double* v, const double* e,
                                      const double* x, double* F1, double* dt_est, void* stream) {
   if (!mesh || !disc || !phys || !v || !e || !x || !F1) return LH_EINVAL;
-  const int d = mesh->dim;
-  if (d != 2 && d != 3) return LH_EINVAL;
-  const int k = disc->order;
-  if (k < 1 || k > 3 || (d == 3 && k > 2) || disc->nq != 2 * k) return LH_EUNSUPPORTED;
-  if (!(phys->gamma > 1.0) || phys->problem < LH_SEDOV || phys->problem > LH_UNIFORM)
-    return LH_EINVAL;
-  int nel[3] = {mesh->nx, mesh->ny, d == 3 ? mesh->nz : 1};
-  for (int i = 0; i < d; ++i)
-    if (nel[i] < 1 || !(mesh->hi[i] > mesh->lo[i])) return LH_EINVAL;
-
   // geometry of the Cartesian box (the same quantities lh_create derives)
   lh_ctx c;
   memset(&c.g, 0, sizeof(c.g));
   memset(&c.a, 0, sizeof(c.a));
-  Geom& g = c.g;
-  g.dim = d;
-  g.k = k;
-  g.nq = disc->nq;
-  g.nnodes = 1;
-  g.nelem = 1;
-  double vol = 1.0;
-  for (int i = 0; i < 3; ++i) {
-    g.n[i] = i < d ? nel[i] : 1;
-    g.nn[i] = i < d ? nel[i] * k + 1 : 1;
-    g.nnodes *= g.nn[i];
-    g.nelem *= g.n[i];
-    const double h = i < d ? (mesh->hi[i] - mesh->lo[i]) / nel[i] : 1.0;
-    if (i < d) vol *= h;
-    g.lo[i] = i < d ? mesh->lo[i] : 0.0;
-    g.h[i] = h;
-    g.J0inv[i] = 1.0 / h;
+  {
+    lh_status gs = make_geom(mesh, disc, &c.g, nullptr);
+    if (gs != LH_OK) return gs;
   }
+  if (!(phys->gamma > 1.0) || phys->problem < LH_SEDOV || phys->problem > LH_UNIFORM)
+    return LH_EINVAL;
+  const Geom& g = c.g;
+  const int d = g.dim, k = g.k;
   int nd1 = 1;
   for (int i = 0; i < d; ++i) nd1 *= k + 1;
-  g.nv = (int64_t)d * g.nnodes;
-  g.ne = g.nelem * (d == 2 ? k * k : k * k * k);
-  g.detJ0 = vol;
-  g.ell0 = pow(vol, 1.0 / d) / k;
+  const double vol = g.detJ0;
   // the array must hold the per-element quadrature data and the element rows
   if (16 + g.nelem * (1 + (int64_t)d * nd1) > kStaticScratchDoubles) return LH_ETOOLARGE;
 
@@ -100,6 +77,7 @@ extern "C" lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_des
   c.ph.visc = phys->visc;
   c.ph.problem = phys->problem;
   c.ph.source = 0;
+  set_phys_floats(c.ph);
   c.precision = LH_FP64;
   build_basis(k, g.nq, d, &c.basis);
 

@@ -149,6 +149,15 @@ __device__ __forceinline__ T sigma_min_of(const T (&J)[DIM][DIM], T detJ) {
   }
 }
 
+// A physical constant in the working precision: the FP64 value, or its FP32
+// copy rounded once on the host (no conversion per point).
+template <typename T>
+__device__ __forceinline__ T pconst(double d, float f);
+template <>
+__device__ __forceinline__ double pconst<double>(double d, float) { return d; }
+template <>
+__device__ __forceinline__ float pconst<float>(double, float f) { return f; }
+
 // Stress and time-step estimate at one point.  J, Gv: reference gradients
 // (row = component, column = reference direction).  p_ref: a constant
 // reference pressure taken out of the returned stress (sigma + p_ref I is
@@ -159,7 +168,7 @@ __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&
                                               T e_q, T rho0K, const Phys& ph,
                                               const T (&J0inv)[DIM], T ell0, T kinv, T p_ref,
                                               T (&sigma)[DIM][DIM], T& tau) {
-  const T gam = (T)ph.gamma;
+  const T gam = pconst<T>(ph.gamma, ph.gammaf);
   T detJ = det_of<T, DIM>(J);
   for (int c = 0; c < DIM; ++c)
     for (int n = 0; n < DIM; ++n) sigma[c][n] = T(0);
@@ -194,13 +203,13 @@ __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&
         n2 += dc * dc;
       }
       T ell = ell0 * t_sqrt(n2);
-      mu = rho * ((T)ph.q2 * ell * ell * (-lam) + (T)ph.q1 * ell * cs);
+      mu = rho * (pconst<T>(ph.q2, ph.q2f) * ell * ell * (-lam) + pconst<T>(ph.q1, ph.q1f) * ell * cs);
       for (int c = 0; c < DIM; ++c)
         for (int n = 0; n < DIM; ++n) sigma[c][n] += mu * eps[c][n];
     }
   }
-  T inv = cs / hmin + (T)ph.cfl_mu * mu / (rho * hmin * hmin);
-  tau = inv > T(0) ? (T)ph.cfl / inv : t_inf<T>();
+  T inv = cs / hmin + pconst<T>(ph.cfl_mu, ph.cfl_muf) * mu / (rho * hmin * hmin);
+  tau = inv > T(0) ? pconst<T>(ph.cfl, ph.cflf) / inv : t_inf<T>();
   return 0;
 }
 

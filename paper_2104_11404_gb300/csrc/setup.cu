@@ -227,6 +227,8 @@ lh_status lagh::make_geom(const lh_mesh_desc* mesh, const lh_disc_desc* disc, Ge
   g.ne = g.nelem * nd2;
   g.detJ0 = vol;
   g.ell0 = pow(vol, 1.0 / d) / k;
+  for (int i = 0; i < 3; ++i) g.J0invf[i] = (float)g.J0inv[i];
+  g.ell0f = (float)g.ell0;
   if (g.nelem > (int64_t)1 << 31) return bad(LH_EINVAL, "mesh too large");
   *out = g;
   return LH_OK;
@@ -388,6 +390,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   ph.visc = phys->visc;
   ph.problem = phys->problem;
   ph.source = (phys->source && phys->problem == LH_TAYLOR_GREEN && d == 2) ? 1 : 0;
+  set_phys_floats(ph);
   c->cg_rtol = phys->cg_rtol;
   c->cg_maxit = phys->cg_maxit;
   build_basis(k, g.nq, d, &c->basis);

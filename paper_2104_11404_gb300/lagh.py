@@ -28,6 +28,7 @@ API_NAMES = [
     "lh_batch_layout", "lh_batch_init_state", "lh_batch_set_state", "lh_batch_get_state",
     "lh_batch_query", "lh_batch_run_to", "lh_batch_step_fixed", "lh_batch_total_energy",
     "lh_batch_force_sampled", "lh_batch_autotune", "lh_batch_tuning_get",
+    "lh_check_conversions",
 ]
 
 
@@ -143,6 +144,7 @@ def load():
     L.lh_batch_force_sampled.argtypes = [_vp, _vp, _vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.lh_batch_autotune.argtypes = [_vp, ctypes.c_int32, P(lh_batch_tuning)]
     L.lh_batch_tuning_get.argtypes = [_vp, P(lh_batch_tuning)]
+    L.lh_check_conversions.argtypes = [_dp, ctypes.c_int64, _vp, _dp, _vp]
     for name in API_NAMES:
         if name not in ("lh_default_phys", "lh_status_string", "lh_last_error",
                         "lh_batch_last_error"):
@@ -392,3 +394,9 @@ def lh_batch_tuning_get(b):
     t = lh_batch_tuning()
     _bcheck(b, load().lh_batch_tuning_get(b, ctypes.byref(t)))
     return t
+
+
+def lh_check_conversions(inp, f_out, d_out, stream=None):
+    st = load().lh_check_conversions(_ptr(inp), int(inp.numel()), _ptr(f_out), _ptr(d_out), stream)
+    if st != LH_OK:
+        raise LaghError(st, "lh_check_conversions failed")

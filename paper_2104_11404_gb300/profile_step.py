@@ -3,6 +3,12 @@ one by one, for kernel profilers (ncu cannot see kernels inside CUDA graphs
 that contain conditional nodes, which is how the library normally runs).
 
     python -m paper_2104_11404_gb300.profile_step --workload tg2d_64 --precision mixed --steps 5
+    python -m paper_2104_11404_gb300.profile_step --batch --steps 2 --tuning 1024,1,1
+
+--batch runs the 512-instance point-blast sweep through the batched form
+instead (its attempt graph holds kernel nodes only, so profilers see them);
+--tuning threads,ctas_per_sm,smem_lines fixes the launch shape (no autotuner
+launches before the profiled ones).
 """
 import argparse
 import json
@@ -17,7 +23,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--graph", action="store_true", help="keep the CUDA graph launches")
+    ap.add_argument("--batch", action="store_true", help="the batched point-blast sweep")
+    ap.add_argument("--instances", type=int, default=512)
+    ap.add_argument("--tuning", default="", help="threads,ctas_per_sm,smem_lines")
     args = ap.parse_args()
+    if args.batch:
+        return run_batch(args)
     import torch
 
     from . import build as libbuild
@@ -34,6 +45,30 @@ def main():
     st = g.run_to(cfg["t_final"], max_steps=args.steps)
     print(json.dumps({"workload": args.workload, "precision": args.precision, **st}))
     g.close()
+
+
+def run_batch(args):
+    import torch
+
+    from . import build as libbuild
+    from . import workloads as W
+    from .batch import Batch
+    libbuild.build()
+    torch.cuda.set_device(0)
+    tuning = None
+    if args.tuning:
+        t, c, sl = (int(v) for v in args.tuning.split(","))
+        tuning = dict(threads=t, ctas_per_sm=c, smem_lines=sl)
+    b = Batch(W.batch_instances(args.instances), precision=args.precision, tuning=tuning)
+    b.init_state()
+    if tuning is None:
+        b.autotune()
+    if args.warmup:
+        b.run_to(0.8, max_steps=args.warmup)
+    st = b.run_to(0.8, max_steps=args.steps)
+    print(json.dumps({"batch": args.instances, "precision": args.precision, "tuning": b.tuning(),
+                      **st}))
+    b.close()
 
 
 if __name__ == "__main__":

@@ -284,3 +284,39 @@ def test_invalid_descriptors():
     with pytest.raises(lagh.LaghError) as ei:
         gpu_for(cfg)
     assert ei.value.status == lagh.LH_EINVAL
+
+
+def test_integer_pipe_conversions_match_ieee_casts():
+    """The FP32 paths convert with integer operations; they must equal the
+    IEEE 754 casts bit for bit (nearest-even rounding to FP32 in its normal
+    range, exact widening back to FP64)."""
+    from paper_2104_11404_gb300 import lagh
+    rng = np.random.default_rng(2)
+    vals = [0.0, -0.0, 1.0, -1.0, 0.1, 1.0 / 3.0, np.pi, 1e-30, -1e30, 3.4028234663852886e38,
+            3.4028235677973366e38, 1e39, -1e39, np.inf, -np.inf, 1.1754943508222875e-38,
+            1e-40, 5e-324, 2.2250738585072014e-308]
+    # ties and the carry into the exponent: 1 + (2k+1) 2^-24 and (2 - 2^-24)
+    vals += [1.0 + (2 * k + 1) * 2.0 ** -24 for k in range(8)]
+    vals += [2.0 - 2.0 ** -24, 2.0 - 2.0 ** -25, 1.0 + 2.0 ** -24 + 2.0 ** -60]
+    vals += list(rng.normal(size=2000) * 10.0 ** rng.integers(-30, 30, size=2000))
+    vals += list(rng.uniform(-1, 1, size=2000))
+    a = np.array(vals, dtype=np.float64)
+    f = torch.empty(len(a), dtype=torch.float32, device="cuda")
+    d = torch.empty(len(a), dtype=torch.float64, device="cuda")
+    lagh.lh_check_conversions(dev(a), f, d)
+    torch.cuda.synchronize()
+    fh, dh = host(f), host(d)
+    with np.errstate(over="ignore"):
+        ref = a.astype(np.float32)
+    normal = (np.abs(ref) >= np.finfo(np.float32).tiny) | ~np.isfinite(ref)
+    assert np.array_equal(fh[normal].view(np.uint32), ref[normal].view(np.uint32))
+    # below the normal range: signed zero
+    assert np.all(fh[~normal] == 0.0)
+    assert np.array_equal(np.signbit(fh[~normal]), np.signbit(a[~normal]))
+    # widening is exact
+    assert np.array_equal(dh.view(np.uint64), fh.astype(np.float64).view(np.uint64))
+    nan = torch.tensor([np.nan], dtype=torch.float64, device="cuda")
+    f1 = torch.empty(1, dtype=torch.float32, device="cuda")
+    d1 = torch.empty(1, dtype=torch.float64, device="cuda")
+    lagh.lh_check_conversions(nan, f1, d1)
+    assert np.isnan(host(f1)[0]) and np.isnan(host(d1)[0])
