@@ -165,9 +165,11 @@ typedef struct lh_batch_stats {
 /* Launch shape of the batched kernels.  threads: 256, 512 or 1024 (2D only)
  * threads per CTA; with one thread per quadrature point, the force and energy
  * tiles hold threads / nq^dim elements and the mass tiles threads /
- * (dim (k+1)^dim).  ctas_per_sm: 0 = as many as fit.  smem_lines: 1 = the
- * node lines of the velocity solve are staged in shared memory (needs
- * 8 x nodes of the largest instance), 0 = solved in place in device memory. */
+ * (dim (k+1)^dim).  ctas_per_sm: 0 = as many as fit.  smem_lines: where the
+ * node-line solves of the velocity CG run: 2 = every component staged in
+ * shared memory and solved together (needs 8 x dim x nodes of the largest
+ * instance), 1 = one component at a time (8 x nodes), 0 = in place in device
+ * memory. */
 typedef struct lh_batch_tuning {
   int32_t threads;
   int32_t ctas_per_sm;

@@ -48,6 +48,7 @@ struct lh_batch {
   double *v = nullptr, *e = nullptr, *x = nullptr, *vh = nullptr, *eh = nullptr, *xh = nullptr;
   double *vn = nullptr, *en = nullptr, *xn = nullptr, *vbar = nullptr;
   double* rho0K = nullptr;
+  double* rho0Kinv = nullptr;
   double* fac = nullptr;
   double* F1E = nullptr;
   float* FK = nullptr;
@@ -96,6 +97,7 @@ static BatchArgs bargs(const lh_batch* b) {
   a.vn = b->vn; a.en = b->en; a.xn = b->xn;
   a.vbar = b->vbar;
   a.rho0K = b->rho0K;
+  a.rho0Kinv = b->rho0Kinv;
   a.fac = b->fac;
   a.F1E = b->F1E;
   a.FK = b->FK;
@@ -312,7 +314,7 @@ static lh_status run_loop(lh_batch* b, int64_t max_attempts, int64_t first_batch
 
 static void free_batch(lh_batch* b) {
   void* ptrs[] = {b->d_inst, b->d_order, b->d_ctl, b->v, b->e, b->x, b->vh, b->eh, b->xh,
-                  b->vn, b->en, b->xn, b->vbar, b->rho0K, b->fac, b->F1E, b->FK, b->D,
+                  b->vn, b->en, b->xn, b->vbar, b->rho0K, b->rho0Kinv, b->fac, b->F1E, b->FK, b->D,
                   b->srcE, b->vec, b->aux, b->qctr, b->ndone};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -464,6 +466,7 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
   for (double** p : ee)
     if (e == cudaSuccess) e = balloc(p, b->tot_e);
   if (e == cudaSuccess) e = balloc(&b->rho0K, b->tot_el);
+  if (e == cudaSuccess) e = balloc(&b->rho0Kinv, b->tot_el);
   if (e == cudaSuccess) e = balloc(&b->fac, fac.size());
   if (e == cudaSuccess) e = balloc(&b->F1E, slots * b->s_f1e);
   if (precision == LH_MIXED) {
@@ -493,15 +496,19 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
     cudaGetLastError();
     return fail(oom ? LH_ENOMEM : LH_ECUDA, cudaGetErrorString(e));
   }
-  std::vector<double> r0(b->tot_el);
+  std::vector<double> r0(b->tot_el), r0i(b->tot_el);
   for (int i = 0; i < n; ++i)
-    for (int64_t el = 0; el < b->inst[i].g.nelem; ++el) r0[b->inst[i].oel + el] = b->inst[i].rho0K;
+    for (int64_t el = 0; el < b->inst[i].g.nelem; ++el) {
+      r0[b->inst[i].oel + el] = b->inst[i].rho0K;
+      r0i[b->inst[i].oel + el] = b->inst[i].scale;
+    }
   std::vector<Ctl> c0(n);
   memset(c0.data(), 0, sizeof(Ctl) * n);
   e = cudaMemcpy(b->d_inst, b->inst.data(), sizeof(BInst) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_order, order.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->d_ctl, c0.data(), sizeof(Ctl) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(b->rho0K, r0.data(), sizeof(double) * b->tot_el, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(b->rho0Kinv, r0i.data(), sizeof(double) * b->tot_el, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !fac.empty())
     e = cudaMemcpy(b->fac, fac.data(), sizeof(double) * fac.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(b->qctr, 0, 8 * sizeof(unsigned int));
@@ -515,13 +522,14 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
     t = *tuning;
     b->tuned = 1;
   } else {
-    t.threads = 512;
+    t.threads = 1024;
     t.ctas_per_sm = 0;
-    t.smem_lines = 1;
+    t.smem_lines = 2;
   }
   lh_status st = apply_tuning(b, t);
-  if (st != LH_OK && !(tuning && tuning->threads > 0)) {
-    t.smem_lines = 0;  // largest instance's node lines do not fit: solve in place
+  // the largest instance's node lines do not fit: fewer in shared memory
+  while (st != LH_OK && !(tuning && tuning->threads > 0) && t.smem_lines > 0) {
+    --t.smem_lines;
     st = apply_tuning(b, t);
   }
   if (st != LH_OK) return fail(st, b->err);
@@ -762,7 +770,7 @@ extern "C" lh_status lh_batch_autotune(lh_batch* b, int32_t reps, lh_batch_tunin
   float best = 1e30f;
   lh_batch_tuning best_t = keep;
   for (int ti = 0; ti < 3; ++ti)
-    for (int sl = 1; sl >= 0; --sl)
+    for (int sl = 2; sl >= 0; --sl)
       for (int cps = 1; cps <= 4; ++cps) {
         lh_batch_tuning t;
         memset(&t, 0, sizeof(t));

@@ -44,6 +44,7 @@ struct BatchArgs {
   Ctl* ctl;              // one control block per instance
   double *v, *e, *x, *vh, *eh, *xh, *vn, *en, *xn, *vbar;
   const double* rho0K;   // per element (packed by oel)
+  const double* rho0Kinv;
   const double* fac;     // row i of a table: 1 / L_ii, L_{i,i-1}, ..., L_{i,i-k}
   double* F1E;           // element rows of F.1, then of M p (CG)
   float* FK;             // mixed: element force matrices
@@ -107,72 +108,82 @@ __device__ __forceinline__ void load_instance(const BatchArgs& a, int i, BInst* 
   __syncthreads();
 }
 
+// Forward and backward substitution along one node line of w (m entries,
+// stride apart): w <- (L L^T)^-1 w with the banded Cholesky factor F of the
+// assembled 1D matrix (row i: 1 / L_ii, L_{i,i-1}, ..., L_{i,i-K}).
+template <int K>
+__device__ __forceinline__ void line_solve(double* L, int64_t stride, int m,
+                                           const double* __restrict__ F) {
+  double win[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) win[q] = 0.0;
+  for (int i = 0; i < m; ++i) {  // y_i = (b_i - sum_q L_{i,i-q} y_{i-q}) / L_ii
+    const double* Fi = F + (int64_t)i * (K + 1);
+    double s = L[i * stride];
+#pragma unroll
+    for (int q = 1; q <= K; ++q) s -= Fi[q] * win[q - 1];
+    s *= Fi[0];
+#pragma unroll
+    for (int q = K - 1; q > 0; --q) win[q] = win[q - 1];
+    win[0] = s;
+    L[i * stride] = s;
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) win[q] = 0.0;
+  for (int i = m - 1; i >= 0; --i) {  // x_i = (y_i - sum_q L_{i+q,i} x_{i+q}) / L_ii
+    double s = L[i * stride];
+#pragma unroll
+    for (int q = 1; q <= K; ++q)
+      if (i + q < m) s -= F[(int64_t)(i + q) * (K + 1) + q] * win[q - 1];
+    s *= F[(int64_t)i * (K + 1)];
+#pragma unroll
+    for (int q = K - 1; q > 0; --q) win[q] = win[q - 1];
+    win[0] = s;
+    L[i * stride] = s;
+  }
+}
+
 // z_c = scale (G^-1 (x) ... (x) G^-1) r_c on the free entries of component c
-// (zero on its wall-normal nodes), for every component, by forward and
-// backward substitution along each node line.  buf: nnodes doubles of shared
-// memory, or NULL to work in place on z.
+// (zero on its wall-normal nodes) for every component: the 1D solves along
+// each direction in turn, every node line independent.  mode 2: all
+// components staged in buf (DIM nnodes doubles of shared memory) and solved
+// together; mode 1: one component at a time in buf (nnodes doubles); mode 0:
+// in place on z in device memory.
 template <int DIM, int K>
 __device__ void tensor_solve(const Geom& g, const double* __restrict__ fac,
                              const int64_t (*fo)[2], double scale, const double* r, double* z,
-                             double* buf) {
+                             double* buf, int mode) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t nn = g.nnodes;
-  for (int c = 0; c < DIM; ++c) {
-    const double* rc = r + c * nn;
-    double* zc = z + c * nn;
-    double* w = buf ? buf : zc;
-    for (int64_t node = tid; node < nn; node += nt) {
+  const int cpass = mode == 2 ? DIM : 1;  // components per pass
+  for (int c0 = 0; c0 < DIM; c0 += cpass) {
+    double* w = mode == 0 ? z + c0 * nn : buf;  // holds components c0 .. c0 + cpass - 1
+    for (int64_t idx = tid; idx < cpass * nn; idx += nt) {
+      const int c = c0 + (int)(idx / nn);
+      const int64_t node = idx - (int64_t)(c - c0) * nn;
       int I[3];
       node_ijk(g, node, I);
-      w[node] = (I[c] == 0 || I[c] == g.nn[c] - 1) ? 0.0 : rc[node];
+      w[idx] = (I[c] == 0 || I[c] == g.nn[c] - 1) ? 0.0 : r[c * nn + node];
     }
     __syncthreads();
     for (int d = 0; d < DIM; ++d) {
-      const int var = (d == c) ? 1 : 0;
-      const double* F = fac + fo[d][var];
-      const int m = g.nn[d] - 2 * var;
       const int64_t nlines = nn / g.nn[d];
       const int64_t stride = d == 0 ? 1 : (d == 1 ? (int64_t)g.nn[0] : (int64_t)g.nn[0] * g.nn[1]);
-      for (int64_t line = tid; line < nlines; line += nt) {
+      for (int64_t li = tid; li < cpass * nlines; li += nt) {
+        const int c = c0 + (int)(li / nlines);
+        const int64_t line = li - (int64_t)(c - c0) * nlines;
+        const int var = (d == c) ? 1 : 0;
         int I[3] = {0, 0, 0};
         if (d == 0) { I[1] = (int)(line % g.nn[1]); I[2] = (int)(line / g.nn[1]); }
         else if (d == 1) { I[0] = (int)(line % g.nn[0]); I[2] = (int)(line / g.nn[0]); }
         else { I[0] = (int)(line % g.nn[0]); I[1] = (int)(line / g.nn[0]); }
         if (d != c && (I[c] == 0 || I[c] == g.nn[c] - 1)) continue;  // essential line
-        double* L = w + node_index(g, I[0], I[1], I[2]) + var * stride;
-        double win[K];
-#pragma unroll
-        for (int q = 0; q < K; ++q) win[q] = 0.0;
-        // forward: y_i = (b_i - sum_q L_{i,i-q} y_{i-q}) / L_ii
-        for (int i = 0; i < m; ++i) {
-          const double* Fi = F + (int64_t)i * (K + 1);
-          double s = L[i * stride];
-#pragma unroll
-          for (int q = 1; q <= K; ++q) s -= Fi[q] * win[q - 1];
-          s *= Fi[0];
-#pragma unroll
-          for (int q = K - 1; q > 0; --q) win[q] = win[q - 1];
-          win[0] = s;
-          L[i * stride] = s;
-        }
-#pragma unroll
-        for (int q = 0; q < K; ++q) win[q] = 0.0;
-        // backward: x_i = (y_i - sum_q L_{i+q,i} x_{i+q}) / L_ii
-        for (int i = m - 1; i >= 0; --i) {
-          double s = L[i * stride];
-#pragma unroll
-          for (int q = 1; q <= K; ++q)
-            if (i + q < m) s -= F[(int64_t)(i + q) * (K + 1) + q] * win[q - 1];
-          s *= F[(int64_t)i * (K + 1)];
-#pragma unroll
-          for (int q = K - 1; q > 0; --q) win[q] = win[q - 1];
-          win[0] = s;
-          L[i * stride] = s;
-        }
+        line_solve<K>(w + (int64_t)(c - c0) * nn + node_index(g, I[0], I[1], I[2]) + var * stride,
+                      stride, g.nn[d] - 2 * var, fac + fo[d][var]);
       }
       __syncthreads();
     }
-    for (int64_t node = tid; node < nn; node += nt) zc[node] = scale * w[node];
+    for (int64_t idx = tid; idx < cpass * nn; idx += nt) z[c0 * nn + idx] = scale * w[idx];
     __syncthreads();
   }
 }
@@ -188,9 +199,11 @@ struct BL {
   static constexpr size_t B_MASS = (size_t)(3 * CGT * DIM * ND1 + P * P) * sizeof(double);
   static constexpr size_t B_FIXED = F::BYTES > E::BYTES ? (F::BYTES > B_MASS ? F::BYTES : B_MASS)
                                                         : (E::BYTES > B_MASS ? E::BYTES : B_MASS);
-  // bytes with the line buffer of nnodes doubles after the mass tile
+  // bytes with the line buffer after the mass tile: DIM (smem_lines = 2), one
+  // (1) or no (0) components of nnodes doubles
   static size_t bytes(int64_t nnodes_max, int smem_lines) {
-    size_t cg = B_MASS + (smem_lines ? (size_t)nnodes_max * sizeof(double) : 0);
+    const int comps = smem_lines == 2 ? DIM : (smem_lines == 1 ? 1 : 0);
+    size_t cg = B_MASS + (size_t)comps * nnodes_max * sizeof(double);
     return cg > B_FIXED ? cg : B_FIXED;
   }
 };
@@ -225,7 +238,7 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
     *conv = true;
     return 0;
   }
-  tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines);
+  tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines, a.smem_lines);
   double rz = 0.0;
   for (int64_t k = tid; k < nv; k += NTT) {
     const double zv = Z[k];
@@ -266,7 +279,7 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
     rr = cta_sum(lrr);
     ok = rr <= a.rtol * a.rtol * bb;
     if (ok || !(rr == rr) || it >= a.maxit) break;
-    tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines);
+    tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines, a.smem_lines);
     double lrz = 0.0;
     for (int64_t k = tid; k < nv; k += NTT) lrz += R[k] * Z[k];
     const double rz_new = cta_sum(lrz);
@@ -327,10 +340,11 @@ __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, con
     fa.tau_bits = &s_tau;
     fa.status = &s_status;
     fa.mode = kForceFull;
-    for (int64_t el0 = 0; el0 < g.nelem; el0 += F::EPB) {
+    force_tables<DIM, K, MIXED, NTT>(bas, smem);
+    __syncthreads();
+    for (int64_t el0 = 0; el0 < g.nelem; el0 += F::EPB)
       force_tile<DIM, K, MIXED, NTT>(g, sI.ph, bas, fa, rho0K, smem, el0);
-      __syncthreads();
-    }
+    __syncthreads();
     if (tid == 0) {
       ctl->tau_bits[stage] = s_tau;
       ctl->status |= s_status;
@@ -396,10 +410,12 @@ __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, con
     ea.frac = stage == 0 ? 0.5 : 1.0;
     ea.dt = dt;
     ea.ctl = nullptr;
-    for (int64_t el0 = 0; el0 < g.nelem; el0 += E::EPB) {
+    ea.rho0Kinv = a.rho0Kinv + sI.oel;
+    energy_tables<DIM, K, MIXED, NTT>(bas, smem);
+    __syncthreads();
+    for (int64_t el0 = 0; el0 < g.nelem; el0 += E::EPB)
       energy_tile<DIM, K, MIXED, NTT>(g, bas, ea, rho0K, smem, el0);
-      __syncthreads();
-    }
+    __syncthreads();
     if (stage == 0) continue;
     // ---- step control and commit ----
     if (tid == 0) {
@@ -435,6 +451,7 @@ __global__ void __launch_bounds__(NTT) batch_estimate_kernel(const BatchArgs a, 
   __shared__ unsigned long long s_tau;
   __shared__ int s_status;
   double* F1E = a.F1E + (int64_t)blockIdx.x * a.s_f1e;
+  force_tables<DIM, K, MIXED, NTT>(bas, smem);  // next_instance synchronises
   for (int i = next_instance(a, kQAux); i >= 0; i = next_instance(a, kQAux)) {
     if (threadIdx.x == 0) {
       s_tau = kInfBits;
@@ -449,10 +466,9 @@ __global__ void __launch_bounds__(NTT) batch_estimate_kernel(const BatchArgs a, 
     fa.tau_bits = &s_tau;
     fa.status = &s_status;
     fa.mode = kForceFull;
-    for (int64_t el0 = 0; el0 < g.nelem; el0 += F::EPB) {
+    for (int64_t el0 = 0; el0 < g.nelem; el0 += F::EPB)
       force_tile<DIM, K, MIXED, NTT>(g, sI.ph, bas, fa, a.rho0K + sI.oel, smem, el0);
-      __syncthreads();
-    }
+    __syncthreads();
     if (threadIdx.x == 0) {
       reinterpret_cast<unsigned long long*>(a.out)[i] = s_tau;
       a.ctl[i].status |= (s_status & kDevNonFinite);
@@ -473,6 +489,7 @@ __global__ void __launch_bounds__(NTT) batch_sampled_kernel(const BatchArgs a, c
   __shared__ BInst sI;
   __shared__ unsigned long long s_tau;
   __shared__ int s_status;
+  force_tables<DIM, K, MIXED, NTT>(bas, smem);  // next_instance synchronises
   for (int i = next_instance(a, kQAux); i >= 0; i = next_instance(a, kQAux)) {
     if (threadIdx.x == 0) {
       s_tau = kInfBits;
@@ -491,10 +508,9 @@ __global__ void __launch_bounds__(NTT) batch_sampled_kernel(const BatchArgs a, c
     fa.tau_bits = &s_tau;
     fa.status = &s_status;
     fa.mode = kForceFull;
-    for (int64_t s0 = 0; s0 < cnt; s0 += F::EPB) {
+    for (int64_t s0 = 0; s0 < cnt; s0 += F::EPB)
       force_tile<DIM, K, MIXED, NTT>(g, sI.ph, bas, fa, a.rho0K + sI.oel, smem, s0);
-      __syncthreads();
-    }
+    __syncthreads();
     if (threadIdx.x == 0) est[i] = (s_status & kDevTangled) ? 0ull : s_tau;
   }
 }

@@ -70,6 +70,60 @@ __device__ __forceinline__ double tg_source(double X, double Y, double gam) {
          (cos(3.0 * pi * X) * cos(pi * Y) - cos(pi * X) * cos(3.0 * pi * Y));
 }
 
+// Synchronisation of one element's team.  A team of at most 32 threads that
+// divides 32 lies inside one warp, so a warp barrier orders its shared-memory
+// traffic and the warps of the block run their elements independently;
+// larger teams use the block barrier.
+template <int TEAM>
+__device__ __forceinline__ void team_sync() {
+  if constexpr (TEAM <= 32 && 32 % TEAM == 0) __syncwarp();
+  else __syncthreads();
+}
+
+// Minimum of v over the tile into *dst (ordered bits): one atomicMin per warp
+// when the block is made of whole warps, else through a shared-memory tree.
+template <int NTT>
+__device__ __forceinline__ void tile_min_to(unsigned long long v, unsigned long long* sh,
+                                            unsigned long long* dst) {
+  if constexpr (NTT % 32 == 0) {
+    v = warp_min_u64(v);
+    if ((threadIdx.x & 31) == 0) atomicMin(dst, v);
+  } else {
+    block_min_to(v, sh, dst);
+  }
+}
+
+// Basis tables of the force tiles, written once into the front of the shared
+// buffer (the caller synchronises the block before the first tile).
+template <int DIM, int K, bool MIXED, int NTT>
+__device__ __forceinline__ void force_tables(const Basis1D& bas, unsigned char* smem) {
+  using F = FL<DIM, K, MIXED, NTT>;
+  using T = typename F::T;
+  constexpr int P = F::P, NQ = F::NQ;
+  unsigned char* sp = smem;
+  T* Bs = reinterpret_cast<T*>(sp); sp += F::al(NQ * P * sizeof(T));
+  T* Gs = reinterpret_cast<T*>(sp); sp += F::al(NQ * P * sizeof(T));
+  T* Ls = reinterpret_cast<T*>(sp); sp += F::al(NQ * K * sizeof(T));
+  double* Ld = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * sizeof(double));
+  double* Wd = reinterpret_cast<double*>(sp); sp += F::al(NQ * sizeof(double));
+  T* Wt = reinterpret_cast<T*>(sp);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NQ * P; i += blockDim.x) {
+    int q = i / P, a = i - q * P;
+    Bs[i] = tab<T>(bas.B[q][a], bas.Bf[q][a]);
+    Gs[i] = tab<T>(bas.G[q][a], bas.Gf[q][a]);
+  }
+  for (int i = tid; i < NQ * K; i += blockDim.x) {
+    int q = i / K, j = i - q * K;
+    Ls[i] = tab<T>(bas.L[q][j], bas.Lf[q][j]);
+    Ld[i] = bas.L[q][j];
+  }
+  for (int i = tid; i < NQ; i += blockDim.x) {
+    Wd[i] = bas.W[i];
+    Wt[i] = tab<T>(bas.W[i], bas.Wf[i]);
+  }
+}
+
 // One tile of EPB element slots [slot0, slot0 + EPB) of the force evaluation,
 // by all NTT threads of the block (the grid kernel below uses one tile per
 // block; the batched stage kernel loops over the tiles of an instance).
@@ -105,21 +159,6 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
   T* scr = reinterpret_cast<T*>(ep); ep += F::B_SCR;
   double* l2s = reinterpret_cast<double*>(ep);
 
-  for (int i = tid; i < NQ * P; i += blockDim.x) {
-    int q = i / P, a = i - q * P;
-    Bs[i] = tab<T>(prm.b.B[q][a], prm.b.Bf[q][a]);
-    Gs[i] = tab<T>(prm.b.G[q][a], prm.b.Gf[q][a]);
-  }
-  for (int i = tid; i < NQ * K; i += blockDim.x) {
-    int q = i / K, j = i - q * K;
-    Ls[i] = tab<T>(prm.b.L[q][j], prm.b.Lf[q][j]);
-    Ld[i] = prm.b.L[q][j];
-  }
-  for (int i = tid; i < NQ; i += blockDim.x) {
-    Wd[i] = prm.b.W[i];
-    Wt[i] = tab<T>(prm.b.W[i], prm.b.Wf[i]);
-  }
-
   const int64_t slot = slot0 + le;
   const bool active = le < F::EPB && slot < A.nslots;
   const int64_t el = active ? (A.list ? (int64_t)A.list[slot] : slot) : 0;
@@ -144,7 +183,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     }
     for (int j = tq; j < ND2; j += NQD) es[j] = from_double<T>(A.e[el * ND2 + j]);
   }
-  __syncthreads();
+  team_sync<NQD>();
 
   // ---- reference gradients at the quadrature points (sum factorisation) ----
   // fields f: [0, DIM) x, [DIM, 2 DIM) v, [2 DIM, 3 DIM) test vector (FP64 path)
@@ -172,7 +211,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         TB[(f * P + b) * NQ + x_] = sb;
         TG[(f * P + b) * NQ + x_] = sg;
       }
-    __syncthreads();
+    team_sync<NQD>();
     if (active)
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
@@ -208,7 +247,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         TB[r * NQ + x_] = sb;
         TG[r * NQ + x_] = sg;
       }
-    __syncthreads();
+    team_sync<NQD>();
     if (active)
       for (int w = tq; w < nf * P * NQ * NQ; w += NQD) {
         int x_ = w % NQ, y_ = (w / NQ) % NQ, fz = w / (NQ * NQ);
@@ -223,7 +262,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         PGB[w] = gb;
         PBG[w] = bg;
       }
-    __syncthreads();
+    team_sync<NQD>();
     if (active)
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
@@ -242,7 +281,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         if (f < DIM) xval[f] = vv;
       }
   }
-  __syncthreads();  // scratch is reused below
+  team_sync<NQD>();  // scratch is reused below
 
   // ---- quadrature-point physics ----
   double tau_q = t_inf<double>();
@@ -301,12 +340,9 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     }
   }
   // time-step estimate and error flags of the block
-  if (A.tau_bits != nullptr) {
-    unsigned long long* rsh = red;
-    block_min_to(tau_to_bits(tau_q), rsh, A.tau_bits);
-  }
+  if (A.tau_bits != nullptr) tile_min_to<NTT>(tau_to_bits(tau_q), red, A.tau_bits);
   if (flags && A.status != nullptr) atomicOr(A.status, flags);
-  __syncthreads();
+  team_sync<NQD>();
 
   // ---- transposed contractions ----
   if constexpr (!MIXED) {
@@ -323,7 +359,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
           for (int y_ = 0; y_ < NQ; ++y_) s += X[y_ * P + b] * dq[cm * NQD + y_ * NQ + x_];
           Y[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < DIM * ND1; w += NQD) {
           int c = w / ND1, i = w - c * ND1, a = i % P, b = i / P;
@@ -348,7 +384,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[z_ * P + cz] * dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
           Y[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < DIM * DIM * P * P * NQ; w += NQD) {
           int x_ = w % NQ, b = (w / NQ) % P, cz = (w / (NQ * P)) % P, cm = w / (NQ * P * P);
@@ -359,7 +395,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[y_ * P + b] * Y[((cm * P + cz) * NQ + y_) * NQ + x_];
           Z[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < DIM * ND1; w += NQD) {
           int c = w / ND1, i = w - c * ND1, a = i % P, b = (i / P) % P, cz = i / (P * P);
@@ -389,7 +425,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[y_ * P + b] * Ls[y_ * K + jy] * dq[cm * NQD + y_ * NQ + x_];
           Y[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < DIM * ND1 * ND2; w += NQD) {
           int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
@@ -415,7 +451,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[z_ * P + cz] * Ls[z_ * K + jz] * dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
           Y[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < DIM * DIM * PK * PK * NQ; w += NQD) {
           int x_ = w % NQ, uy = (w / NQ) % PK, uz = (w / (NQ * PK)) % PK, cm = w / (NQ * PK * PK);
@@ -426,7 +462,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[y_ * P + b] * Ls[y_ * K + jy] * Y[((cm * PK + uz) * NQ + y_) * NQ + x_];
           Z[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < DIM * ND1 * ND2; w += NQD) {
           int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
@@ -443,7 +479,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
           fk[w] = s;
         }
     }
-    __syncthreads();
+    team_sync<NQD>();
     if (active) {
       if (A.FK != nullptr)
         for (int w = tq; w < DIM * ND1 * ND2; w += NQD) A.FK[el * (DIM * ND1 * ND2) + w] = fk[w];
@@ -468,7 +504,7 @@ l2_part:
   const bool do_ftv = (!MIXED) && with_w;
   const bool do_src = (A.srcE != nullptr) && DIM == 2;
   if (do_ftv || do_src) {
-    __syncthreads();
+    team_sync<NQD>();
     // field 0: F^T w integrand, field 1: source integrand
     if constexpr (DIM == 2) {
       double* R1 = l2s;  // [2][K][NQ]
@@ -479,7 +515,7 @@ l2_part:
           for (int x_ = 0; x_ < NQ; ++x_) s += Ld[x_ * K + jx] * gq[fld * NQD + y_ * NQ + x_];
           R1[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < 2 * ND2; w += NQD) {
           int fld = w / ND2, j = w - fld * ND2, jx = j % K, jy = j / K;
@@ -500,7 +536,7 @@ l2_part:
             s += Ld[x_ * K + jx] * gq[fld * NQD + (z_ * NQ + y_) * NQ + x_];
           R1[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < 2 * K * K * NQ; w += NQD) {
           int z_ = w % NQ, jx = (w / NQ) % K, jy = (w / (NQ * K)) % K, fld = w / (NQ * K * K);
@@ -509,7 +545,7 @@ l2_part:
             s += Ld[y_ * K + jy] * R1[((fld * K + jx) * NQ + z_) * NQ + y_];
           R2[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < 2 * ND2; w += NQD) {
           int fld = w / ND2, j = w - fld * ND2, jx = j % K, jy = (j / K) % K, jz = j / (K * K);
@@ -522,6 +558,7 @@ l2_part:
         }
     }
   }
+  team_sync<NQD>();  // the team reuses its element area in the next tile
 }
 
 template <int DIM, int K, bool MIXED>
@@ -530,6 +567,8 @@ force_kernel(const ForceKParams prm) {
   using F = FL<DIM, K, MIXED>;
   if (prm.a.ctl != nullptr && prm.a.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  force_tables<DIM, K, MIXED, F::NT>(prm.b, smem);
+  __syncthreads();
   force_tile<DIM, K, MIXED, F::NT>(prm.g, prm.ph, prm.b, prm.a, prm.rho0K, smem,
                                    (int64_t)blockIdx.x * F::EPB);
 }
@@ -577,6 +616,26 @@ struct EnergyKParams {
   const double* rho0K;
 };
 
+// Basis tables of the energy tiles (written once; the caller synchronises).
+template <int DIM, int K, bool MIXED, int NTT>
+__device__ __forceinline__ void energy_tables(const Basis1D& bas, unsigned char* smem) {
+  using F = EL<DIM, K, MIXED, NTT>;
+  constexpr int P = F::P, NQ = F::NQ, ND2 = F::ND2;
+  unsigned char* sp = smem;
+  double* Bs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
+  double* Gs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
+  sp += F::al(NQ * P * 8);
+  double* Ls = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * 8);
+  double* Mi = reinterpret_cast<double*>(sp);
+  const int tid = threadIdx.x;
+  for (int i = tid; i < NQ * P; i += blockDim.x) {
+    Bs[i] = bas.B[i / P][i % P];
+    Gs[i] = bas.G[i / P][i % P];
+  }
+  for (int i = tid; i < NQ * K; i += blockDim.x) Ls[i] = bas.L[i / K][i % K];
+  for (int i = tid; i < ND2 * ND2; i += blockDim.x) Mi[i] = bas.MEinv[i];
+}
+
 // One tile of EPB elements [el0, el0 + EPB) of the energy update.
 template <int DIM, int K, bool MIXED, int NTT>
 __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, const EnergyArgs& A,
@@ -601,13 +660,6 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   double* ftv = reinterpret_cast<double*>(ep); ep += F::al(ND2 * 8);
   double* crs = reinterpret_cast<double*>(ep);  // coef / (rho0 |J0|) of the element
 
-  for (int i = tid; i < NQ * P; i += blockDim.x) {
-    Bs[i] = prm.b.B[i / P][i % P];
-    Gs[i] = prm.b.G[i / P][i % P];
-  }
-  for (int i = tid; i < NQ * K; i += blockDim.x) Ls[i] = prm.b.L[i / K][i % K];
-  for (int i = tid; i < ND2 * ND2; i += blockDim.x) Mi[i] = prm.b.MEinv[i];
-
   const int64_t el = el0 + le;
   const bool active = le < F::EPB && el < g.nelem;
   int E[3] = {0, 0, 0};
@@ -618,17 +670,29 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
       int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
       ws[w] = A.w[c * g.nnodes + elem_node<K>(g, E, a, b, cc)];
     }
-  __syncthreads();
+  team_sync<NQD>();
 
   if constexpr (MIXED) {
-    // F^T w from the stored FP32 element matrix, FP64 accumulation
-    if (active)
-      for (int j = tq; j < ND2; j += NQD) {
-        const float* fk = A.FK + el * (DIM * ND1 * ND2);
-        double s = 0.0;
-        for (int ci = 0; ci < DIM * ND1; ++ci) s = fma(f2d_exact(fk[ci * ND2 + j]), ws[ci], s);
-        ftv[j] = s;
-      }
+    // F^T w from the stored FP32 element matrix, FP64 accumulation.  The
+    // team's NQD = 2^DIM ND2 threads split the DIM ND1 terms of each of the
+    // ND2 sums into 2^DIM chunks (short dependent chains); the chunk sums
+    // are then added in chunk order.
+    constexpr int NPART = NQD / ND2, NCI = DIM * ND1, CH = (NCI + NPART - 1) / NPART;
+    double* part = gq;  // NQD doubles per element, free on this path
+    if (active) {
+      const int j = tq % ND2, pc = tq / ND2;
+      const float* fk = A.FK + el * (DIM * ND1 * ND2);
+      const int c0 = pc * CH, c1 = (c0 + CH < NCI) ? c0 + CH : NCI;
+      double s = 0.0;
+      for (int ci = c0; ci < c1; ++ci) s = fma(f2d_exact(fk[ci * ND2 + j]), ws[ci], s);
+      part[tq] = s;
+    }
+    team_sync<NQD>();
+    if (active && tq < ND2) {
+      double s = part[tq];
+      for (int pc = 1; pc < NPART; ++pc) s += part[pc * ND2 + tq];
+      ftv[tq] = s;
+    }
   } else {
     const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
     double gw[DIM][DIM];
@@ -647,7 +711,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
           TB[w] = sb;
           TG[w] = sg;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int f = 0; f < DIM; ++f) {
           double d0 = 0.0, d1 = 0.0;
@@ -677,7 +741,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
           TB[w] = sb;
           TG[w] = sg;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < DIM * P * NQ * NQ; w += NQD) {
           int x_ = w % NQ, y_ = (w / NQ) % NQ, fz = w / (NQ * NQ);
@@ -692,7 +756,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
           PGB[w] = gb;
           PBG[w] = bg;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int f = 0; f < DIM; ++f) {
           double d0 = 0.0, d1 = 0.0, d2 = 0.0;
@@ -714,7 +778,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
         for (int m = 0; m < DIM; ++m) s += D[(c * DIM + m) * NQD + tq] * gw[c][m];
       gq[tq] = s;
     }
-    __syncthreads();
+    team_sync<NQD>();
     if constexpr (DIM == 2) {
       if (active)
         for (int w = tq; w < K * NQ; w += NQD) {
@@ -723,7 +787,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
           for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[y_ * NQ + x_];
           l2s[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int j = tq; j < ND2; j += NQD) {
           int jx = j % K, jy = j / K;
@@ -741,7 +805,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
           for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[(z_ * NQ + y_) * NQ + x_];
           R1[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int w = tq; w < K * K * NQ; w += NQD) {
           int z_ = w % NQ, jx = (w / NQ) % K, jy = w / (NQ * K);
@@ -749,7 +813,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
           for (int y_ = 0; y_ < NQ; ++y_) s += Ls[y_ * K + jy] * R1[(jx * NQ + z_) * NQ + y_];
           R2[w] = s;
         }
-      __syncthreads();
+      team_sync<NQD>();
       if (active)
         for (int j = tq; j < ND2; j += NQD) {
           int jx = j % K, jy = (j / K) % K, jz = j / (K * K);
@@ -759,8 +823,8 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
         }
     }
   }
-  if (active && tq == 0) crs[0] = coef / prm.rho0K[el];
-  __syncthreads();
+  if (active && tq == 0) crs[0] = A.rho0Kinv ? coef * A.rho0Kinv[el] : coef / prm.rho0K[el];
+  team_sync<NQD>();
   if (active)
     for (int j = tq; j < ND2; j += NQD) {
       // M_E,K^{-1} = Mref^{-1} / (rho0 |J0|)_K, applied to F^T w + src
@@ -773,6 +837,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
       }
       A.e_out[el * ND2 + j] = fma(crs[0], s, A.e_base[el * ND2 + j]);
     }
+  team_sync<NQD>();  // the team reuses its element area in the next tile
 }
 
 template <int DIM, int K, bool MIXED>
@@ -781,6 +846,8 @@ energy_update_kernel(const EnergyKParams prm) {
   using F = EL<DIM, K, MIXED>;
   if (prm.a.ctl != nullptr && prm.a.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  energy_tables<DIM, K, MIXED, F::NT>(prm.b, smem);
+  __syncthreads();
   energy_tile<DIM, K, MIXED, F::NT>(prm.g, prm.b, prm.a, prm.rho0K, smem,
                                     (int64_t)blockIdx.x * F::EPB);
 }

@@ -129,6 +129,7 @@ struct Arrays {
   float *FK;                    // mixed path: element force matrices [nelem][dim*nd1][nd2]
   double *srcE;                 // energy source [N_E]
   double *rho0K;                // rho0 |J0| per element
+  double *rho0Kinv;             // its reciprocal
   double *dinv;                 // 1 / diag(M_s) per node
   double *partials;             // reduction partials [4][max_blocks]
   double *tmpE;                 // N_E scratch
@@ -224,6 +225,7 @@ struct EnergyArgs {
   double frac;
   double dt;
   const Ctl* ctl;
+  const double* rho0Kinv;  // 1 / (rho0 |J0|) per element (NULL: divide)
 };
 cudaError_t launch_energy_update(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s);
 

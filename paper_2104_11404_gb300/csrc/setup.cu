@@ -309,7 +309,7 @@ static void free_all(lh_ctx* c) {
   double** dptrs[] = {&c->a.v, &c->a.e, &c->a.x, &c->a.vh, &c->a.eh, &c->a.xh, &c->a.vn,
                       &c->a.en, &c->a.xn, &c->a.vbar, &c->a.F1E, &c->a.rhs, &c->a.acc,
                       &c->a.r, &c->a.z, &c->a.p, &c->a.Ap, &c->a.ApE, &c->a.D, &c->a.srcE,
-                      &c->a.rho0K, &c->a.dinv, &c->a.partials, &c->a.tmpE, &c->a.tmpV,
+                      &c->a.rho0K, &c->a.rho0Kinv, &c->a.dinv, &c->a.partials, &c->a.tmpE, &c->a.tmpV,
                       &c->a.aux};
   for (double** p : dptrs)
     if (*p) { cudaFree(*p); *p = nullptr; }
@@ -421,6 +421,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     if (e == cudaSuccess) e = dalloc(&A.FK, nelem * d * nd1 * nd2);
   }
   if (e == cudaSuccess) e = dalloc(&A.rho0K, nelem);
+  if (e == cudaSuccess) e = dalloc(&A.rho0Kinv, nelem);
   if (e == cudaSuccess) e = dalloc(&A.dinv, (size_t)g.nnodes);
   if (e == cudaSuccess) e = dalloc(&A.partials, (size_t)5 * kMaxPartials);
   if (e == cudaSuccess) e = dalloc(&A.cg, 1);
@@ -519,6 +520,12 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   Ctl ctl0;
   memset(&ctl0, 0, sizeof(ctl0));
   e = cudaMemcpy(A.rho0K, rho0K.data(), nelem * sizeof(double), cudaMemcpyHostToDevice);
+  {
+    std::vector<double> inv(nelem);
+    for (size_t i = 0; i < nelem; ++i) inv[i] = 1.0 / rho0K[i];
+    if (e == cudaSuccess)
+      e = cudaMemcpy(A.rho0Kinv, inv.data(), nelem * sizeof(double), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess)
     e = cudaMemcpy(A.dinv, diag.data(), g.nnodes * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(A.bar, 0, sizeof(Barrier));

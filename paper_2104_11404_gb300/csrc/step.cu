@@ -137,6 +137,7 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   e1.srcE = c->ph.source ? A.srcE : nullptr;
   e1.prefE = mixed ? A.tmpE : nullptr;
   e1.e_base = A.e; e1.e_out = A.eh; e1.frac = 0.5; e1.dt = 0.0; e1.ctl = A.ctl;
+  e1.rho0Kinv = A.rho0Kinv;
   if ((e = launch_energy_update(c, e1, s)) != cudaSuccess) return e;
   // stage 2: forces of S^{n+1/2}
   ForceArgs f2 = f1;

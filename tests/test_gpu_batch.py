@@ -155,7 +155,7 @@ def test_batch_launch_shapes_agree_and_autotune_keeps_state():
     dts = np.array([1e-3, 1.5e-3, 0.7e-3])
     ref = None
     for threads in (256, 512, 1024):
-        for sl in (1, 0):
+        for sl in (2, 1, 0):
             b = _batch(cfgs, "mixed", tuning=dict(threads=threads, ctas_per_sm=1, smem_lines=sl))
             assert b.tuning()["threads"] == threads
             b.set_state(dev(_pack(vs)), dev(_pack(es)), dev(_pack(xs)))
