@@ -413,11 +413,16 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
         if (it == fac_at.end()) {
           std::vector<double> L;
           banded_cholesky_1d(b->basis, g.k, g.n[d], var, L);
+          // row r: d_r = 1 / L_rr, d_r L_{r,r-q}, d_r L_{r+q,r} (q = 1..k; zero
+          // beyond the line)
           const int64_t off = (int64_t)fac.size();
-          const int rows = (int)(L.size() / (g.k + 1));
+          const int kk = g.k, rows = (int)(L.size() / (kk + 1));
           for (int r = 0; r < rows; ++r) {
-            fac.push_back(1.0 / L[(size_t)r * (g.k + 1)]);
-            for (int m = 1; m <= g.k; ++m) fac.push_back(L[(size_t)r * (g.k + 1) + m]);
+            const double dr = 1.0 / L[(size_t)r * (kk + 1)];
+            fac.push_back(dr);
+            for (int q = 1; q <= kk; ++q) fac.push_back(dr * L[(size_t)r * (kk + 1) + q]);
+            for (int q = 1; q <= kk; ++q)
+              fac.push_back(r + q < rows ? dr * L[(size_t)(r + q) * (kk + 1) + q] : 0.0);
           }
           it = fac_at.emplace(key, off).first;
         }

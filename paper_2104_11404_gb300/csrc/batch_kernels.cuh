@@ -45,7 +45,7 @@ struct BatchArgs {
   double *v, *e, *x, *vh, *eh, *xh, *vn, *en, *xn, *vbar;
   const double* rho0K;   // per element (packed by oel)
   const double* rho0Kinv;
-  const double* fac;     // row i of a table: 1 / L_ii, L_{i,i-1}, ..., L_{i,i-k}
+  const double* fac;     // line-solve tables (see line_solve)
   double* F1E;           // element rows of F.1, then of M p (CG)
   float* FK;             // mixed: element force matrices
   double* D;             // FP64: stress weights
@@ -109,37 +109,44 @@ __device__ __forceinline__ void load_instance(const BatchArgs& a, int i, BInst* 
 }
 
 // Forward and backward substitution along one node line of w (m entries,
-// stride apart): w <- (L L^T)^-1 w with the banded Cholesky factor F of the
-// assembled 1D matrix (row i: 1 / L_ii, L_{i,i-1}, ..., L_{i,i-K}).
+// stride apart): w <- (L L^T)^-1 w with the banded Cholesky factor L of the
+// assembled 1D matrix.  Row i of the table F holds d_i = 1 / L_ii, the scaled
+// forward coefficients d_i L_{i,i-q} and the scaled backward coefficients
+// d_i L_{i+q,i} (q = 1..K), so each substitution step has one dependent FMA.
 template <int K>
 __device__ __forceinline__ void line_solve(double* L, int64_t stride, int m,
                                            const double* __restrict__ F) {
+  constexpr int W = 2 * K + 1;
   double win[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) win[q] = 0.0;
-  for (int i = 0; i < m; ++i) {  // y_i = (b_i - sum_q L_{i,i-q} y_{i-q}) / L_ii
-    const double* Fi = F + (int64_t)i * (K + 1);
-    double s = L[i * stride];
+  double b = m > 0 ? L[0] : 0.0;
+  for (int i = 0; i < m; ++i) {  // y_i = d_i b_i - sum_q d_i L_{i,i-q} y_{i-q}
+    const double* Fi = F + (int64_t)i * W;
+    const double bn = (i + 1 < m) ? L[(i + 1) * stride] : 0.0;  // next input, off the chain
+    double s = Fi[0] * b;
 #pragma unroll
-    for (int q = 1; q <= K; ++q) s -= Fi[q] * win[q - 1];
-    s *= Fi[0];
+    for (int q = K; q >= 1; --q) s = fma(-Fi[q], win[q - 1], s);
 #pragma unroll
     for (int q = K - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = s;
     L[i * stride] = s;
+    b = bn;
   }
 #pragma unroll
   for (int q = 0; q < K; ++q) win[q] = 0.0;
-  for (int i = m - 1; i >= 0; --i) {  // x_i = (y_i - sum_q L_{i+q,i} x_{i+q}) / L_ii
-    double s = L[i * stride];
+  double y = m > 0 ? L[(m - 1) * stride] : 0.0;
+  for (int i = m - 1; i >= 0; --i) {  // x_i = d_i y_i - sum_q d_i L_{i+q,i} x_{i+q}
+    const double* Fi = F + (int64_t)i * W;
+    const double yn = i > 0 ? L[(i - 1) * stride] : 0.0;
+    double s = Fi[0] * y;
 #pragma unroll
-    for (int q = 1; q <= K; ++q)
-      if (i + q < m) s -= F[(int64_t)(i + q) * (K + 1) + q] * win[q - 1];
-    s *= F[(int64_t)i * (K + 1)];
+    for (int q = K; q >= 1; --q) s = fma(-Fi[K + q], win[q - 1], s);
 #pragma unroll
     for (int q = K - 1; q > 0; --q) win[q] = win[q - 1];
     win[0] = s;
     L[i * stride] = s;
+    y = yn;
   }
 }
 
@@ -208,6 +215,72 @@ struct BL {
   }
 };
 
+// A p for the CG of a 2D instance, with p and the node sums in shared memory
+// (buf: 2 nnodes doubles), one component at a time: every element's
+// (M1 x M1) p_K is formed in registers and added to its nodes.  The elements
+// are taken in four colours (parity of the element indices), so no two
+// elements of one colour share a node and every node receives its (at most
+// four) contributions in colour order: the sums are deterministic.  Writes
+// AP (zero on the wall-normal entries) and returns p . Ap.
+template <int K>
+__device__ double cta_mass_colored(const Geom& g, const double* M1s, double rho0K,
+                                   const double* Pv, double* AP, double* buf) {
+  constexpr int P = K + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t nn = g.nnodes;
+  double* pc = buf;
+  double* ac = buf + nn;
+  double pap = 0.0;
+  for (int c = 0; c < 2; ++c) {
+    for (int64_t node = tid; node < nn; node += nt) {
+      pc[node] = Pv[c * nn + node];
+      ac[node] = 0.0;
+    }
+    __syncthreads();
+    for (int color = 0; color < 4; ++color) {
+      const int bx = color & 1, by = color >> 1;
+      const int mx = (g.n[0] - bx + 1) / 2, my = (g.n[1] - by + 1) / 2;
+      for (int item = tid; item < mx * my; item += nt) {
+        const int ex = 2 * (item % mx) + bx, ey = 2 * (item / mx) + by;
+        const int64_t base = (int64_t)ex * K + (int64_t)g.nn[0] * ((int64_t)ey * K);
+        double t[P][P];
+#pragma unroll
+        for (int b = 0; b < P; ++b) {
+          double u[P];
+#pragma unroll
+          for (int a = 0; a < P; ++a) u[a] = pc[base + (int64_t)g.nn[0] * b + a];
+#pragma unroll
+          for (int ap = 0; ap < P; ++ap) {
+            double acc = 0.0;
+#pragma unroll
+            for (int a = 0; a < P; ++a) acc = fma(M1s[ap * P + a], u[a], acc);
+            t[b][ap] = acc;
+          }
+        }
+#pragma unroll
+        for (int bp = 0; bp < P; ++bp)
+#pragma unroll
+          for (int ap = 0; ap < P; ++ap) {
+            double acc = 0.0;
+#pragma unroll
+            for (int b = 0; b < P; ++b) acc = fma(M1s[bp * P + b], t[b][ap], acc);
+            ac[base + (int64_t)g.nn[0] * bp + ap] += acc;
+          }
+      }
+      __syncthreads();
+    }
+    for (int64_t node = tid; node < nn; node += nt) {
+      const int i0 = (int)(node % g.nn[0]), i1 = (int)(node / g.nn[0]);
+      const int ic = c == 0 ? i0 : i1;
+      const double ap = (ic == 0 || ic == g.nn[c] - 1) ? 0.0 : rho0K * ac[node];
+      AP[c * nn + node] = ap;
+      pap += pc[node] * ap;
+    }
+    __syncthreads();
+  }
+  return cta_sum(pap);
+}
+
 // In-CTA preconditioned CG: M_V x = b on the free components, b in R (the
 // essential entries of b are zero), x in X.  Returns the iteration count;
 // *relres = ||r|| / ||b||; *conv = converged.
@@ -251,23 +324,29 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
   bool ok = false;
   while (true) {
     ++it;
-    // A p: element phase (tiles of CGT elements), then the node gather
-    for (int64_t el0 = 0; el0 < g.nelem; el0 += CGT) {
-      const int nel = (int)((g.nelem - el0) < CGT ? (g.nelem - el0) : CGT);
-      mass_elements<DIM, K>(g, M1s, Pv, rho0K, ApE, el0, nel, u, t, y);
-    }
-    double pap = 0.0;
-    for (int64_t node = tid; node < nn; node += NTT) {
-      int Ix[3];
-      node_ijk(g, node, Ix);
-      for (int c = 0; c < DIM; ++c) {
-        const int64_t k = c * nn + node;
-        const double ap = essential(g, Ix, c) ? 0.0 : gather_node<DIM, K>(g, ApE, Ix, c);
-        AP[k] = ap;
-        pap += Pv[k] * ap;
+    double pap;
+    if (DIM == 2 && a.smem_lines == 2) {
+      // A p on shared-memory node arrays (rho0 |J0| is uniform in an instance)
+      pap = cta_mass_colored<K>(g, M1s, I.rho0K, Pv, AP, lines);
+    } else {
+      // element phase (tiles of CGT elements), then the node gather
+      for (int64_t el0 = 0; el0 < g.nelem; el0 += CGT) {
+        const int nel = (int)((g.nelem - el0) < CGT ? (g.nelem - el0) : CGT);
+        mass_elements<DIM, K>(g, M1s, Pv, rho0K, ApE, el0, nel, u, t, y);
       }
+      pap = 0.0;
+      for (int64_t node = tid; node < nn; node += NTT) {
+        int Ix[3];
+        node_ijk(g, node, Ix);
+        for (int c = 0; c < DIM; ++c) {
+          const int64_t k = c * nn + node;
+          const double ap = essential(g, Ix, c) ? 0.0 : gather_node<DIM, K>(g, ApE, Ix, c);
+          AP[k] = ap;
+          pap += Pv[k] * ap;
+        }
+      }
+      pap = cta_sum(pap);
     }
-    pap = cta_sum(pap);
     const double alpha = rz / pap;
     double lrr = 0.0;
     for (int64_t k = tid; k < nv; k += NTT) {
