@@ -8,11 +8,14 @@
 // (ticket counter) adds the partials in block order and publishes the scalar.
 //
 // Preconditioners:
-//  - tensor product: with rho0|J0| the same in every element, M_s is
-//    rho0|J0| G_x (x) G_y [(x) G_z] with G_d the assembled 1D reference mass
-//    matrices; its inverse is applied by banded Cholesky solves along every
-//    node line, one direction per kernel.  This is the exact inverse, so the
-//    CG stops after one iteration;
+//  - tensor product: with rho0|J0| the same in every element, M_V restricted
+//    to the free entries of component c is rho0|J0| times the Kronecker
+//    product of assembled 1D reference mass matrices G_d (without their end
+//    nodes along direction c).  The inverse of each G_d decays exponentially
+//    away from the diagonal; its entries within a band of half-width B are
+//    kept in FP32 and applied by one line pass per direction (a tile of node
+//    lines and its halo staged in shared memory).  The CG converges in about
+//    three iterations (Jacobi needs ~28 on the 64x64 Taylor-Green mesh);
 //  - Jacobi: the inverse assembled diagonal.
 #include "mass_ops.cuh"
 
