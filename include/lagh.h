@@ -112,7 +112,7 @@ typedef struct lh_phys_desc {
   double q1, q2;         /* linear and quadratic viscosity coefficients */
   double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2 */
   double dt_min_frac;    /* dt < dt_min_frac * t_final -> LH_EDTMIN */
-  int32_t cg_precond;    /* LH_PRECOND_TENSOR (default) or LH_PRECOND_JACOBI */
+  int32_t cg_precond;    /* LH_PRECOND_EXACT (default), LH_PRECOND_TENSOR or LH_PRECOND_JACOBI */
   int32_t direct_launch; /* 0 (default): each step attempt is one CUDA graph launch
                             (the CG iterations a WHILE node inside it); 1: the same
                             kernels launched one by one, with a host poll of the CG
@@ -123,7 +123,15 @@ typedef struct lh_phys_desc {
  * kinematic mass matrix when rho0 |J0| is the same in every element (then
  * M_V is a Kronecker product of assembled 1D mass matrices), applied by
  * banded 1D line solves; JACOBI: the inverse diagonal. */
-enum { LH_PRECOND_JACOBI = 0, LH_PRECOND_TENSOR = 1 };
+/* Velocity CG preconditioners.  With rho0 |J0| the same in every element (every
+ * problem of Section 6.1 on a Cartesian box), M_V restricted to the free
+ * entries of a component is rho0 |J0| times a Kronecker product of assembled
+ * 1D mass matrices.  EXACT applies its inverse by FP64 banded Cholesky solves
+ * along every node line (the CG stops after one iteration); TENSOR applies the
+ * inverses of the 1D matrices truncated to a band, in FP32 (about three
+ * iterations); JACOBI the inverse diagonal.  Meshes where rho0 |J0| varies use
+ * JACOBI whatever is asked. */
+enum { LH_PRECOND_JACOBI = 0, LH_PRECOND_TENSOR = 1, LH_PRECOND_EXACT = 2 };
 
 typedef struct lh_layout_info {
   int64_t nv;            /* N_V = dim * nnodes */

@@ -17,6 +17,7 @@
 //    lines and its halo staged in shared memory).  The CG converges in about
 //    three iterations (Jacobi needs ~28 on the 64x64 Taylor-Green mesh);
 //  - Jacobi: the inverse assembled diagonal.
+#include "line_solve.cuh"
 #include "mass_ops.cuh"
 
 namespace lagh {
@@ -32,6 +33,7 @@ struct CgArgs {
   double M1[(kMaxOrder + 1) * (kMaxOrder + 1)];
   TensorPC tpc;
   const float* lfac;
+  const double* lchol;
   const double* rhs;
   double *x, *r, *z, *p, *Ap, *ApE;
   const double* dinv;
@@ -245,6 +247,119 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
   }
 }
 
+// ------------------------------------------------- exact line solves ----
+
+// One direction of the exact tensor-product preconditioner: every node line
+// of every component along direction d is solved with the banded Cholesky
+// factor of its assembled 1D matrix (forward and backward substitution,
+// FP64).  A CTA owns kLineGroup lines of one component: it stages them in
+// shared memory (coalesced), kLineGroup threads solve one line each, and the
+// block writes them back.  mode / last / init as for cg_pass_kernel.
+constexpr int kLineGroup = 8;
+constexpr int kLineThreadsX = 64;
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(kLineThreadsX) cg_line_kernel(const CgArgs a, int d, int mode,
+                                                               int last, int init,
+                                                               const double* src_in,
+                                                               double* dst) {
+  if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) return;
+  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
+    a.cg->done = 0;
+    a.cg->it = 0;
+  }
+  extern __shared__ double lbuf[];
+  const Geom& g = a.g;
+  const int nd = g.nn[d];
+  const int ldb = nd | 1;  // odd row length (bank spread)
+  const int64_t nlines = g.nnodes / nd;
+  const int64_t groups = (nlines + kLineGroup - 1) / kLineGroup;
+  const int c = (int)(blockIdx.x / groups);
+  const int64_t l0 = (int64_t)(blockIdx.x % groups) * kLineGroup;
+  const int var = (c == d) ? 1 : 0;
+  const int64_t stride = d == 0 ? 1 : (d == 1 ? (int64_t)g.nn[0] : (int64_t)g.nn[0] * g.nn[1]);
+  const int tid = threadIdx.x;
+  // line l of the group: its first node and whether it is a wall-normal line
+  auto line_info = [&](int l, int64_t& base, bool& wall) -> bool {
+    const int64_t line = l0 + l;
+    if (line >= nlines) return false;
+    int I[3] = {0, 0, 0};
+    if (d == 0) { I[1] = (int)(line % g.nn[1]); I[2] = (int)(line / g.nn[1]); }
+    else if (d == 1) { I[0] = (int)(line % g.nn[0]); I[2] = (int)(line / g.nn[0]); }
+    else { I[0] = (int)(line % g.nn[0]); I[1] = (int)(line / g.nn[0]); }
+    base = (int64_t)c * g.nnodes + node_index(g, I[0], I[1], I[2]);
+    wall = (c != d) && (I[c] == 0 || I[c] == g.nn[c] - 1);
+    return true;
+  };
+  const double* src = mode == 0 ? a.rhs : src_in;
+  const double scl = (mode == 2) ? 1.0 : a.tpc.scale;
+  // along x the lines are rows (walk a line), otherwise neighbouring lines
+  // are neighbouring nodes (walk across lines)
+  for (int idx = tid; idx < kLineGroup * nd; idx += kLineThreadsX) {
+    const int l = d == 0 ? idx / nd : idx % kLineGroup;
+    const int pos = d == 0 ? idx - l * nd : idx / kLineGroup;
+    int64_t base;
+    bool wall;
+    double val = 0.0;
+    if (line_info(l, base, wall) && !wall && pos >= var && pos < nd - var)
+      val = src[base + pos * stride] * scl;
+    lbuf[l * ldb + pos] = val;
+  }
+  __syncthreads();
+  if (tid < kLineGroup) {
+    int64_t base;
+    bool wall;
+    if (line_info(tid, base, wall) && !wall)
+      line_solve<K>(lbuf + tid * ldb + var, 1, nd - 2 * var, a.lchol + a.tpc.coff[d][var]);
+  }
+  __syncthreads();
+  double l_bb = 0.0, l_rz = 0.0;
+  for (int idx = tid; idx < kLineGroup * nd; idx += kLineThreadsX) {
+    const int l = d == 0 ? idx / nd : idx % kLineGroup;
+    const int pos = d == 0 ? idx - l * nd : idx / kLineGroup;
+    int64_t base;
+    bool wall;
+    if (!line_info(l, base, wall)) continue;
+    const int64_t kk = base + pos * stride;
+    const double zv = lbuf[l * ldb + pos];
+    if (mode == 0) {
+      const bool ess = wall || pos < var || pos >= nd - var;
+      const double bv = ess ? 0.0 : a.rhs[kk];
+      a.r[kk] = bv;
+      a.x[kk] = 0.0;
+      l_bb += bv * bv;
+    }
+    dst[kk] = zv;
+    if (last) {
+      l_rz += a.r[kk] * zv;
+      if (init) a.p[kk] = zv;
+    }
+  }
+  double tot;
+  if (mode == 0) {
+    if (reduce_last(l_bb, a.part, &a.cg->ticket[kTicketPass0], &tot) && threadIdx.x == 0)
+      a.cg->bb = tot;
+  }
+  if (last) {
+    if (reduce_last(l_rz, a.part + kMaxPartials, &a.cg->ticket[kTicketPassL], &tot) &&
+        threadIdx.x == 0) {
+      CgDev* cg = a.cg;
+      if (init) {
+        cg->rz = tot;
+        cg->it = 0;
+        cg->beta = 0.0;
+        if (!(cg->bb > 0.0)) {  // zero right-hand side: x = 0 is the solution
+          cg->done = 1;
+          report(a, true, 0.0);
+        }
+      } else {
+        cg->beta = tot / cg->rz;
+        cg->rz = tot;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------- Jacobi init ----
 
 template <int DIM, int K>
@@ -413,6 +528,7 @@ static CgArgs make_args(const lh_ctx* c, const double* rhs, double* out, const C
     for (int j = 0; j <= kMaxOrder; ++j) a.M1[i * (kMaxOrder + 1) + j] = c->basis.M1[i][j];
   a.tpc = c->tpc;
   a.lfac = c->a.lfac;
+  a.lchol = c->a.lchol;
   a.rhs = rhs;
   a.x = out;
   a.r = c->a.r;
@@ -433,12 +549,28 @@ static CgArgs make_args(const lh_ctx* c, const double* rhs, double* out, const C
   return a;
 }
 
+static size_t line_smem(const lh_ctx* c, int d) {
+  return (size_t)kLineGroup * (c->g.nn[d] | 1) * sizeof(double);
+}
+
 template <int DIM, int K>
 static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, cudaStream_t s) {
   // out of place: r -> z (d = 0), then alternate between Ap (free here) and z
   // so that the last direction writes z
   const double* src = a.r;
   double* bufs[2] = {a.z, a.Ap};
+  if (c->tpc.exact) {
+    for (int d = 0; d < DIM; ++d) {
+      const int64_t nlines = c->g.nnodes / c->g.nn[d];
+      const int64_t blocks = (int64_t)DIM * ((nlines + kLineGroup - 1) / kLineGroup);
+      const int mode = d == 0 ? (init ? 0 : 1) : 2;
+      double* dst = bufs[(DIM - 1 - d) & 1];
+      cg_line_kernel<DIM, K><<<(unsigned)blocks, kLineThreadsX, line_smem(c, d), s>>>(
+          a, d, mode, d == DIM - 1, init ? 1 : 0, src, dst);
+      src = dst;
+    }
+    return cudaGetLastError();
+  }
   for (int d = 0; d < DIM; ++d) {
     const int nd = c->g.nn[d];
     const int64_t nlines = c->g.nnodes / nd;
@@ -496,7 +628,11 @@ static cudaError_t cg_body(const lh_ctx* c, const CgArgs& a, cudaStream_t s) {
 
 template <int DIM, int K>
 static cudaError_t cg_prepare_dk(const lh_ctx* c) {
-  return c->tpc.B[0] == PB<K>::B ? cudaSuccess : cudaErrorInvalidValue;
+  if (c->tpc.B[0] != PB<K>::B) return cudaErrorInvalidValue;
+  size_t mx = 0;
+  for (int d = 0; d < DIM; ++d) mx = line_smem(c, d) > mx ? line_smem(c, d) : mx;
+  return cudaFuncSetAttribute(cg_line_kernel<DIM, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)mx);
 }
 
 // Shared memory of the line passes, set before any stream capture.

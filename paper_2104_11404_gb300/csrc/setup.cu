@@ -318,6 +318,7 @@ static void free_all(lh_ctx* c) {
   if (c->a.ctl) { cudaFree(c->a.ctl); c->a.ctl = nullptr; }
   if (c->a.cg) { cudaFree(c->a.cg); c->a.cg = nullptr; }
   if (c->a.lfac) { cudaFree(c->a.lfac); c->a.lfac = nullptr; }
+  if (c->a.lchol) { cudaFree(c->a.lchol); c->a.lchol = nullptr; }
   if (c->side) { cudaStreamDestroy(c->side); c->side = nullptr; }
   if (c->ctl_host) { cudaFreeHost(c->ctl_host); c->ctl_host = nullptr; }
   if (c->graph_ready == 1) cudaGraphExecDestroy(c->step_graph);
@@ -469,6 +470,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   // entries within half-width B are kept (relative size of the dropped ones
   // below 1e-9 for B = 14, 22, 30 at k = 1, 2, 3) and applied in FP32.
   std::vector<float> lf;
+  std::vector<double> lc;  // exact variant: scaled banded Cholesky rows
   memset(&c->tpc, 0, sizeof(c->tpc));
   {
     bool uniform = true;
@@ -487,6 +489,15 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
         if (N <= 0) continue;
         std::vector<double> L;  // L[i][m] = L_{i,i-m}
         banded_cholesky_1d(c->basis, k, g.n[dd], var, L);
+        // exact variant, row r: d_r = 1 / L_rr, d_r L_{r,r-q}, d_r L_{r+q,r} (q = 1..k)
+        c->tpc.coff[dd][var] = (int64_t)lc.size();
+        for (int r = 0; r < N; ++r) {
+          const double dr = 1.0 / L[(size_t)r * (k + 1)];
+          lc.push_back(dr);
+          for (int q = 1; q <= k; ++q) lc.push_back(dr * L[(size_t)r * (k + 1) + q]);
+          for (int q = 1; q <= k; ++q)
+            lc.push_back(r + q < N ? dr * L[(size_t)(r + q) * (k + 1) + q] : 0.0);
+        }
         // columns of the inverse by banded solves; keep |i - j| <= B
         const int W = 2 * B + 1;
         std::vector<double> band((size_t)N * W, 0.0), col(N);
@@ -510,11 +521,16 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     }
     c->tpc.Bmax = Bmax;
     c->tpc.scale = 1.0 / rho0K[0];
-    c->tpc.enabled = (phys->cg_precond == LH_PRECOND_TENSOR) && uniform;
+    c->tpc.enabled = (phys->cg_precond == LH_PRECOND_TENSOR ||
+                      phys->cg_precond == LH_PRECOND_EXACT) && uniform;
+    c->tpc.exact = c->tpc.enabled && phys->cg_precond == LH_PRECOND_EXACT;
   }
   e = dalloc(&A.lfac, lf.size() > 0 ? lf.size() : 1);
   if (e == cudaSuccess && !lf.empty())
     e = cudaMemcpy(A.lfac, lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dalloc(&A.lchol, lc.size() > 0 ? lc.size() : 1);
+  if (e == cudaSuccess && !lc.empty())
+    e = cudaMemcpy(A.lchol, lc.data(), lc.size() * sizeof(double), cudaMemcpyHostToDevice);
   if ((st = cuda_check(c, e, "preconditioner")) != LH_OK) return fail(st, c->err);
   if ((st = cuda_check(c, cg_prepare(c), "cg attributes")) != LH_OK) return fail(st, c->err);
   Ctl ctl0;

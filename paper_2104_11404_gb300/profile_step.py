@@ -26,6 +26,8 @@ def main():
     ap.add_argument("--batch", action="store_true", help="the batched point-blast sweep")
     ap.add_argument("--instances", type=int, default=512)
     ap.add_argument("--tuning", default="", help="threads,ctas_per_sm,smem_lines")
+    ap.add_argument("--precond", type=int, default=-1,
+                    help="cg_precond (0 Jacobi, 1 tensor bands, 2 exact); default: the library's")
     args = ap.parse_args()
     if args.batch:
         return run_batch(args)
@@ -37,8 +39,10 @@ def main():
     libbuild.build()
     torch.cuda.set_device(0)
     cfg = W.CONFIGS[args.workload]
-    g = Hydro(cfg, precision=args.precision,
-              phys_overrides=None if args.graph else {"direct_launch": 1})
+    over = {} if args.graph else {"direct_launch": 1}
+    if args.precond >= 0:
+        over["cg_precond"] = args.precond
+    g = Hydro(cfg, precision=args.precision, phys_overrides=over or None)
     g.init_state()
     if args.warmup:
         g.run_to(cfg["t_final"], max_steps=args.warmup)

@@ -86,10 +86,14 @@ def test_cg_preconditioners_agree(dim, k, n):
     xo, _, _, _ = o.mass_solve_v(b)
     gt = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_TENSOR})
     gj = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_JACOBI})
+    ge = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_EXACT})
     xt, it_t, rr_t = gt.mass_solve_v(dev(b))
     xj, it_j, rr_j = gj.mass_solve_v(dev(b))
-    assert rel_l2(xo, host(xt)) <= 1e-12 and rel_l2(xo, host(xj)) <= 1e-12
-    # the tensor-product preconditioner is the inverse (applied in FP32) here
+    xe, it_e, rr_e = ge.mass_solve_v(dev(b))
+    for xg in (xt, xj, xe):
+        assert rel_l2(xo, host(xg)) <= 1e-12
+    # banded inverse in FP32: a few iterations; the exact inverse: one
+    assert it_e == 1 and rr_e <= 1e-14
     assert it_t <= 3 < it_j
 
 
@@ -107,6 +111,13 @@ def test_precond_apply_approximates_mass_inverse(dim, k, n):
     assert np.all(z[W.essential_mask(cfg)] == 0.0)
     # FP32 banded inverse: close to M_V^{-1} b, not equal
     assert 1e-12 < rel_l2(xo, z) <= 1e-6
+    # the exact variant is M_V^{-1} up to rounding
+    ge = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_EXACT})
+    out = ge.zeros_v()
+    lagh.lh_precond_apply(ge.ctx, dev(b), out)
+    ze = host(out)
+    assert np.all(ze[W.essential_mask(cfg)] == 0.0)
+    assert rel_l2(xo, ze) <= 1e-13
 
 
 def _per_step(cfg, nsteps, precision="fp64", tol=1e-12):
