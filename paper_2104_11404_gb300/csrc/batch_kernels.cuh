@@ -442,7 +442,6 @@ __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, con
     ea.D = D;
     ea.FK = FK;
     ea.srcE = fa.srcE;
-    ea.prefE = nullptr;
     ea.e_base = a.e + sI.oe;
     ea.e_out = (stage == 0 ? a.eh : a.en) + sI.oe;
     ea.frac = stage == 0 ? 0.5 : 1.0;

@@ -599,11 +599,13 @@ struct EL {
   static constexpr int ND1 = ipow(P, DIM), ND2 = ipow(K, DIM), NQD = ipow(NQ, DIM);
   static constexpr int EPB = (NTT / NQD) > 0 ? NTT / NQD : 1;
   static constexpr int NT = EPB * NQD;
-  static constexpr int S_INTERP = DIM == 2 ? 2 * DIM * P * NQ
-                                           : 2 * DIM * P * P * NQ + 3 * DIM * P * NQ * NQ;
+  // interpolated fields: w (FP64 path); w and x (mixed path, reference pressure)
+  static constexpr int NFI = MIXED ? 2 * DIM : DIM;
+  static constexpr int S_INTERP = DIM == 2 ? 2 * NFI * P * NQ
+                                           : 2 * NFI * P * P * NQ + 3 * NFI * P * NQ * NQ;
   static constexpr int S_L2 = DIM == 2 ? K * NQ : K * NQ * NQ + K * K * NQ;
   static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
-  static constexpr size_t B_ELEM = al(DIM * ND1 * 8) + al(S_INTERP * 8) + al(NQD * 8) +
+  static constexpr size_t B_ELEM = al(NFI * ND1 * 8) + al(S_INTERP * 8) + al(NQD * 8) +
                                    al(S_L2 * 8) + al(ND2 * 8) + al(8);
   static constexpr size_t B_TAB = 3 * al(NQ * P * 8) + al(NQ * K * 8) + al(81 * 8);
   static constexpr size_t BYTES = B_TAB + EPB * B_ELEM;
@@ -624,7 +626,7 @@ __device__ __forceinline__ void energy_tables(const Basis1D& bas, unsigned char*
   unsigned char* sp = smem;
   double* Bs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
   double* Gs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
-  sp += F::al(NQ * P * 8);
+  double* Wd = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
   double* Ls = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * 8);
   double* Mi = reinterpret_cast<double*>(sp);
   const int tid = threadIdx.x;
@@ -632,8 +634,145 @@ __device__ __forceinline__ void energy_tables(const Basis1D& bas, unsigned char*
     Bs[i] = bas.B[i / P][i % P];
     Gs[i] = bas.G[i / P][i % P];
   }
+  for (int i = tid; i < NQ; i += blockDim.x) Wd[i] = bas.W[i];
   for (int i = tid; i < NQ * K; i += blockDim.x) Ls[i] = bas.L[i / K][i % K];
   for (int i = tid; i < ND2 * ND2; i += blockDim.x) Mi[i] = bas.MEinv[i];
+}
+
+// Reference gradients of nf FP64 fields (fields[f][ND1], staged by the team)
+// at the team's quadrature point: grad[f][m] = d_m u_f (sum factorisation in
+// the team's scratch).  Every thread of the block calls it.
+template <int DIM, int K, int NQD, int NFMAX>
+__device__ __forceinline__ void interp_grads(const double* fields, int nf, double* scr,
+                                             const double* Bs, const double* Gs, int tq,
+                                             bool active, double (&grad)[NFMAX][DIM]) {
+  constexpr int P = K + 1, NQ = 2 * K, ND1 = ipow(P, DIM);
+  const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
+  if constexpr (DIM == 2) {
+    double* TB = scr;
+    double* TG = scr + nf * P * NQ;
+    if (active)
+      for (int w = tq; w < nf * P * NQ; w += NQD) {
+        int x_ = w % NQ, b = (w / NQ) % P, f = w / (NQ * P);
+        double sb = 0.0, sg = 0.0;
+        for (int a = 0; a < P; ++a) {
+          double u = fields[f * ND1 + b * P + a];
+          sb += Bs[x_ * P + a] * u;
+          sg += Gs[x_ * P + a] * u;
+        }
+        TB[w] = sb;
+        TG[w] = sg;
+      }
+    team_sync<NQD>();
+    if (active)
+      for (int f = 0; f < nf; ++f) {
+        double d0 = 0.0, d1 = 0.0;
+        for (int b = 0; b < P; ++b) {
+          d0 += Bs[qy * P + b] * TG[(f * P + b) * NQ + qx];
+          d1 += Gs[qy * P + b] * TB[(f * P + b) * NQ + qx];
+        }
+        grad[f][0] = d0;
+        grad[f][1] = d1;
+      }
+  } else {
+    double* TB = scr;
+    double* TG = TB + nf * P * P * NQ;
+    double* PBB = TG + nf * P * P * NQ;
+    double* PGB = PBB + nf * P * NQ * NQ;
+    double* PBG = PGB + nf * P * NQ * NQ;
+    if (active)
+      for (int w = tq; w < nf * P * P * NQ; w += NQD) {
+        int x_ = w % NQ, r = w / NQ, b = r % P, fz = r / P;
+        int f = fz / P, cz = fz - f * P;
+        double sb = 0.0, sg = 0.0;
+        for (int a = 0; a < P; ++a) {
+          double u = fields[f * ND1 + (cz * P + b) * P + a];
+          sb += Bs[x_ * P + a] * u;
+          sg += Gs[x_ * P + a] * u;
+        }
+        TB[w] = sb;
+        TG[w] = sg;
+      }
+    team_sync<NQD>();
+    if (active)
+      for (int w = tq; w < nf * P * NQ * NQ; w += NQD) {
+        int x_ = w % NQ, y_ = (w / NQ) % NQ, fz = w / (NQ * NQ);
+        double bb = 0.0, gb = 0.0, bg = 0.0;
+        for (int b = 0; b < P; ++b) {
+          double tb = TB[(fz * P + b) * NQ + x_], tg = TG[(fz * P + b) * NQ + x_];
+          bb += Bs[y_ * P + b] * tb;
+          gb += Bs[y_ * P + b] * tg;
+          bg += Gs[y_ * P + b] * tb;
+        }
+        PBB[w] = bb;
+        PGB[w] = gb;
+        PBG[w] = bg;
+      }
+    team_sync<NQD>();
+    if (active)
+      for (int f = 0; f < nf; ++f) {
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0;
+        for (int cz = 0; cz < P; ++cz) {
+          int idx = ((f * P + cz) * NQ + qy) * NQ + qx;
+          d0 += Bs[qz * P + cz] * PGB[idx];
+          d1 += Bs[qz * P + cz] * PBG[idx];
+          d2 += Gs[qz * P + cz] * PBB[idx];
+        }
+        grad[f][0] = d0;
+        grad[f][1] = d1;
+        grad[f][2] = d2;
+      }
+  }
+}
+
+// out[j] (+)= sum_q phi_j(q) gq(q) over the team's quadrature points.
+template <int DIM, int K, int NQD>
+__device__ __forceinline__ void l2_contract(const double* gq, double* l2s, const double* Ls,
+                                            int tq, bool active, double* out, bool add) {
+  constexpr int NQ = 2 * K, ND2 = ipow(K, DIM);
+  if constexpr (DIM == 2) {
+    if (active)
+      for (int w = tq; w < K * NQ; w += NQD) {
+        int y_ = w % NQ, jx = w / NQ;
+        double s = 0.0;
+        for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[y_ * NQ + x_];
+        l2s[w] = s;
+      }
+    team_sync<NQD>();
+    if (active)
+      for (int j = tq; j < ND2; j += NQD) {
+        int jx = j % K, jy = j / K;
+        double s = 0.0;
+        for (int y_ = 0; y_ < NQ; ++y_) s += Ls[y_ * K + jy] * l2s[jx * NQ + y_];
+        out[j] = add ? out[j] + s : s;
+      }
+  } else {
+    double* R1 = l2s;
+    double* R2 = l2s + K * NQ * NQ;
+    if (active)
+      for (int w = tq; w < K * NQ * NQ; w += NQD) {
+        int y_ = w % NQ, z_ = (w / NQ) % NQ, jx = w / (NQ * NQ);
+        double s = 0.0;
+        for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[(z_ * NQ + y_) * NQ + x_];
+        R1[w] = s;
+      }
+    team_sync<NQD>();
+    if (active)
+      for (int w = tq; w < K * K * NQ; w += NQD) {
+        int z_ = w % NQ, jx = (w / NQ) % K, jy = w / (NQ * K);
+        double s = 0.0;
+        for (int y_ = 0; y_ < NQ; ++y_) s += Ls[y_ * K + jy] * R1[(jx * NQ + z_) * NQ + y_];
+        R2[w] = s;
+      }
+    team_sync<NQD>();
+    if (active)
+      for (int j = tq; j < ND2; j += NQD) {
+        int jx = j % K, jy = (j / K) % K, jz = j / (K * K);
+        double s = 0.0;
+        for (int z_ = 0; z_ < NQ; ++z_) s += Ls[z_ * K + jz] * R2[(jy * K + jx) * NQ + z_];
+        out[j] = add ? out[j] + s : s;
+      }
+  }
 }
 
 // One tile of EPB elements [el0, el0 + EPB) of the energy update.
@@ -643,17 +782,18 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
                                             int64_t el0) {
   using F = EL<DIM, K, MIXED, NTT>;
   constexpr int P = F::P, NQ = F::NQ, ND1 = F::ND1, ND2 = F::ND2, NQD = F::NQD;
-  struct Prm { const Basis1D& b; const double* rho0K; } prm{bas, rho0Kp};
   const double coef = A.frac * (A.ctl != nullptr ? A.ctl->dt_use : A.dt);
+  // mixed path: F^T w of the reference pressure -p_ref I, in FP64
+  const double pref = (MIXED && A.p_ref != nullptr && A.x != nullptr) ? *A.p_ref : 0.0;
   unsigned char* sp = smem;
   double* Bs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
   double* Gs = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
-  sp += F::al(NQ * P * 8);
+  double* Wd = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
   double* Ls = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * 8);
   double* Mi = reinterpret_cast<double*>(sp); sp += F::al(81 * 8);
   const int tid = threadIdx.x, le = tid / NQD, tq = tid - le * NQD;
   unsigned char* ep = sp + le * F::B_ELEM;
-  double* ws = reinterpret_cast<double*>(ep); ep += F::al(DIM * ND1 * 8);
+  double* ws = reinterpret_cast<double*>(ep); ep += F::al(F::NFI * ND1 * 8);  // w, then x
   double* scr = reinterpret_cast<double*>(ep); ep += F::al(F::S_INTERP * 8);
   double* gq = reinterpret_cast<double*>(ep); ep += F::al(NQD * 8);
   double* l2s = reinterpret_cast<double*>(ep); ep += F::al(F::S_L2 * 8);
@@ -664,11 +804,13 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   const bool active = le < F::EPB && el < g.nelem;
   int E[3] = {0, 0, 0};
   elem_ijk(g, active ? el : 0, E);
+  const int nstage = (pref != 0.0) ? 2 * DIM * ND1 : DIM * ND1;
   if (active)
-    for (int w = tq; w < DIM * ND1; w += NQD) {
-      int c = w / ND1, i = w - c * ND1;
-      int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
-      ws[w] = A.w[c * g.nnodes + elem_node<K>(g, E, a, b, cc)];
+    for (int w = tq; w < nstage; w += NQD) {
+      const int f = w / ND1, i = w - f * ND1;
+      const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+      const int64_t node = elem_node<K>(g, E, a, b, cc);
+      ws[w] = f < DIM ? A.w[f * g.nnodes + node] : A.x[(f - DIM) * g.nnodes + node];
     }
   team_sync<NQD>();
 
@@ -678,7 +820,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
     // ND2 sums into 2^DIM chunks (short dependent chains); the chunk sums
     // are then added in chunk order.
     constexpr int NPART = NQD / ND2, NCI = DIM * ND1, CH = (NCI + NPART - 1) / NPART;
-    double* part = gq;  // NQD doubles per element, free on this path
+    double* part = gq;  // NQD doubles per element, free here
     if (active) {
       const int j = tq % ND2, pc = tq / ND2;
       const float* fk = A.FK + el * (DIM * ND1 * ND2);
@@ -693,84 +835,29 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
       for (int pc = 1; pc < NPART; ++pc) s += part[pc * ND2 + tq];
       ftv[tq] = s;
     }
-  } else {
-    const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
-    double gw[DIM][DIM];
-    if constexpr (DIM == 2) {
-      double* TB = scr;
-      double* TG = scr + DIM * P * NQ;
-      if (active)
-        for (int w = tq; w < DIM * P * NQ; w += NQD) {
-          int x_ = w % NQ, b = (w / NQ) % P, f = w / (NQ * P);
-          double sb = 0.0, sg = 0.0;
-          for (int a = 0; a < P; ++a) {
-            double u = ws[f * ND1 + b * P + a];
-            sb += Bs[x_ * P + a] * u;
-            sg += Gs[x_ * P + a] * u;
-          }
-          TB[w] = sb;
-          TG[w] = sg;
-        }
+    if (pref != 0.0) {
+      // -p_ref alpha_q tr(adj(J) grad w) at the points, J from the FP64 positions
+      double grad[2 * DIM][DIM];
+      team_sync<NQD>();  // gq is reused
+      interp_grads<DIM, K, NQD, 2 * DIM>(ws, 2 * DIM, scr, Bs, Gs, tq, active, grad);
+      if (active) {
+        const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
+        double J[DIM][DIM], Aj[DIM][DIM];
+        for (int c = 0; c < DIM; ++c)
+          for (int m = 0; m < DIM; ++m) J[c][m] = grad[DIM + c][m];
+        adj_of<double, DIM>(J, Aj);
+        double tr = 0.0;
+        for (int c = 0; c < DIM; ++c)
+          for (int m = 0; m < DIM; ++m) tr += Aj[m][c] * grad[c][m];
+        const double alpha = Wd[qx] * Wd[qy] * (DIM == 3 ? Wd[qz] : 1.0);
+        gq[tq] = -pref * alpha * tr;
+      }
       team_sync<NQD>();
-      if (active)
-        for (int f = 0; f < DIM; ++f) {
-          double d0 = 0.0, d1 = 0.0;
-          for (int b = 0; b < P; ++b) {
-            d0 += Bs[qy * P + b] * TG[(f * P + b) * NQ + qx];
-            d1 += Gs[qy * P + b] * TB[(f * P + b) * NQ + qx];
-          }
-          gw[f][0] = d0;
-          gw[f][1] = d1;
-        }
-    } else {
-      double* TB = scr;
-      double* TG = TB + DIM * P * P * NQ;
-      double* PBB = TG + DIM * P * P * NQ;
-      double* PGB = PBB + DIM * P * NQ * NQ;
-      double* PBG = PGB + DIM * P * NQ * NQ;
-      if (active)
-        for (int w = tq; w < DIM * P * P * NQ; w += NQD) {
-          int x_ = w % NQ, r = w / NQ, b = r % P, fz = r / P;
-          int f = fz / P, cz = fz - f * P;
-          double sb = 0.0, sg = 0.0;
-          for (int a = 0; a < P; ++a) {
-            double u = ws[f * ND1 + (cz * P + b) * P + a];
-            sb += Bs[x_ * P + a] * u;
-            sg += Gs[x_ * P + a] * u;
-          }
-          TB[w] = sb;
-          TG[w] = sg;
-        }
-      team_sync<NQD>();
-      if (active)
-        for (int w = tq; w < DIM * P * NQ * NQ; w += NQD) {
-          int x_ = w % NQ, y_ = (w / NQ) % NQ, fz = w / (NQ * NQ);
-          double bb = 0.0, gb = 0.0, bg = 0.0;
-          for (int b = 0; b < P; ++b) {
-            double tb = TB[(fz * P + b) * NQ + x_], tg = TG[(fz * P + b) * NQ + x_];
-            bb += Bs[y_ * P + b] * tb;
-            gb += Bs[y_ * P + b] * tg;
-            bg += Gs[y_ * P + b] * tb;
-          }
-          PBB[w] = bb;
-          PGB[w] = gb;
-          PBG[w] = bg;
-        }
-      team_sync<NQD>();
-      if (active)
-        for (int f = 0; f < DIM; ++f) {
-          double d0 = 0.0, d1 = 0.0, d2 = 0.0;
-          for (int cz = 0; cz < P; ++cz) {
-            int idx = ((f * P + cz) * NQ + qy) * NQ + qx;
-            d0 += Bs[qz * P + cz] * PGB[idx];
-            d1 += Bs[qz * P + cz] * PBG[idx];
-            d2 += Gs[qz * P + cz] * PBB[idx];
-          }
-          gw[f][0] = d0;
-          gw[f][1] = d1;
-          gw[f][2] = d2;
-        }
+      l2_contract<DIM, K, NQD>(gq, l2s, Ls, tq, active, ftv, true);
     }
+  } else {
+    double gw[DIM][DIM];
+    interp_grads<DIM, K, NQD, DIM>(ws, DIM, scr, Bs, Gs, tq, active, gw);
     if (active) {
       const double* D = A.D + el * DIM * DIM * NQD;
       double s = 0.0;
@@ -779,51 +866,9 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
       gq[tq] = s;
     }
     team_sync<NQD>();
-    if constexpr (DIM == 2) {
-      if (active)
-        for (int w = tq; w < K * NQ; w += NQD) {
-          int y_ = w % NQ, jx = w / NQ;
-          double s = 0.0;
-          for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[y_ * NQ + x_];
-          l2s[w] = s;
-        }
-      team_sync<NQD>();
-      if (active)
-        for (int j = tq; j < ND2; j += NQD) {
-          int jx = j % K, jy = j / K;
-          double s = 0.0;
-          for (int y_ = 0; y_ < NQ; ++y_) s += Ls[y_ * K + jy] * l2s[jx * NQ + y_];
-          ftv[j] = s;
-        }
-    } else {
-      double* R1 = l2s;
-      double* R2 = l2s + K * NQ * NQ;
-      if (active)
-        for (int w = tq; w < K * NQ * NQ; w += NQD) {
-          int y_ = w % NQ, z_ = (w / NQ) % NQ, jx = w / (NQ * NQ);
-          double s = 0.0;
-          for (int x_ = 0; x_ < NQ; ++x_) s += Ls[x_ * K + jx] * gq[(z_ * NQ + y_) * NQ + x_];
-          R1[w] = s;
-        }
-      team_sync<NQD>();
-      if (active)
-        for (int w = tq; w < K * K * NQ; w += NQD) {
-          int z_ = w % NQ, jx = (w / NQ) % K, jy = w / (NQ * K);
-          double s = 0.0;
-          for (int y_ = 0; y_ < NQ; ++y_) s += Ls[y_ * K + jy] * R1[(jx * NQ + z_) * NQ + y_];
-          R2[w] = s;
-        }
-      team_sync<NQD>();
-      if (active)
-        for (int j = tq; j < ND2; j += NQD) {
-          int jx = j % K, jy = (j / K) % K, jz = j / (K * K);
-          double s = 0.0;
-          for (int z_ = 0; z_ < NQ; ++z_) s += Ls[z_ * K + jz] * R2[(jy * K + jx) * NQ + z_];
-          ftv[j] = s;
-        }
-    }
+    l2_contract<DIM, K, NQD>(gq, l2s, Ls, tq, active, ftv, false);
   }
-  if (active && tq == 0) crs[0] = A.rho0Kinv ? coef * A.rho0Kinv[el] : coef / prm.rho0K[el];
+  if (active && tq == 0) crs[0] = A.rho0Kinv ? coef * A.rho0Kinv[el] : coef / rho0Kp[el];
   team_sync<NQD>();
   if (active)
     for (int j = tq; j < ND2; j += NQD) {
@@ -832,7 +877,6 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
       for (int l = 0; l < ND2; ++l) {
         double rhs = ftv[l];
         if (A.srcE) rhs += A.srcE[el * ND2 + l];
-        if (A.prefE) rhs += A.prefE[el * ND2 + l];
         s = fma(Mi[j * ND2 + l], rhs, s);
       }
       A.e_out[el * ND2 + j] = fma(crs[0], s, A.e_base[el * ND2 + j]);

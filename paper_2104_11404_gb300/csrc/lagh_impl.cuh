@@ -222,7 +222,8 @@ struct EnergyArgs {
   const double* D;       // FP64 path
   const float* FK;       // mixed path
   const double* srcE;    // may be NULL
-  const double* prefE;   // mixed path: F^T w of the reference pressure (may be NULL)
+  const double* x;       // mixed path: positions of the force's state, for the F^T w of
+  const double* p_ref;   //   the reference pressure -p_ref I in FP64 (either NULL: none)
   const double* e_base;
   double* e_out;
   double frac;

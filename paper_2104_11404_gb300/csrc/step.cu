@@ -85,20 +85,6 @@ static int node_blocks(const lh_ctx* c, int64_t n) {
   return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
-// Mixed path: F^T w of the constant reference pressure -p_ref I (FP64), the
-// part of the stress the FP32 element matrices leave out.
-static cudaError_t launch_pref_ftv(lh_ctx* c, const double* v, const double* e, const double* x,
-                                   const double* w, double* out, cudaStream_t s) {
-  ForceArgs f = {};
-  f.v = v; f.e = e; f.x = x; f.vtest = w;
-  f.nslots = c->g.nelem;
-  f.FTvE = out;
-  f.ctl = c->a.ctl;
-  f.p_ref = &c->a.ctl->p_ref;
-  f.mode = kForceRefPressure;
-  return launch_force_fp64(c, f, s);
-}
-
 // CG of one stage: a WHILE graph node when capturing, else an eager loop.
 static cudaError_t stage_cg(lh_ctx* c, cudaStream_t s, bool capturing) {
   if (capturing) return cg_solve_capture(c, c->a.rhs, c->a.acc, c->a.ctl, s, c->side);
@@ -131,11 +117,11 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   if ((e = stage_cg(c, s, capturing)) != cudaSuccess) return e;
   stage1_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vh, A.xh, A.ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (mixed && (e = launch_pref_ftv(c, A.v, A.e, A.x, A.vh, A.tmpE, s)) != cudaSuccess) return e;
   EnergyArgs e1 = {};
   e1.w = A.vh; e1.D = A.D; e1.FK = A.FK;
   e1.srcE = c->ph.source ? A.srcE : nullptr;
-  e1.prefE = mixed ? A.tmpE : nullptr;
+  e1.x = mixed ? A.x : nullptr;  // the reference-pressure term uses the force's state
+  e1.p_ref = mixed ? &A.ctl->p_ref : nullptr;
   e1.e_base = A.e; e1.e_out = A.eh; e1.frac = 0.5; e1.dt = 0.0; e1.ctl = A.ctl;
   e1.rho0Kinv = A.rho0Kinv;
   if ((e = launch_energy_update(c, e1, s)) != cudaSuccess) return e;
@@ -149,10 +135,9 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   stage2_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vn, A.vbar,
                                                              A.xn, A.ctl);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (mixed && (e = launch_pref_ftv(c, A.vh, A.eh, A.xh, A.vbar, A.tmpE, s)) != cudaSuccess)
-    return e;
   EnergyArgs e2 = e1;
   e2.w = A.vbar; e2.e_out = A.en; e2.frac = 1.0;
+  e2.x = mixed ? A.xh : nullptr;
   if ((e = launch_energy_update(c, e2, s)) != cudaSuccess) return e;
   CtlConsts k;
   k.beta1 = c->phys_desc.beta1;
