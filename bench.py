@@ -258,6 +258,7 @@ def run_native(args):
     res = {p: measure(p) for p in ("mixed", "fp64")}
     batched = None if args.no_batch else measure_batched(args, stream, flush, max_over_ranks,
                                                          sum_over_ranks)
+    others = None if (args.no_configs or rank != 0) else measure_configs(stream)
     if rank != 0:
         return None
     m, f = res["mixed"], res["fp64"]
@@ -316,6 +317,8 @@ def run_native(args):
         "gpu_launches": int(launches),
         "clocks": m["clocks"],
     }
+    if others is not None:
+        line["configs"] = others
     if batched is not None:
         batched["config"] = ("512 independent 2D point-blast instances, E0 U[0.1,1], gamma "
                              "U[1.3,1.67], n x n quads with n from {16,24,32,48}, Q2/Q1, mixed, "
@@ -324,6 +327,54 @@ def run_native(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, bounded_seconds=12.0)
     return line
+
+
+CONFIG_WINDOW = {"sedov2d_8": 50, "sedov3d_32": 10, "gresho2d_256": 20}
+
+
+def measure_configs(stream):
+    """The other workloads, each through the single-problem path in both
+    precisions: a window of accepted steps from the initial state after three
+    warm-up steps, device time, throughput, the mixed state's relative L2
+    difference from the FP64 state after the same steps, and the mixed
+    total-energy drift (the problems without an energy source)."""
+    import numpy as np
+    import torch
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.hydro import Hydro
+    out = {}
+    for name, nsteps in CONFIG_WINDOW.items():
+        cfg = W.CONFIGS[name]
+        res = {}
+        states = {}
+        for prec in ("fp64", "mixed"):
+            with torch.cuda.stream(stream):
+                g = Hydro(cfg, precision=prec, stream=stream)
+                g.init_state()
+                E0 = g.total_energy()
+                g.run_to(cfg["t_final"], max_steps=3)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = g.run_to(cfg["t_final"], max_steps=nsteps)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                N = 2 * g.nv + g.ne
+                v, e, x, t, _ = g.get_state()
+                states[prec] = (v.cpu().numpy(), e.cpu().numpy(), t)
+                res[prec] = {"value": N * st["steps"] / (ms * 1e-3), "ms_per_step": ms / st["steps"],
+                             "cg_iters_per_step": st["cg_iters"] / max(1, st["steps"]),
+                             "energy_drift": abs(g.total_energy() - E0) / abs(E0)}
+                g.close()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(a), 1e-300))
+        out[name] = {"dofs": int(N), "time_steps": nsteps + 3,
+                     "fp64": res["fp64"], "mixed": res["mixed"],
+                     "speedup_mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+                     "mixed_vs_fp64_rel_l2": {"v": rel(states["fp64"][0], states["mixed"][0]),
+                                              "e": rel(states["fp64"][1], states["mixed"][1]),
+                                              "t_diff": abs(states["fp64"][2] - states["mixed"][2])}}
+    return out
 
 
 def batch_fp64_flops(cfgs):
@@ -549,6 +600,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (2D blast 8x8, 3D blast 32^3, Gresho 256^2 Q3)")
     ap.add_argument("--direct-launch", action="store_true",
                     help="launch the step's kernels one by one instead of one CUDA graph per "
                          "attempt (kernel profilers cannot see kernels inside graphs with "
