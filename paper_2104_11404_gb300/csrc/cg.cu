@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
                                                               int last, int init,
                                                               const double* src_in,
                                                               double* dst) {
+  pdl_enter();
   if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) return;
   if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
     a.cg->done = 0;
@@ -263,6 +264,7 @@ __global__ void __launch_bounds__(kLineThreadsX) cg_line_kernel(const CgArgs a, 
                                                                int last, int init,
                                                                const double* src_in,
                                                                double* dst) {
+  pdl_enter();
   if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) return;
   if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
     a.cg->done = 0;
@@ -364,6 +366,7 @@ __global__ void __launch_bounds__(kLineThreadsX) cg_line_kernel(const CgArgs a, 
 
 template <int DIM, int K>
 __global__ void __launch_bounds__(kNodeThreads) cg_jacobi_init_kernel(const CgArgs a) {
+  pdl_enter();
   if (a.gate != nullptr && a.gate->done) return;
   const Geom& g = a.g;
   double l_bb = 0.0, l_rz = 0.0;
@@ -407,6 +410,7 @@ __global__ void __launch_bounds__(kNodeThreads) cg_jacobi_init_kernel(const CgAr
 // p = z + beta p_old (beta = 0 on the first iteration, where p_old = z).
 template <int DIM, int K>
 __global__ void __launch_bounds__(256) cg_elem_kernel(const CgArgs a) {
+  pdl_enter();
   using L = ML<DIM, K>;
   constexpr int P = L::P, ND1 = L::ND1, EPB = L::EPB;
   if (gated(a)) return;
@@ -436,6 +440,7 @@ __global__ void __launch_bounds__(256) cg_elem_kernel(const CgArgs a) {
 
 template <int DIM, int K>
 __global__ void __launch_bounds__(kNodeThreads) cg_gather_kernel(const CgArgs a) {
+  pdl_enter();
   if (gated(a)) return;
   const Geom& g = a.g;
   const double beta = a.cg->beta;
@@ -461,6 +466,7 @@ __global__ void __launch_bounds__(kNodeThreads) cg_gather_kernel(const CgArgs a)
 // x += alpha p, r -= alpha Ap; convergence test; ends the WHILE loop.
 template <int DIM, int K>
 __global__ void __launch_bounds__(kNodeThreads) cg_update_kernel(const CgArgs a, int jacobi) {
+  pdl_enter();
   if (gated(a)) {
     if (blockIdx.x == 0 && threadIdx.x == 0 && a.has_cond) cudaGraphSetConditional(a.cond, 0);
     return;
@@ -506,6 +512,7 @@ __global__ void __launch_bounds__(kNodeThreads) cg_update_kernel(const CgArgs a,
 }
 
 __global__ void cg_reset_kernel(CgDev* cg, const Ctl* gate) {
+  pdl_enter();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     cg->done = 0;
     cg->it = 0;
@@ -565,8 +572,10 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
       const int64_t blocks = (int64_t)DIM * ((nlines + kLineGroup - 1) / kLineGroup);
       const int mode = d == 0 ? (init ? 0 : 1) : 2;
       double* dst = bufs[(DIM - 1 - d) & 1];
-      cg_line_kernel<DIM, K><<<(unsigned)blocks, kLineThreadsX, line_smem(c, d), s>>>(
-          a, d, mode, d == DIM - 1, init ? 1 : 0, src, dst);
+      cudaError_t e = launch_k(c->use_pdl != 0, cg_line_kernel<DIM, K>, dim3((unsigned)blocks),
+                               dim3(kLineThreadsX), line_smem(c, d), s, a, d, mode,
+                               (int)(d == DIM - 1), init ? 1 : 0, src, dst);
+      if (e != cudaSuccess) return e;
       src = dst;
     }
     return cudaGetLastError();
@@ -577,8 +586,10 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
     const int64_t blocks = (int64_t)DIM * ((nlines + 31) / 32) * ((nd + 31) / 32);
     const int mode = d == 0 ? (init ? 0 : 1) : 2;
     double* dst = bufs[(DIM - 1 - d) & 1];
-    cg_pass_kernel<DIM, K><<<(unsigned)blocks, kLineThreads, 0, s>>>(a, d, mode, d == DIM - 1,
-                                                                    init ? 1 : 0, src, dst);
+    cudaError_t e = launch_k(c->use_pdl != 0, cg_pass_kernel<DIM, K>, dim3((unsigned)blocks),
+                             dim3(kLineThreads), 0, s, a, d, mode, (int)(d == DIM - 1),
+                             init ? 1 : 0, src, dst);
+    if (e != cudaSuccess) return e;
     src = dst;
   }
   return cudaGetLastError();
@@ -587,19 +598,24 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
 template <int DIM, int K>
 static cudaError_t cg_init_dk(const lh_ctx* c, const CgArgs& a, cudaStream_t s) {
   if (c->tpc.enabled) return precond_passes<DIM, K>(c, a, true, s);
-  cg_reset_kernel<<<1, 32, 0, s>>>(c->a.cg, a.gate);
-  cg_jacobi_init_kernel<DIM, K><<<node_grid(c), kNodeThreads, 0, s>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = launch_k(c->use_pdl != 0, cg_reset_kernel, dim3(1), dim3(32), 0, s, c->a.cg,
+                           a.gate);
+  if (e != cudaSuccess) return e;
+  return launch_k(c->use_pdl != 0, cg_jacobi_init_kernel<DIM, K>, dim3(node_grid(c)),
+                  dim3(kNodeThreads), 0, s, a);
 }
 
 template <int DIM, int K>
 static cudaError_t cg_body_dk(const lh_ctx* c, const CgArgs& a, cudaStream_t s) {
   using L = ML<DIM, K>;
   const int eblocks = (int)((c->g.nelem + L::EPB - 1) / L::EPB);
-  cg_elem_kernel<DIM, K><<<eblocks, 256, 0, s>>>(a);
-  cg_gather_kernel<DIM, K><<<node_grid(c), kNodeThreads, 0, s>>>(a);
-  cg_update_kernel<DIM, K><<<node_grid(c), kNodeThreads, 0, s>>>(a, c->tpc.enabled ? 0 : 1);
-  cudaError_t e = cudaGetLastError();
+  const bool pdl = c->use_pdl != 0;
+  cudaError_t e = launch_k(pdl, cg_elem_kernel<DIM, K>, dim3(eblocks), dim3(256), 0, s, a);
+  if (e == cudaSuccess)
+    e = launch_k(pdl, cg_gather_kernel<DIM, K>, dim3(node_grid(c)), dim3(kNodeThreads), 0, s, a);
+  if (e == cudaSuccess)
+    e = launch_k(pdl, cg_update_kernel<DIM, K>, dim3(node_grid(c)), dim3(kNodeThreads), 0, s, a,
+                 c->tpc.enabled ? 0 : 1);
   if (e != cudaSuccess) return e;
   if (c->tpc.enabled) {
     if ((e = precond_passes<DIM, K>(c, a, false, s)) != cudaSuccess) return e;

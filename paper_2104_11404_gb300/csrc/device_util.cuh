@@ -10,6 +10,21 @@
 
 namespace lagh {
 
+// ------------------------------------------------- dependent launches ----
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialisation attribute may be launched while its predecessor
+// drains; it waits here (in hardware) until the predecessor has completed and
+// its memory is visible.  Without the attribute it is a no-op.  Every kernel
+// of the step calls pdl_enter() before touching memory.  An explicit early
+// trigger (pdl_launch_dependents) was measured slower on the 64x64 step (the
+// waiting successor's blocks compete with the running grid), so the trigger
+// stays implicit at grid completion.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+__device__ __forceinline__ void pdl_enter() { pdl_wait(); }
+
 // ---------------------------------------------------------------- mesh ----
 
 // Node multi-index (I, J, K) of a lexicographic node number.

@@ -34,8 +34,7 @@ static cudaError_t launch_force_t(const lh_ctx* c, const ForceArgs& fa, cudaStre
   prm.a = fa;
   prm.rho0K = c->a.rho0K;
   int64_t blocks = (fa.nslots + F::EPB - 1) / F::EPB;
-  kern<<<(unsigned)blocks, F::NT, F::BYTES, s>>>(prm);
-  return cudaGetLastError();
+  return launch_k(c->use_pdl != 0, kern, dim3((unsigned)blocks), dim3(F::NT), F::BYTES, s, prm);
 }
 
 #define LAGH_DISPATCH(DIMV, KV, FN, ...)                                            \
@@ -72,8 +71,8 @@ static cudaError_t launch_gather_dk(const lh_ctx* c, const double* E, double* ou
                                     int apply_bc, const Ctl* ctl, cudaStream_t s) {
   const int nt = 256;
   int64_t blocks = (c->g.nnodes + nt - 1) / nt;
-  gather_kernel<DIM, K><<<(unsigned)blocks, nt, 0, s>>>(c->g, E, out, scale, apply_bc, ctl);
-  return cudaGetLastError();
+  return launch_k(c->use_pdl != 0, gather_kernel<DIM, K>, dim3((unsigned)blocks), dim3(nt), 0, s,
+                  c->g, E, out, scale, apply_bc, ctl);
 }
 
 cudaError_t launch_gather(const lh_ctx* c, const double* E, double* out, double scale,
@@ -91,8 +90,7 @@ static cudaError_t launch_energy_t(const lh_ctx* c, const EnergyArgs& ea, cudaSt
   prm.a = ea;
   prm.rho0K = c->a.rho0K;
   int64_t blocks = (c->g.nelem + F::EPB - 1) / F::EPB;
-  kern<<<(unsigned)blocks, F::NT, F::BYTES, s>>>(prm);
-  return cudaGetLastError();
+  return launch_k(c->use_pdl != 0, kern, dim3((unsigned)blocks), dim3(F::NT), F::BYTES, s, prm);
 }
 
 template <int DIM, int K>

@@ -564,6 +564,7 @@ l2_part:
 template <int DIM, int K, bool MIXED>
 __global__ void __launch_bounds__(FL<DIM, K, MIXED>::NT)
 force_kernel(const ForceKParams prm) {
+  pdl_enter();
   using F = FL<DIM, K, MIXED>;
   if (prm.a.ctl != nullptr && prm.a.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -578,6 +579,7 @@ force_kernel(const ForceKParams prm) {
 template <int DIM, int K>
 __global__ void gather_kernel(Geom g, const double* __restrict__ E, double* __restrict__ out,
                               double scale, int apply_bc, const Ctl* ctl) {
+  pdl_enter();
   if (ctl != nullptr && ctl->done) return;
   int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (node >= g.nnodes) return;
@@ -887,6 +889,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
 template <int DIM, int K, bool MIXED>
 __global__ void __launch_bounds__(EL<DIM, K, MIXED>::NT)
 energy_update_kernel(const EnergyKParams prm) {
+  pdl_enter();
   using F = EL<DIM, K, MIXED>;
   if (prm.a.ctl != nullptr && prm.a.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem[];

@@ -164,11 +164,30 @@ struct lh_ctx {
   int own_work;               // work stream created by the context
   cudaGraphExec_t step_graph;
   int graph_ready;            // 1: graph built, -1: capture unsupported (eager launches)
+  int use_pdl;                // programmatic dependent launch between the step's kernels
   cudaEvent_t ev0, ev1;
   std::string err;
 };
 
 namespace lagh {
+
+// Launches kern on s, with programmatic dependent launch when pdl is set (the
+// kernel must call pdl_enter() first; see device_util.cuh).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
 
 // ---- host helpers (setup.cu) ----
 lh_status set_error(lh_ctx* c, lh_status s, const std::string& msg);

@@ -353,6 +353,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   memset(&c->a, 0, sizeof(c->a));
   c->ctl_host = nullptr;
   c->graph_ready = 0;
+  c->use_pdl = 1;
   c->ev0 = c->ev1 = nullptr;
   c->work = nullptr;
   c->side = nullptr;

@@ -20,6 +20,7 @@ __global__ void stage1_update_kernel(int64_t nv, const double* __restrict__ v,
                                      const double* __restrict__ x, const double* __restrict__ a,
                                      double* __restrict__ vh, double* __restrict__ xh,
                                      const Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   const double hdt = 0.5 * ctl->dt_use;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv;
@@ -34,6 +35,7 @@ __global__ void stage2_update_kernel(int64_t nv, const double* __restrict__ v,
                                      const double* __restrict__ x, const double* __restrict__ a,
                                      double* __restrict__ vn, double* __restrict__ vbar,
                                      double* __restrict__ xn, const Ctl* ctl) {
+  pdl_enter();
   if (ctl->done) return;
   const double dt = ctl->dt_use;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv;
@@ -47,6 +49,7 @@ __global__ void stage2_update_kernel(int64_t nv, const double* __restrict__ v,
 }
 
 __global__ void control_kernel(Ctl* ctl, CtlConsts k) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   control_update(ctl, k);
 }
@@ -55,6 +58,7 @@ __global__ void commit_kernel(int64_t nv, int64_t ne, double* __restrict__ v, do
                               double* __restrict__ e, const double* __restrict__ vn,
                               const double* __restrict__ xn, const double* __restrict__ en,
                               const Ctl* ctl) {
+  pdl_enter();
   if (!ctl->accepted) return;
   int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
@@ -68,11 +72,13 @@ __global__ void commit_kernel(int64_t nv, int64_t ne, double* __restrict__ v, do
 __global__ void begin_kernel(Ctl* ctl, double t_final, long long max_steps, double dt_min,
                              int fixed, double dt_fixed, double* dt_log, long long dt_log_cap,
                              const unsigned long long* est_bits) {
+  pdl_enter();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   control_begin(ctl, t_final, max_steps, dt_min, fixed, dt_fixed, dt_log, dt_log_cap, est_bits);
 }
 
 __global__ void set_bits_kernel(unsigned long long* p, unsigned long long v, int* flag) {
+  pdl_enter();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     *p = v;
     if (flag) *flag = 0;
@@ -115,8 +121,10 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   if ((e = launch_force(c, f1, s)) != cudaSuccess) return e;
   if ((e = launch_gather(c, A.F1E, A.rhs, -1.0, 1, A.ctl, s)) != cudaSuccess) return e;
   if ((e = stage_cg(c, s, capturing)) != cudaSuccess) return e;
-  stage1_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vh, A.xh, A.ctl);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const bool pdl = c->use_pdl != 0;
+  e = launch_k(pdl, stage1_update_kernel, dim3(node_blocks(c, g.nv)), dim3(256), 0, s, g.nv, A.v,
+               A.x, A.acc, A.vh, A.xh, A.ctl);
+  if (e != cudaSuccess) return e;
   EnergyArgs e1 = {};
   e1.w = A.vh; e1.D = A.D; e1.FK = A.FK;
   e1.srcE = c->ph.source ? A.srcE : nullptr;
@@ -132,9 +140,9 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   if ((e = launch_force(c, f2, s)) != cudaSuccess) return e;
   if ((e = launch_gather(c, A.F1E, A.rhs, -1.0, 1, A.ctl, s)) != cudaSuccess) return e;
   if ((e = stage_cg(c, s, capturing)) != cudaSuccess) return e;
-  stage2_update_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, A.v, A.x, A.acc, A.vn, A.vbar,
-                                                             A.xn, A.ctl);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  e = launch_k(pdl, stage2_update_kernel, dim3(node_blocks(c, g.nv)), dim3(256), 0, s, g.nv, A.v,
+               A.x, A.acc, A.vn, A.vbar, A.xn, A.ctl);
+  if (e != cudaSuccess) return e;
   EnergyArgs e2 = e1;
   e2.w = A.vbar; e2.e_out = A.en; e2.frac = 1.0;
   e2.x = mixed ? A.xh : nullptr;
@@ -143,11 +151,31 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   k.beta1 = c->phys_desc.beta1;
   k.beta2 = c->phys_desc.beta2;
   k.gamma_dt = c->phys_desc.gamma_dt;
-  control_kernel<<<1, 32, 0, s>>>(A.ctl, k);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  commit_kernel<<<node_blocks(c, g.nv), 256, 0, s>>>(g.nv, g.ne, A.v, A.x, A.e, A.vn, A.xn, A.en,
-                                                      A.ctl);
-  return cudaGetLastError();
+  e = launch_k(pdl, control_kernel, dim3(1), dim3(32), 0, s, A.ctl, k);
+  if (e != cudaSuccess) return e;
+  return launch_k(pdl, commit_kernel, dim3(node_blocks(c, g.nv)), dim3(256), 0, s, g.nv, g.ne, A.v,
+                  A.x, A.e, (const double*)A.vn, (const double*)A.xn, (const double*)A.en,
+                  (const Ctl*)A.ctl);
+}
+
+static cudaError_t capture_attempt(lh_ctx* c, const char** where) {
+  cudaGraph_t graph = nullptr;
+  *where = "begin capture";
+  cudaError_t e = cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaError_t e2 = enqueue_attempt(c, c->work, true);
+    *where = "enqueue";
+    e = cudaStreamEndCapture(c->work, &graph);
+    if (e2 != cudaSuccess) e = e2;
+    else *where = "end capture";
+  }
+  if (e == cudaSuccess) {
+    *where = "instantiate";
+    e = cudaGraphInstantiate(&c->step_graph, graph, 0);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
 }
 
 static lh_status build_graph(lh_ctx* c) {
@@ -156,26 +184,16 @@ static lh_status build_graph(lh_ctx* c) {
     c->graph_ready = -1;
     return LH_OK;
   }
-  cudaGraph_t graph = nullptr;
-  const char* where = "begin capture";
-  cudaError_t e = cudaStreamBeginCapture(c->work, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    cudaError_t e2 = enqueue_attempt(c, c->work, true);
-    where = "enqueue";
-    e = cudaStreamEndCapture(c->work, &graph);
-    if (e2 != cudaSuccess) e = e2;
-    else where = "end capture";
+  const char* where = "";
+  cudaError_t e = capture_attempt(c, &where);
+  if (e != cudaSuccess && c->use_pdl) {  // retry without programmatic dependent launch
+    c->use_pdl = 0;
+    e = capture_attempt(c, &where);
   }
-  if (e == cudaSuccess) {
-    where = "instantiate";
-    e = cudaGraphInstantiate(&c->step_graph, graph, 0);
-  }
-  if (graph) cudaGraphDestroy(graph);
   if (e == cudaSuccess) {
     c->graph_ready = 1;
   } else {
-    cudaGetLastError();  // capture not available: launch the sequence eagerly
-    c->graph_ready = -1;
+    c->graph_ready = -1;  // capture not available: launch the sequence eagerly
     fprintf(stderr, "lagh: step graph not built at %s (%s); launching kernels directly\n",
             where, cudaGetErrorString(e));
   }
