@@ -112,17 +112,17 @@ typedef struct lh_phys_desc {
   double q1, q2;         /* linear and quadratic viscosity coefficients */
   double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2 */
   double dt_min_frac;    /* dt < dt_min_frac * t_final -> LH_EDTMIN */
-  int32_t cg_precond;    /* LH_PRECOND_EXACT (default), LH_PRECOND_TENSOR or LH_PRECOND_JACOBI */
+  int32_t cg_precond;    /* LH_PRECOND_TENSOR (default), LH_PRECOND_EXACT or LH_PRECOND_JACOBI */
   int32_t direct_launch; /* 0 (default): each step attempt is one CUDA graph launch
                             (the CG iterations a WHILE node inside it); 1: the same
                             kernels launched one by one, with a host poll of the CG
                             between iteration batches (for kernel profilers) */
+  int32_t cg_cluster;    /* 0 (default): the whole velocity solve of a small 2D problem
+                            (N_V <= 6,000, tensor preconditioner) runs as one launch of a
+                            thread-block cluster when the device allows it; 1: whenever it
+                            can (any 2D size); -1: never (one kernel per CG phase) */
 } lh_phys_desc;
 
-/* Preconditioners of the velocity CG.  TENSOR: the exact inverse of the
- * kinematic mass matrix when rho0 |J0| is the same in every element (then
- * M_V is a Kronecker product of assembled 1D mass matrices), applied by
- * banded 1D line solves; JACOBI: the inverse diagonal. */
 /* Velocity CG preconditioners.  With rho0 |J0| the same in every element (every
  * problem of Section 6.1 on a Cartesian box), M_V restricted to the free
  * entries of a component is rho0 |J0| times a Kronecker product of assembled

@@ -17,6 +17,8 @@
 //    lines and its halo staged in shared memory).  The CG converges in about
 //    three iterations (Jacobi needs ~28 on the 64x64 Taylor-Green mesh);
 //  - Jacobi: the inverse assembled diagonal.
+#include <cooperative_groups.h>
+
 #include "line_solve.cuh"
 #include "mass_ops.cuh"
 
@@ -118,31 +120,40 @@ __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
 // on free components and x = 0, sums b.b), 1 = first pass inside the loop
 // (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
 // last: the pass along the last direction (sums r.z; init also writes p = z).
+// Shared memory of one band-pass tile: 32 lines x (32 positions + halo) of
+// input and the band rows of the 32 positions.
+template <int K>
+struct PassTile {
+  static constexpr int B = PB<K>::B, W = 2 * B + 1, TP = 32, ldt = TP + 2 * B + 1;
+  float tile[32 * ldt];
+  float wrows[TP * W];
+};
+
+template <int DIM>
+__device__ __forceinline__ int64_t pass_tiles(const Geom& g, int d) {
+  const int nd = g.nn[d];
+  const int64_t nlines = g.nnodes / nd;
+  return (int64_t)DIM * ((nlines + 31) / 32) * ((nd + 31) / 32);
+}
+
+// One tile of a band pass along direction d (all threads of the block): the
+// tile's outputs dst = band-inverse(src) and, per mode, r / x / p writes and
+// the partial sums b.b (mode 0) and r.z (last), added to l_bb / l_rz.
 template <int DIM, int K>
-__global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, int d, int mode,
-                                                              int last, int init,
-                                                              const double* src_in,
-                                                              double* dst) {
-  pdl_enter();
-  if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) return;
-  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
-    a.cg->done = 0;
-    a.cg->it = 0;
-  }
-  constexpr int B = PB<K>::B;
-  constexpr int W = 2 * B + 1;
-  constexpr int TP = 32;
-  constexpr int ldt = TP + 2 * B + 1;  // odd row length
-  __shared__ float tile[32 * ldt];     // 32 lines x (32 positions + halo)
-  __shared__ float wrows[TP * W];      // band rows of the 32 positions
+__device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int last, int init,
+                                          const double* src_in, double* dst, int64_t bid,
+                                          PassTile<K>& sm, double& l_bb, double& l_rz) {
+  using PT = PassTile<K>;
+  constexpr int B = PT::B, W = PT::W, TP = PT::TP, ldt = PT::ldt;
+  float* tile = sm.tile;
+  float* wrows = sm.wrows;
   const Geom& g = a.g;
   const int nd = g.nn[d];
   const int64_t nlines = g.nnodes / nd;
   const int64_t lgroups = (nlines + 31) / 32;
   const int pblocks = (nd + TP - 1) / TP;
   const int64_t stride = d == 0 ? 1 : (d == 1 ? (int64_t)g.nn[0] : (int64_t)g.nn[0] * g.nn[1]);
-  // block -> (component, line group, position block)
-  int64_t bid = blockIdx.x;
+  // tile -> (component, line group, position block)
   const int pb = (int)(bid % pblocks);
   bid /= pblocks;
   const int64_t lg = bid % lgroups;
@@ -150,7 +161,7 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
   const int p0 = pb * TP;
   const int var = (c == d) ? 1 : 0;
   const float* Wt = a.lfac + a.tpc.off[d][var];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
   // line l of the tile: its base node and whether it is a wall-normal line
   auto line_info = [&](int l, int64_t& base, bool& wall) -> bool {
     const int64_t line = lg * 32 + l;
@@ -165,10 +176,9 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
   };
   const double* src = mode == 0 ? a.rhs : src_in;
   const float scl = (mode == 2) ? 1.0f : (float)a.tpc.scale;
-  double l_bb = 0.0, l_rz = 0.0;
   // stage the tile with its halo: positions [p0 - B, p0 + TP + B)
   const int span = TP + 2 * B;
-  for (int idx = tid; idx < 32 * span; idx += kLineThreads) {
+  for (int idx = tid; idx < 32 * span; idx += nt) {
     // along x (d == 0) walk a line, otherwise walk across lines
     const int l = d == 0 ? idx / span : idx % 32;
     const int q = d == 0 ? idx - l * span : idx / 32;
@@ -184,15 +194,14 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
   }
   {
     const int nrow = nd - 2 * var;  // rows of the band (interior positions)
-    for (int idx = tid; idx < TP * W; idx += kLineThreads) {
+    for (int idx = tid; idx < TP * W; idx += nt) {
       const int q = idx / W, m = idx - q * W;
       const int row = p0 + q - var;
       wrows[idx] = (row >= 0 && row < nrow) ? Wt[(int64_t)row * W + m] : 0.0f;
     }
   }
   __syncthreads();
-  // outputs: thread -> (line, 4 positions)
-  for (int o = tid; o < 32 * TP; o += kLineThreads) {
+  for (int o = tid; o < 32 * TP; o += nt) {
     const int l = d == 0 ? o / TP : o % 32;
     const int q = d == 0 ? o - l * TP : o / 32;
     const int pos = p0 + q;
@@ -222,7 +231,34 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
       if (init) a.p[kk] = zv;
     }
   }
+  __syncthreads();  // the tile buffers are reused by the next tile
+}
 
+// One pass of the tensor-product preconditioner along direction d: every
+// node line of every component is multiplied by the banded inverse of the 1D
+// mass matrix.  A CTA owns a tile of 32 lines x 32 positions: it stages the
+// tile and its +-B halo along the line in shared memory (coalesced: along x
+// the lines are contiguous rows, along y / z neighbouring lines are
+// neighbouring nodes), then each thread forms 4 outputs in FP32.
+//
+// mode: 0 = first pass of the initial preconditioning (reads rhs, writes r = b
+// on free components and x = 0, sums b.b), 1 = first pass inside the loop
+// (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
+// last: the pass along the last direction (sums r.z; init also writes p = z).
+template <int DIM, int K>
+__global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, int d, int mode,
+                                                              int last, int init,
+                                                              const double* src_in,
+                                                              double* dst) {
+  pdl_enter();
+  if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) return;
+  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
+    a.cg->done = 0;
+    a.cg->it = 0;
+  }
+  __shared__ PassTile<K> sm;
+  double l_bb = 0.0, l_rz = 0.0;
+  pass_tile<DIM, K>(a, d, mode, last, init, src_in, dst, (int64_t)blockIdx.x, sm, l_bb, l_rz);
   double tot;
   if (mode == 0) {
     if (reduce_last(l_bb, a.part, &a.cg->ticket[kTicketPass0], &tot) && threadIdx.x == 0)
@@ -360,6 +396,158 @@ __global__ void __launch_bounds__(kLineThreadsX) cg_line_kernel(const CgArgs a, 
       }
     }
   }
+}
+
+// ------------------------------------------------ cluster-resident CG ----
+
+// The whole solve of a small problem in one launch: a cluster of CTAs (16
+// where the device allows it, else 8) runs the initial preconditioning and
+// every iteration, separated by hardware cluster barriers, with the sums
+// reduced through distributed shared memory in rank order (every CTA gets the
+// same, deterministic value).  Same algorithm and arithmetic as the kernel
+// chain (tensor-product band preconditioner, element PA apply, node gather),
+// without a launch per phase.
+namespace cgx = cooperative_groups;
+constexpr int kClusterThreads = 256;
+
+__device__ __forceinline__ double block_sum_all(double v) {
+  __shared__ double sh[32];
+  __shared__ double res;
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) res = s;
+  __syncthreads();
+  return res;
+}
+
+// Sum of v over the cluster (every thread of every CTA calls it); slot: this
+// reduction's word of shared memory.  Ends with every CTA past a cluster
+// barrier, so all global writes made before the call are visible after it.
+__device__ __forceinline__ double cluster_sum(cgx::cluster_group& cl, double v, double* slot) {
+  const double s = block_sum_all(v);
+  if (threadIdx.x == 0) *slot = s;
+  cl.sync();
+  double tot = 0.0;
+  for (unsigned r = 0; r < cl.num_blocks(); ++r) tot += *cl.map_shared_rank(slot, r);
+  return tot;
+}
+
+// A p element by element (one thread per element and component, the element
+// operator in registers): ApE[el][c][i] = rho0K[el] ((M1 x M1) p_K)_i.
+template <int K>
+__device__ __forceinline__ void elem_apply_2d(const Geom& g, const double* M1s, const double* p,
+                                              const double* rho0K, double* ApE, int64_t i0,
+                                              int64_t stride) {
+  constexpr int P = K + 1, ND1 = P * P;
+  for (int64_t item = i0; item < g.nelem * 2; item += stride) {
+    const int64_t el = item >> 1;
+    const int c = (int)(item & 1);
+    int E[3] = {0, 0, 0};
+    elem_ijk(g, el, E);
+    const double* pc = p + c * g.nnodes;
+    double t[P][P];
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      double u[P];
+#pragma unroll
+      for (int a = 0; a < P; ++a) u[a] = pc[elem_node<K>(g, E, a, b, 0)];
+#pragma unroll
+      for (int ap = 0; ap < P; ++ap) {
+        double acc = 0.0;
+#pragma unroll
+        for (int a = 0; a < P; ++a) acc = fma(M1s[ap * P + a], u[a], acc);
+        t[b][ap] = acc;
+      }
+    }
+    const double w = rho0K[el];
+    double* out = ApE + (el * 2 + c) * ND1;
+#pragma unroll
+    for (int bp = 0; bp < P; ++bp)
+#pragma unroll
+      for (int ap = 0; ap < P; ++ap) {
+        double acc = 0.0;
+#pragma unroll
+        for (int b = 0; b < P; ++b) acc = fma(M1s[bp * P + b], t[b][ap], acc);
+        out[bp * P + ap] = w * acc;
+      }
+  }
+}
+
+template <int DIM, int K>
+__global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(const CgArgs a) {
+  pdl_enter();
+  if (a.gate != nullptr && a.gate->done) return;  // the same in every CTA
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int64_t rank = cl.block_rank(), nrank = cl.num_blocks();
+  __shared__ PassTile<K> sm;
+  __shared__ double M1s[(K + 1) * (K + 1)];
+  __shared__ double slots[4];
+  constexpr int P = K + 1;
+  const Geom& g = a.g;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int64_t i0 = rank * nt + tid, stride = nrank * nt;
+  for (int i = tid; i < P * P; i += nt) M1s[i] = a.M1[(i / P) * (kMaxOrder + 1) + i % P];
+  const int64_t tiles0 = pass_tiles<DIM>(g, 0), tiles1 = pass_tiles<DIM>(g, 1);
+  // initial preconditioning: r = b, x = 0, z = B r (x pass into Ap, y pass
+  // into z), p = z
+  double l_bb = 0.0, l_rz = 0.0;
+  for (int64_t t = rank; t < tiles0; t += nrank)
+    pass_tile<DIM, K>(a, 0, 0, 0, 1, nullptr, a.Ap, t, sm, l_bb, l_rz);
+  const double bb = cluster_sum(cl, l_bb, &slots[0]);
+  for (int64_t t = rank; t < tiles1; t += nrank)
+    pass_tile<DIM, K>(a, 1, 2, 1, 1, a.Ap, a.z, t, sm, l_bb, l_rz);
+  double rz = cluster_sum(cl, l_rz, &slots[1]);
+  int it = 0;
+  double rr = bb;
+  bool conv = !(bb > 0.0);
+  while (!conv && it < a.maxit) {
+    ++it;
+    elem_apply_2d<K>(g, M1s, a.p, a.rho0K, a.ApE, i0, stride);
+    cl.sync();
+    double l = 0.0;
+    for (int64_t node = i0; node < g.nnodes; node += stride) {
+      int I[3];
+      node_ijk(g, node, I);
+      for (int c = 0; c < DIM; ++c) {
+        const int64_t k = c * g.nnodes + node;
+        const double ap = essential(g, I, c) ? 0.0 : gather_node<DIM, K>(g, a.ApE, I, c);
+        a.Ap[k] = ap;
+        l += a.p[k] * ap;
+      }
+    }
+    const double alpha = rz / cluster_sum(cl, l, &slots[2]);
+    l = 0.0;
+    for (int64_t k = i0; k < g.nv; k += stride) {
+      a.x[k] += alpha * a.p[k];
+      const double rv = a.r[k] - alpha * a.Ap[k];
+      a.r[k] = rv;
+      l += rv * rv;
+    }
+    rr = cluster_sum(cl, l, &slots[3]);
+    conv = rr <= a.rtol * a.rtol * bb;
+    if (conv || !(rr == rr)) break;
+    double unused = 0.0, l_rz2 = 0.0;
+    for (int64_t t = rank; t < tiles0; t += nrank)
+      pass_tile<DIM, K>(a, 0, 1, 0, 0, a.r, a.Ap, t, sm, unused, l_rz2);
+    cl.sync();
+    for (int64_t t = rank; t < tiles1; t += nrank)
+      pass_tile<DIM, K>(a, 1, 2, 1, 0, a.Ap, a.z, t, sm, unused, l_rz2);
+    const double rz_new = cluster_sum(cl, l_rz2, &slots[0]);
+    const double beta = rz_new / rz;
+    rz = rz_new;
+    for (int64_t k = i0; k < g.nv; k += stride) a.p[k] = a.z[k] + beta * a.p[k];
+    cl.sync();
+  }
+  if (rank == 0 && tid == 0) {
+    CgDev* cgd = a.cg;
+    cgd->it = it;
+    cgd->bb = bb;
+    cgd->done = 1;
+    a.ctl->cg_last_iters = it;
+    a.ctl->cg_last_relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    a.ctl->cg_iters += it;
+    if (!conv) atomicOr(&a.ctl->status, kDevCG);
+  }
+  cl.sync();  // no CTA leaves while others may still read its shared memory
 }
 
 // ------------------------------------------------------- Jacobi init ----
@@ -671,11 +859,82 @@ cudaError_t precond_apply(const lh_ctx* c, const double* in, double* out, cudaSt
   LAGH_DISPATCH_CG(precond_apply_dk, c, in, out, s);
 }
 
+// The cluster-resident solve: one launch of a cluster of c->cg_cluster CTAs.
+template <int DIM, int K>
+static cudaError_t cluster_launch_dk(const lh_ctx* c, const CgArgs& a, cudaStream_t s) {
+  if constexpr (DIM != 2) {
+    return cudaErrorInvalidValue;
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)c->cg_cluster);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c->cg_cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->use_pdl ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, cg_cluster_kernel<DIM, K>, a);
+  }
+}
+
+static cudaError_t cluster_launch(const lh_ctx* c, const CgArgs& a, cudaStream_t s) {
+  LAGH_DISPATCH_CG(cluster_launch_dk, c, a, s);
+}
+
+// Cluster size for the cluster-resident solve of this context (0: not used).
+template <int DIM, int K>
+static int cluster_choose_dk(const lh_ctx* c) {
+  if constexpr (DIM != 2) {
+    return 0;
+  } else {
+    auto kern = cg_cluster_kernel<DIM, K>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaSuccess)
+      cudaGetLastError();
+    for (int n : {16, 8}) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)n);
+      cfg.blockDim = dim3(kClusterThreads);
+      cudaLaunchAttribute at;
+      at.id = cudaLaunchAttributeClusterDimension;
+      at.val.clusterDim.x = (unsigned)n;
+      at.val.clusterDim.y = 1;
+      at.val.clusterDim.z = 1;
+      cfg.attrs = &at;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0)
+        return n;
+      cudaGetLastError();
+    }
+    return 0;
+  }
+}
+
+int cg_cluster_choose(const lh_ctx* c) {
+  const int D_ = c->g.dim, K_ = c->g.k;
+  if (D_ == 2 && K_ == 1) return cluster_choose_dk<2, 1>(c);
+  if (D_ == 2 && K_ == 2) return cluster_choose_dk<2, 2>(c);
+  if (D_ == 2 && K_ == 3) return cluster_choose_dk<2, 3>(c);
+  return 0;
+}
+
 // Eager solve (API): the body is launched in batches and the host polls the
-// done flag between batches.
+// done flag between batches (or one cluster-resident launch).
 cudaError_t cg_solve_eager(const lh_ctx* c, const double* rhs, double* out, cudaStream_t s,
                            int* done_host) {
   CgArgs a = make_args(c, rhs, out, nullptr);
+  if (c->cg_cluster > 0) {
+    cudaError_t e = cluster_launch(c, a, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(done_host, &c->a.cg->done, sizeof(int),
+                                              cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? cudaStreamSynchronize(s) : e;
+  }
   cudaError_t e = cg_init(c, a, s);
   if (e != cudaSuccess) return e;
   for (int it = 0; it < c->cg_maxit + 1; it += 8) {
@@ -694,6 +953,7 @@ cudaError_t cg_solve_eager(const lh_ctx* c, const double* rhs, double* out, cuda
 cudaError_t cg_solve_capture(const lh_ctx* c, const double* rhs, double* out, const Ctl* gate,
                              cudaStream_t s, cudaStream_t side) {
   CgArgs a = make_args(c, rhs, out, gate);
+  if (c->cg_cluster > 0) return cluster_launch(c, a, s);  // one node, no conditional
   cudaError_t e = cg_init(c, a, s);
   if (e != cudaSuccess) return e;
   cudaStreamCaptureStatus cs;

@@ -165,6 +165,7 @@ struct lh_ctx {
   cudaGraphExec_t step_graph;
   int graph_ready;            // 1: graph built, -1: capture unsupported (eager launches)
   int use_pdl;                // programmatic dependent launch between the step's kernels
+  int cg_cluster;             // CTAs of the cluster-resident CG (0: kernel chain)
   cudaEvent_t ev0, ev1;
   std::string err;
 };
@@ -267,5 +268,7 @@ cudaError_t launch_total_energy(const lh_ctx* c, const double* v, const double* 
                                 cudaStream_t s);
 cudaError_t prepare_kernels(const lh_ctx* c);
 cudaError_t cg_prepare(const lh_ctx* c);
+// Cluster size the cluster-resident CG can use on this device (16 or 8), 0 if none.
+int cg_cluster_choose(const lh_ctx* c);
 
 }  // namespace lagh

@@ -534,6 +534,13 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     e = cudaMemcpy(A.lchol, lc.data(), lc.size() * sizeof(double), cudaMemcpyHostToDevice);
   if ((st = cuda_check(c, e, "preconditioner")) != LH_OK) return fail(st, c->err);
   if ((st = cuda_check(c, cg_prepare(c), "cg attributes")) != LH_OK) return fail(st, c->err);
+  // cluster-resident CG: small 2D problems with the band preconditioner (measured
+  // faster than the kernel chain up to N_V ~ 8k; slower from ~30k, where the
+  // solve needs more than the cluster's 16 SMs)
+  c->cg_cluster = 0;
+  if (phys->cg_cluster >= 0 && d == 2 && c->tpc.enabled && !c->tpc.exact &&
+      (phys->cg_cluster == 1 || g.nv <= 6000))
+    c->cg_cluster = cg_cluster_choose(c);
   Ctl ctl0;
   memset(&ctl0, 0, sizeof(ctl0));
   e = cudaMemcpy(A.rho0K, rho0K.data(), nelem * sizeof(double), cudaMemcpyHostToDevice);

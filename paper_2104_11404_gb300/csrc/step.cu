@@ -190,6 +190,10 @@ static lh_status build_graph(lh_ctx* c) {
     c->use_pdl = 0;
     e = capture_attempt(c, &where);
   }
+  if (e != cudaSuccess && c->cg_cluster > 0) {  // and with the CG as a kernel chain
+    c->cg_cluster = 0;
+    e = capture_attempt(c, &where);
+  }
   if (e == cudaSuccess) {
     c->graph_ready = 1;
   } else {

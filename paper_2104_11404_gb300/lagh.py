@@ -49,7 +49,8 @@ class lh_phys_desc(ctypes.Structure):
                 ("beta1", ctypes.c_double), ("beta2", ctypes.c_double),
                 ("gamma_dt", ctypes.c_double), ("q1", ctypes.c_double), ("q2", ctypes.c_double),
                 ("cg_rtol", ctypes.c_double), ("dt_min_frac", ctypes.c_double),
-                ("cg_precond", ctypes.c_int32), ("direct_launch", ctypes.c_int32)]
+                ("cg_precond", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
+                ("cg_cluster", ctypes.c_int32)]
 
 
 class lh_layout_info(ctypes.Structure):

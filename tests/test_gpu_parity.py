@@ -331,3 +331,30 @@ def test_integer_pipe_conversions_match_ieee_casts():
     d1 = torch.empty(1, dtype=torch.float64, device="cuda")
     lagh.lh_check_conversions(nan, f1, d1)
     assert np.isnan(host(f1)[0]) and np.isnan(host(d1)[0])
+
+
+@pytest.mark.parametrize("name,n", [("tg2d_64", (24, 20)), ("sedov2d_8", (8, 8)),
+                                    ("gresho2d_256", (10, 12))])
+def test_cluster_cg_matches_kernel_chain(name, n):
+    """The velocity solve of a small 2D problem as one cluster launch gives
+    the solution of the kernel chain (same algorithm, sums in another order),
+    with the same iteration counts, through single solves and a graph run."""
+    cfg = W.scaled(name, n=n)
+    o = oracle_for(cfg)
+    rng = np.random.default_rng(17)
+    b = rng.normal(size=o.nv)
+    xo, _, _, _ = o.mass_solve_v(b)
+    gc = gpu_for(cfg)                                          # cluster form (auto)
+    gk = gpu_for(cfg, phys_overrides={"cg_cluster": -1})
+    xc, itc, rrc = gc.mass_solve_v(dev(b))
+    xk, itk, rrk = gk.mass_solve_v(dev(b))
+    assert itc == itk and rrc <= 1e-14 and rrk <= 1e-14
+    assert rel_l2(xo, host(xc)) <= 1e-12 and rel_l2(host(xk), host(xc)) <= 1e-13
+    gc.init_state()
+    gk.init_state()
+    sc = gc.run_to(cfg["t_final"], max_steps=6)
+    sk = gk.run_to(cfg["t_final"], max_steps=6)
+    assert sc["steps"] == sk["steps"] and sc["cg_iters"] == sk["cg_iters"]
+    vc, ec, _, _, _ = gc.get_state()
+    vk, ek, _, _, _ = gk.get_state()
+    assert rel_l2(host(vk), host(vc)) <= 1e-10 and rel_l2(host(ek), host(ec)) <= 1e-10
