@@ -35,6 +35,7 @@ struct CgArgs {
   double M1[(kMaxOrder + 1) * (kMaxOrder + 1)];
   TensorPC tpc;
   const float* lfac;
+  const double* lfac64;
   const double* lchol;
   const double* rhs;
   double *x, *r, *z, *p, *Ap, *ApE;
@@ -121,12 +122,12 @@ __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
 // (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
 // last: the pass along the last direction (sums r.z; init also writes p = z).
 // Shared memory of one band-pass tile: 32 lines x (32 positions + halo) of
-// input and the band rows of the 32 positions.
-template <int K>
+// input and the band rows of the 32 positions, in the band's precision T.
+template <int K, typename T = float>
 struct PassTile {
   static constexpr int B = PB<K>::B, W = 2 * B + 1, TP = 32, ldt = TP + 2 * B + 1;
-  float tile[32 * ldt];
-  float wrows[TP * W];
+  T tile[32 * ldt];
+  T wrows[TP * W];
 };
 
 template <int DIM>
@@ -139,14 +140,14 @@ __device__ __forceinline__ int64_t pass_tiles(const Geom& g, int d) {
 // One tile of a band pass along direction d (all threads of the block): the
 // tile's outputs dst = band-inverse(src) and, per mode, r / x / p writes and
 // the partial sums b.b (mode 0) and r.z (last), added to l_bb / l_rz.
-template <int DIM, int K>
+template <int DIM, int K, typename T = float>
 __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int last, int init,
                                           const double* src_in, double* dst, int64_t bid,
-                                          PassTile<K>& sm, double& l_bb, double& l_rz) {
-  using PT = PassTile<K>;
+                                          PassTile<K, T>& sm, double& l_bb, double& l_rz) {
+  using PT = PassTile<K, T>;
   constexpr int B = PT::B, W = PT::W, TP = PT::TP, ldt = PT::ldt;
-  float* tile = sm.tile;
-  float* wrows = sm.wrows;
+  T* tile = sm.tile;
+  T* wrows = sm.wrows;
   const Geom& g = a.g;
   const int nd = g.nn[d];
   const int64_t nlines = g.nnodes / nd;
@@ -160,7 +161,6 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
   const int c = (int)(bid / lgroups);
   const int p0 = pb * TP;
   const int var = (c == d) ? 1 : 0;
-  const float* Wt = a.lfac + a.tpc.off[d][var];
   const int tid = threadIdx.x, nt = blockDim.x;
   // line l of the tile: its base node and whether it is a wall-normal line
   auto line_info = [&](int l, int64_t& base, bool& wall) -> bool {
@@ -175,7 +175,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     return true;
   };
   const double* src = mode == 0 ? a.rhs : src_in;
-  const float scl = (mode == 2) ? 1.0f : (float)a.tpc.scale;
+  const T scl = (mode == 2) ? T(1) : (T)a.tpc.scale;
   // stage the tile with its halo: positions [p0 - B, p0 + TP + B)
   const int span = TP + 2 * B;
   for (int idx = tid; idx < 32 * span; idx += nt) {
@@ -183,12 +183,12 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     const int l = d == 0 ? idx / span : idx % 32;
     const int q = d == 0 ? idx - l * span : idx / 32;
     const int pos = p0 - B + q;
-    float val = 0.0f;
+    T val = T(0);
     int64_t base;
     bool wall;
     if (pos >= var && pos < nd - var && line_info(l, base, wall) && !wall) {
       const double v = src[base + pos * stride];
-      val = (float)v * scl;
+      val = (T)v * scl;
     }
     tile[l * ldt + q] = val;
   }
@@ -197,7 +197,12 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     for (int idx = tid; idx < TP * W; idx += nt) {
       const int q = idx / W, m = idx - q * W;
       const int row = p0 + q - var;
-      wrows[idx] = (row >= 0 && row < nrow) ? Wt[(int64_t)row * W + m] : 0.0f;
+      T wv = T(0);
+      if (row >= 0 && row < nrow) {
+        if constexpr (sizeof(T) == 8) wv = a.lfac64[a.tpc.off64[d][var] + (int64_t)row * W + m];
+        else wv = a.lfac[a.tpc.off[d][var] + (int64_t)row * W + m];
+      }
+      wrows[idx] = wv;
     }
   }
   __syncthreads();
@@ -211,9 +216,9 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     const int64_t kk = base + pos * stride;
     double zv = 0.0;
     if (!wall && pos >= var && pos < nd - var) {
-      const float* wr = wrows + q * W;
-      const float* tr = tile + l * ldt + q;  // tile position of offset -B
-      float acc = 0.0f;
+      const T* wr = wrows + q * W;
+      const T* tr = tile + l * ldt + q;  // tile position of offset -B
+      T acc = T(0);
 #pragma unroll
       for (int m = 0; m < W; ++m) acc += wr[m] * tr[m];
       zv = (double)acc;
@@ -245,7 +250,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
 // on free components and x = 0, sums b.b), 1 = first pass inside the loop
 // (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
 // last: the pass along the last direction (sums r.z; init also writes p = z).
-template <int DIM, int K>
+template <int DIM, int K, typename T>
 __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, int d, int mode,
                                                               int last, int init,
                                                               const double* src_in,
@@ -256,9 +261,9 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
     a.cg->done = 0;
     a.cg->it = 0;
   }
-  __shared__ PassTile<K> sm;
+  __shared__ PassTile<K, T> sm;
   double l_bb = 0.0, l_rz = 0.0;
-  pass_tile<DIM, K>(a, d, mode, last, init, src_in, dst, (int64_t)blockIdx.x, sm, l_bb, l_rz);
+  pass_tile<DIM, K, T>(a, d, mode, last, init, src_in, dst, (int64_t)blockIdx.x, sm, l_bb, l_rz);
   double tot;
   if (mode == 0) {
     if (reduce_last(l_bb, a.part, &a.cg->ticket[kTicketPass0], &tot) && threadIdx.x == 0)
@@ -723,6 +728,7 @@ static CgArgs make_args(const lh_ctx* c, const double* rhs, double* out, const C
     for (int j = 0; j <= kMaxOrder; ++j) a.M1[i * (kMaxOrder + 1) + j] = c->basis.M1[i][j];
   a.tpc = c->tpc;
   a.lfac = c->a.lfac;
+  a.lfac64 = c->a.lfac64;
   a.lchol = c->a.lchol;
   a.rhs = rhs;
   a.x = out;
@@ -774,9 +780,14 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
     const int64_t blocks = (int64_t)DIM * ((nlines + 31) / 32) * ((nd + 31) / 32);
     const int mode = d == 0 ? (init ? 0 : 1) : 2;
     double* dst = bufs[(DIM - 1 - d) & 1];
-    cudaError_t e = launch_k(c->use_pdl != 0, cg_pass_kernel<DIM, K>, dim3((unsigned)blocks),
-                             dim3(kLineThreads), 0, s, a, d, mode, (int)(d == DIM - 1),
-                             init ? 1 : 0, src, dst);
+    cudaError_t e =
+        c->tpc.fp64
+            ? launch_k(c->use_pdl != 0, cg_pass_kernel<DIM, K, double>, dim3((unsigned)blocks),
+                       dim3(kLineThreads), 0, s, a, d, mode, (int)(d == DIM - 1), init ? 1 : 0,
+                       src, dst)
+            : launch_k(c->use_pdl != 0, cg_pass_kernel<DIM, K, float>, dim3((unsigned)blocks),
+                       dim3(kLineThreads), 0, s, a, d, mode, (int)(d == DIM - 1), init ? 1 : 0,
+                       src, dst);
     if (e != cudaSuccess) return e;
     src = dst;
   }

@@ -109,12 +109,14 @@ struct Barrier {
 // |i - j| <= B[d] and stored in FP32 as rows [i][j - i + B].
 struct TensorPC {
   int64_t off[3][2];   // offsets into Arrays::lfac (units of float)
+  int64_t off64[3][2]; // offsets into Arrays::lfac64 (units of double)
   int64_t coff[3][2];  // offsets into Arrays::lchol (units of double)
   int B[3];            // band half-width per direction
   int Bmax;
   double scale;        // 1 / (rho0 |J0|), the same for every element
   int enabled;
   int exact;           // 1: banded Cholesky line solves (lchol) instead of the bands
+  int fp64;            // 1: the bands in FP64 (lfac64), FP64 accumulation
 };
 
 // Work arrays of one context (all device pointers).
@@ -138,6 +140,7 @@ struct Arrays {
   double *tmpV;                 // N_V scratch
   double *aux;                  // 16 doubles of API scratch (estimates, flags, energy)
   float *lfac;                  // tensor preconditioner bands (FP32)
+  double *lfac64;               // the same bands in FP64
   double *lchol;                // exact preconditioner: scaled Cholesky rows (FP64)
   CgDev* cg;
   Barrier* bar;

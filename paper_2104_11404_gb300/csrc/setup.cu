@@ -319,6 +319,7 @@ static void free_all(lh_ctx* c) {
   if (c->a.cg) { cudaFree(c->a.cg); c->a.cg = nullptr; }
   if (c->a.lfac) { cudaFree(c->a.lfac); c->a.lfac = nullptr; }
   if (c->a.lchol) { cudaFree(c->a.lchol); c->a.lchol = nullptr; }
+  if (c->a.lfac64) { cudaFree(c->a.lfac64); c->a.lfac64 = nullptr; }
   if (c->side) { cudaStreamDestroy(c->side); c->side = nullptr; }
   if (c->ctl_host) { cudaFreeHost(c->ctl_host); c->ctl_host = nullptr; }
   if (c->graph_ready == 1) cudaGraphExecDestroy(c->step_graph);
@@ -471,7 +472,8 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   // entries within half-width B are kept (relative size of the dropped ones
   // below 1e-9 for B = 14, 22, 30 at k = 1, 2, 3) and applied in FP32.
   std::vector<float> lf;
-  std::vector<double> lc;  // exact variant: scaled banded Cholesky rows
+  std::vector<double> lf64;  // the bands in FP64
+  std::vector<double> lc;    // exact variant: scaled banded Cholesky rows
   memset(&c->tpc, 0, sizeof(c->tpc));
   {
     bool uniform = true;
@@ -487,6 +489,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
       for (int var = 0; var < 2; ++var) {
         const int N = nfull - 2 * var;
         c->tpc.off[dd][var] = (int64_t)lf.size();
+        c->tpc.off64[dd][var] = (int64_t)lf64.size();
         if (N <= 0) continue;
         std::vector<double> L;  // L[i][m] = L_{i,i-m}
         banded_cholesky_1d(c->basis, k, g.n[dd], var, L);
@@ -517,18 +520,26 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
           for (int i = (j - B > 0 ? j - B : 0); i <= j + B && i < N; ++i)
             band[(size_t)i * W + (j - i + B)] = col[i];
         }
-        for (double v : band) lf.push_back((float)v);
+        for (double v : band) {
+          lf.push_back((float)v);
+          lf64.push_back(v);
+        }
       }
     }
     c->tpc.Bmax = Bmax;
     c->tpc.scale = 1.0 / rho0K[0];
     c->tpc.enabled = (phys->cg_precond == LH_PRECOND_TENSOR ||
+                      phys->cg_precond == LH_PRECOND_TENSOR64 ||
                       phys->cg_precond == LH_PRECOND_EXACT) && uniform;
     c->tpc.exact = c->tpc.enabled && phys->cg_precond == LH_PRECOND_EXACT;
+    c->tpc.fp64 = c->tpc.enabled && phys->cg_precond == LH_PRECOND_TENSOR64;
   }
   e = dalloc(&A.lfac, lf.size() > 0 ? lf.size() : 1);
   if (e == cudaSuccess && !lf.empty())
     e = cudaMemcpy(A.lfac, lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dalloc(&A.lfac64, lf64.size() > 0 ? lf64.size() : 1);
+  if (e == cudaSuccess && !lf64.empty())
+    e = cudaMemcpy(A.lfac64, lf64.data(), lf64.size() * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = dalloc(&A.lchol, lc.size() > 0 ? lc.size() : 1);
   if (e == cudaSuccess && !lc.empty())
     e = cudaMemcpy(A.lchol, lc.data(), lc.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -538,7 +549,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   // faster than the kernel chain up to N_V ~ 8k; slower from ~30k, where the
   // solve needs more than the cluster's 16 SMs)
   c->cg_cluster = 0;
-  if (phys->cg_cluster >= 0 && d == 2 && c->tpc.enabled && !c->tpc.exact &&
+  if (phys->cg_cluster >= 0 && d == 2 && c->tpc.enabled && !c->tpc.exact && !c->tpc.fp64 &&
       (phys->cg_cluster == 1 || g.nv <= 6000))
     c->cg_cluster = cg_cluster_choose(c);
   Ctl ctl0;

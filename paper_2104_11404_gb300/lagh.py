@@ -16,7 +16,7 @@ LH_OK, LH_EINVAL, LH_ENOMEM, LH_ECUDA, LH_ETANGLED, LH_ENONFINITE, LH_EDTMIN, LH
     LH_ETIMEOUT, LH_EUNSUPPORTED, LH_ETOOLARGE = range(11)
 LH_FP64, LH_MIXED = 0, 1
 LH_SEDOV, LH_TAYLOR_GREEN, LH_GRESHO, LH_UNIFORM = 1, 2, 3, 4
-LH_PRECOND_JACOBI, LH_PRECOND_TENSOR, LH_PRECOND_EXACT = 0, 1, 2
+LH_PRECOND_JACOBI, LH_PRECOND_TENSOR, LH_PRECOND_EXACT, LH_PRECOND_TENSOR64 = 0, 1, 2, 3
 
 # every entry point declared in include/lagh.h
 API_NAMES = [

@@ -87,13 +87,16 @@ def test_cg_preconditioners_agree(dim, k, n):
     gt = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_TENSOR})
     gj = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_JACOBI})
     ge = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_EXACT})
+    g64 = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_TENSOR64})
     xt, it_t, rr_t = gt.mass_solve_v(dev(b))
     xj, it_j, rr_j = gj.mass_solve_v(dev(b))
     xe, it_e, rr_e = ge.mass_solve_v(dev(b))
-    for xg in (xt, xj, xe):
+    x6, it_6, rr_6 = g64.mass_solve_v(dev(b))
+    for xg in (xt, xj, xe, x6):
         assert rel_l2(xo, host(xg)) <= 1e-12
-    # banded inverse in FP32: a few iterations; the exact inverse: one
+    # banded inverse in FP32: a few iterations; in FP64: two; the exact inverse: one
     assert it_e == 1 and rr_e <= 1e-14
+    assert it_6 <= 2 and rr_6 <= 1e-14
     assert it_t <= 3 < it_j
 
 
