@@ -274,12 +274,13 @@ def run_native(args):
     achieved = fl / (m["force_ms"] * 1e-3) / 1e12
     fl64 = flops_per_element_force(cfg["dim"], cfg["order"], False) * nel
     achieved64 = fl64 / (f["force_ms"] * 1e-3) / 1e12
-    # kernels launched per attempt: per stage force, gather, cg reset, dim init
-    # passes, (cg iterations x (3 + dim + 1)), update, energy (+ FP64 reference
-    # pressure term on the mixed path); then control and commit
+    # kernels launched per attempt: per stage force, node gather, dim initial
+    # preconditioner passes, v/x update and energy update, and per CG iteration
+    # the element apply, node gather, update and dim passes; then control and
+    # commit
     d = cfg["dim"]
     attempts = m["steps"] + m["rejects"]
-    launches = attempts * (2 * (1 + 1 + 1 + d + 1 + 1 + 1) + 2) + m["cg"] * (3 + d + 1)
+    launches = attempts * (2 * (4 + d) + 2) + m["cg"] * (3 + d)
     line = {
         "metric": "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error",
         "value": value,

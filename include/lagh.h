@@ -311,11 +311,13 @@ LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* d
  * library, not a step of the paper; the FP32 paths convert on the integer
  * pipes because the FP64 pipe of this GPU is narrow): f_out[i] = in[i] rounded
  * to FP32 (nearest, ties to even; results below the normal FP32 range flush
- * to zero) and d_out[i] = f_out[i] widened back to FP64 exactly.  Device
- * pointers, n entries, on stream (cudaStream_t as void*).  Errors: LH_EINVAL,
- * LH_ECUDA. */
+ * to zero), d_out[i] = f_out[i] widened back to FP64 exactly, and (if
+ * split_out != NULL) split_out[i] = hi + lo of the two-float split of in[i]
+ * used by the FP32 energy accumulations (|in - split_out| <= 2^-48 |in| in
+ * the normal range).  Device pointers, n entries, on stream (cudaStream_t as
+ * void*).  Errors: LH_EINVAL, LH_ECUDA. */
 LH_API lh_status lh_check_conversions(const double* in, int64_t n, float* f_out, double* d_out,
-                                      void* stream);
+                                      double* split_out, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Batched form: n independent instances of the time step, each on its own

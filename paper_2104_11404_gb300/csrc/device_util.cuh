@@ -150,6 +150,33 @@ __device__ __forceinline__ float d2f_rn(double d) {
   return __uint_as_float(s | ((unsigned)fe << 23) | r);
 }
 
+// Error-free transformations in FP32 (two-float "double-float" sums): with
+// the rounding-exact intrinsics the compiler neither fuses nor reorders them.
+// two_sum_f: s + e == a + b exactly (s = fl(a + b)).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// w = hi + lo to about 2^-48 relative: hi is w with its 29 lowest fraction
+// bits cleared (exactly a float), lo the cleared part rounded to a float.
+// Integer operations only; |w| below 2^-75 or outside the FP32 range keeps
+// lo = 0 (then hi carries the FP32 rounding of w, or 0 / inf).
+__device__ __forceinline__ void split_df(double w, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+  hi = d2f_rn(__longlong_as_double((long long)(b & ~0x1fffffffull)));
+  const int ex = (int)((b >> 52) & 0x7ffu);
+  const unsigned low = (unsigned)(b & 0x1fffffffull);
+  const int fe = ex - 948;  // FP32 biased exponent of 2^(ex - 1075)
+  if (low == 0u || fe <= 0 || fe >= 0xff || ex == 0x7ff || hi == 0.0f) {
+    lo = 0.0f;
+    return;
+  }
+  const float l = __fmul_rn(__uint2float_rn(low), __uint_as_float((unsigned)fe << 23));
+  lo = (b >> 63) ? -l : l;
+}
+
 template <typename T>
 __device__ __forceinline__ T from_double(double d);
 template <>

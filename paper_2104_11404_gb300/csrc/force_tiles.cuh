@@ -483,11 +483,17 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     if (active) {
       if (A.FK != nullptr)
         for (int w = tq; w < DIM * ND1 * ND2; w += NQD) A.FK[el * (DIM * ND1 * ND2) + w] = fk[w];
-      // F.1 = row sums in FP64
+      // F.1 = row sums: error-free FP32 sums (the rounding errors collected
+      // apart), widened to FP64 (the FP32 entries summed to ~2^-48)
       for (int w = tq; w < DIM * ND1; w += NQD) {
-        double s = f2d_exact(fk[w * ND2]);
-        for (int j = 1; j < ND2; ++j) s += f2d_exact(fk[w * ND2 + j]);
-        A.F1E[slot * DIM * ND1 + w] = s;
+        float S = fk[w * ND2], C = 0.0f;
+        for (int j = 1; j < ND2; ++j) {
+          float s2, e2;
+          two_sum_f(S, fk[w * ND2 + j], s2, e2);
+          S = s2;
+          C = __fadd_rn(C, e2);
+        }
+        A.F1E[slot * DIM * ND1 + w] = f2d_exact(S) + f2d_exact(C);
       }
       // F^T w in FP64
       if (with_w)
@@ -608,7 +614,8 @@ struct EL {
   static constexpr int S_L2 = DIM == 2 ? K * NQ : K * NQ * NQ + K * K * NQ;
   static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
   static constexpr size_t B_ELEM = al(NFI * ND1 * 8) + al(S_INTERP * 8) + al(NQD * 8) +
-                                   al(S_L2 * 8) + al(ND2 * 8) + al(8);
+                                   al(S_L2 * 8) + al(ND2 * 8) + al(8) +
+                                   (MIXED ? al(2 * DIM * ND1 * 4) : 0);
   static constexpr size_t B_TAB = 3 * al(NQ * P * 8) + al(NQ * K * 8) + al(81 * 8);
   static constexpr size_t BYTES = B_TAB + EPB * B_ELEM;
 };
@@ -800,7 +807,9 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   double* gq = reinterpret_cast<double*>(ep); ep += F::al(NQD * 8);
   double* l2s = reinterpret_cast<double*>(ep); ep += F::al(F::S_L2 * 8);
   double* ftv = reinterpret_cast<double*>(ep); ep += F::al(ND2 * 8);
-  double* crs = reinterpret_cast<double*>(ep);  // coef / (rho0 |J0|) of the element
+  double* crs = reinterpret_cast<double*>(ep); ep += F::al(8);  // coef / (rho0 |J0|)
+  float* whs = reinterpret_cast<float*>(ep);  // mixed: w split into two floats
+  float* wls = whs + DIM * ND1;
 
   const int64_t el = el0 + le;
   const bool active = le < F::EPB && el < g.nelem;
@@ -817,25 +826,44 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   team_sync<NQD>();
 
   if constexpr (MIXED) {
-    // F^T w from the stored FP32 element matrix, FP64 accumulation.  The
-    // team's NQD = 2^DIM ND2 threads split the DIM ND1 terms of each of the
-    // ND2 sums into 2^DIM chunks (short dependent chains); the chunk sums
-    // are then added in chunk order.
+    // F^T w from the stored FP32 element matrix, to ~2^-48: w is split into
+    // two floats, each product f w_hi is formed exactly (TwoProduct), the
+    // terms are added with error-free sums and the errors collected apart,
+    // all on the FP32 pipe.  The team's NQD = 2^DIM ND2 threads split the
+    // DIM ND1 terms of each of the ND2 sums into 2^DIM chunks; the chunk sums
+    // are then added in chunk order and widened to FP64.
     constexpr int NPART = NQD / ND2, NCI = DIM * ND1, CH = (NCI + NPART - 1) / NPART;
-    double* part = gq;  // NQD doubles per element, free here
+    float2* part = reinterpret_cast<float2*>(gq);  // NQD pairs per element, free here
+    if (active)
+      for (int w = tq; w < NCI; w += NQD) split_df(ws[w], whs[w], wls[w]);
+    team_sync<NQD>();
     if (active) {
       const int j = tq % ND2, pc = tq / ND2;
       const float* fk = A.FK + el * (DIM * ND1 * ND2);
       const int c0 = pc * CH, c1 = (c0 + CH < NCI) ? c0 + CH : NCI;
-      double s = 0.0;
-      for (int ci = c0; ci < c1; ++ci) s = fma(f2d_exact(fk[ci * ND2 + j]), ws[ci], s);
-      part[tq] = s;
+      float S = 0.0f, C = 0.0f;
+      for (int ci = c0; ci < c1; ++ci) {
+        const float f = fk[ci * ND2 + j];
+        const float p = __fmul_rn(f, whs[ci]);
+        const float pe = __fmaf_rn(f, whs[ci], -p);  // f w_hi - p, exact
+        float s2, e2;
+        two_sum_f(S, p, s2, e2);
+        S = s2;
+        C = __fadd_rn(C, __fadd_rn(e2, __fmaf_rn(f, wls[ci], pe)));
+      }
+      part[tq] = make_float2(S, C);
     }
     team_sync<NQD>();
     if (active && tq < ND2) {
-      double s = part[tq];
-      for (int pc = 1; pc < NPART; ++pc) s += part[pc * ND2 + tq];
-      ftv[tq] = s;
+      float S = part[tq].x, C = part[tq].y;
+      for (int pc = 1; pc < NPART; ++pc) {
+        const float2 q = part[pc * ND2 + tq];
+        float s2, e2;
+        two_sum_f(S, q.x, s2, e2);
+        S = s2;
+        C = __fadd_rn(C, __fadd_rn(e2, q.y));
+      }
+      ftv[tq] = f2d_exact(S) + f2d_exact(C);
     }
     if (pref != 0.0) {
       // -p_ref alpha_q tr(adj(J) grad w) at the points, J from the FP64 positions

@@ -138,22 +138,28 @@ cudaError_t launch_total_energy(const lh_ctx* c, const double* v, const double* 
 // ------------------------------------------------ conversion self-check ----
 
 namespace lagh {
-__global__ void convert_check_kernel(const double* in, int64_t n, float* f_out, double* d_out) {
+__global__ void convert_check_kernel(const double* in, int64_t n, float* f_out, double* d_out,
+                                     double* split_out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const float f = d2f_rn(in[i]);
     f_out[i] = f;
     d_out[i] = f2d_exact(f);
+    if (split_out) {
+      float hi, lo;
+      split_df(in[i], hi, lo);
+      split_out[i] = f2d_exact(hi) + f2d_exact(lo);
+    }
   }
 }
 }  // namespace lagh
 
 extern "C" lh_status lh_check_conversions(const double* in, int64_t n, float* f_out,
-                                          double* d_out, void* stream) {
+                                          double* d_out, double* split_out, void* stream) {
   if (n < 0 || (n > 0 && (!in || !f_out || !d_out))) return LH_EINVAL;
   if (n == 0) return LH_OK;
   const int64_t blocks = (n + 255) / 256;
   lagh::convert_check_kernel<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0,
-                               (cudaStream_t)stream>>>(in, n, f_out, d_out);
+                               (cudaStream_t)stream>>>(in, n, f_out, d_out, split_out);
   return cudaGetLastError() == cudaSuccess ? LH_OK : LH_ECUDA;
 }

@@ -145,7 +145,7 @@ def load():
     L.lh_batch_force_sampled.argtypes = [_vp, _vp, _vp, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
     L.lh_batch_autotune.argtypes = [_vp, ctypes.c_int32, P(lh_batch_tuning)]
     L.lh_batch_tuning_get.argtypes = [_vp, P(lh_batch_tuning)]
-    L.lh_check_conversions.argtypes = [_dp, ctypes.c_int64, _vp, _dp, _vp]
+    L.lh_check_conversions.argtypes = [_dp, ctypes.c_int64, _vp, _dp, _dp, _vp]
     for name in API_NAMES:
         if name not in ("lh_default_phys", "lh_status_string", "lh_last_error",
                         "lh_batch_last_error"):
@@ -397,7 +397,8 @@ def lh_batch_tuning_get(b):
     return t
 
 
-def lh_check_conversions(inp, f_out, d_out, stream=None):
-    st = load().lh_check_conversions(_ptr(inp), int(inp.numel()), _ptr(f_out), _ptr(d_out), stream)
+def lh_check_conversions(inp, f_out, d_out, split_out=None, stream=None):
+    st = load().lh_check_conversions(_ptr(inp), int(inp.numel()), _ptr(f_out), _ptr(d_out),
+                                     _ptr(split_out), stream)
     if st != LH_OK:
         raise LaghError(st, "lh_check_conversions failed")

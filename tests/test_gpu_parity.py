@@ -317,9 +317,10 @@ def test_integer_pipe_conversions_match_ieee_casts():
     a = np.array(vals, dtype=np.float64)
     f = torch.empty(len(a), dtype=torch.float32, device="cuda")
     d = torch.empty(len(a), dtype=torch.float64, device="cuda")
-    lagh.lh_check_conversions(dev(a), f, d)
+    sp = torch.empty(len(a), dtype=torch.float64, device="cuda")
+    lagh.lh_check_conversions(dev(a), f, d, sp)
     torch.cuda.synchronize()
-    fh, dh = host(f), host(d)
+    fh, dh, sph = host(f), host(d), host(sp)
     with np.errstate(over="ignore"):
         ref = a.astype(np.float32)
     normal = (np.abs(ref) >= np.finfo(np.float32).tiny) | ~np.isfinite(ref)
@@ -329,6 +330,9 @@ def test_integer_pipe_conversions_match_ieee_casts():
     assert np.array_equal(np.signbit(fh[~normal]), np.signbit(a[~normal]))
     # widening is exact
     assert np.array_equal(dh.view(np.uint64), fh.astype(np.float64).view(np.uint64))
+    # the two-float split holds 48 bits where the value is in the FP32 range
+    mid = np.isfinite(a) & (np.abs(a) > 1e-22) & (np.abs(a) < 1e38)
+    assert np.all(np.abs(sph[mid] - a[mid]) <= 2.0 ** -47 * np.abs(a[mid]))
     nan = torch.tensor([np.nan], dtype=torch.float64, device="cuda")
     f1 = torch.empty(1, dtype=torch.float32, device="cuda")
     d1 = torch.empty(1, dtype=torch.float64, device="cuda")
