@@ -526,16 +526,21 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
   if (tuning && tuning->threads > 0) {
     t = *tuning;
     b->tuned = 1;
-  } else {
-    t.threads = 1024;
-    t.ctas_per_sm = 0;
-    t.smem_lines = 2;
   }
-  lh_status st = apply_tuning(b, t);
-  // the largest instance's node lines do not fit: fewer in shared memory
-  while (st != LH_OK && !(tuning && tuning->threads > 0) && t.smem_lines > 0) {
-    --t.smem_lines;
+  lh_status st;
+  if (b->tuned) {
     st = apply_tuning(b, t);
+  } else {
+    // default shape: the widest CTA built for this dimension whose shared
+    // memory holds the largest instance's node lines (fewer staged if not)
+    st = LH_EUNSUPPORTED;
+    for (int ti = 2; ti >= 0 && st != LH_OK; --ti)
+      for (int sl = 2; sl >= 0 && st != LH_OK; --sl) {
+        t.threads = kThreadChoices[ti];
+        t.ctas_per_sm = 0;
+        t.smem_lines = sl;
+        st = apply_tuning(b, t);
+      }
   }
   if (st != LH_OK) return fail(st, b->err);
   *out = b;

@@ -260,3 +260,32 @@ def test_batch_bench_workload_instances_match_single_contexts():
         o.run(0.8, v, e, x, max_steps=steps)
         assert rel_l2(v, host(gv)) <= 1e-4 and rel_l2(e, host(ge)) <= 1e-4
     assert len(seen) == len(W.BATCH_SIZES)
+
+
+@pytest.mark.parametrize("dim,k,sizes", [(2, 1, [(6, 5), (4, 7)]), (2, 3, [(3, 4), (5, 3)]),
+                                          (3, 1, [(3, 3, 2), (2, 4, 3)]),
+                                          (3, 2, [(2, 3, 2), (3, 2, 2)])])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
+def test_batch_other_orders_and_3d_per_step(dim, k, sizes, precision, tol):
+    """Other orders and 3D instances (3D node lines are solved in device
+    memory, the mass apply in element tiles) against the oracle, two steps."""
+    cfgs = []
+    for i, n in enumerate(sizes):
+        cfgs.append(dict(dim=dim, n=tuple(n) + (1,) * (3 - len(n)), order=k, problem=W.SEDOV,
+                         gamma=1.4 + 0.1 * i, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), visc=1,
+                         blast_energy=0.25 + 0.2 * i, t_final=0.8))
+    os_, vs, es, xs = _random_batch_state(cfgs, seed=300 + 10 * dim + k)
+    b = _batch(cfgs, precision)
+    b.set_state(dev(_pack(vs)), dev(_pack(es)), dev(_pack(xs)))
+    for rep in range(2):
+        dts = np.array([8e-4 * (1 + 0.3 * i + 0.1 * rep) for i in range(len(cfgs))])
+        b.step_fixed(dts)
+        for i, o in enumerate(os_):
+            _, _, s = o.step(float(dts[i]), vs[i], es[i], xs[i])
+            assert s == 0
+        vg, eg, xg = b.get_state()
+        for i in range(len(cfgs)):
+            gv, ge, gx = (host(t) for t in b.instance(i, vg, eg, xg))
+            assert max_rel(vs[i], gv) <= tol and max_rel(es[i], ge) <= tol, (i, rep)
+    q = b.query()
+    assert np.all(q["status"] == 0)
