@@ -62,14 +62,20 @@ __device__ __forceinline__ void adj_of(const T (&J)[DIM][DIM], T (&A)[DIM][DIM])
 
 // Cyclic Jacobi rotations on a symmetric 3x3 matrix S (in place); the columns
 // of V collect the rotations.  Pairs (0,1), (0,2), (1,2) in that order, at
-// most 12 sweeps, stopping once the off-diagonal part is exactly zero.
+// most 12 sweeps.  The sweeps stop once the off-diagonal part is at the
+// rounding level of the diagonal (sum of squares below (8 eps)^2 times the
+// diagonal's): there the rotations only move rounding errors (an exactly
+// zero off-diagonal is never reached in floating point, the iteration would
+// run to its cap).
 template <typename T>
 __device__ __forceinline__ void jacobi_sym3(T (&S)[3][3], T (&V)[3][3]) {
+  constexpr T eps8 = sizeof(T) == 8 ? T(8.0 * 2.220446049250313e-16) : T(8.0 * 1.1920929e-07);
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? T(1) : T(0);
   for (int sweep = 0; sweep < 12; ++sweep) {
-    T off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
-    if (off == T(0)) break;
+    const T off = S[0][1] * S[0][1] + S[0][2] * S[0][2] + S[1][2] * S[1][2];
+    const T dia = S[0][0] * S[0][0] + S[1][1] * S[1][1] + S[2][2] * S[2][2];
+    if (off <= eps8 * eps8 * dia) break;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const int p = r == 2 ? 1 : 0;
