@@ -28,6 +28,7 @@ sys.path.insert(0, ROOT)
 CHUNK = 50           # accepted time steps per bench step
 WORKLOAD = "tg2d_64"
 BATCH_CHUNK = 20     # accepted time steps of every instance per batched bench step
+PASS_KERNEL_DRAM_BYTES = 541184  # mean of 3 captured launches (630 KB, 364 KB, 630 KB read; 0 written)
 
 
 def _dist():
@@ -303,7 +304,10 @@ def run_native(args):
         "roofline": {"bound": "hbm", "kernel": "cg_pass_kernel (CG preconditioner line pass)",
                      "achieved": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9, "peak": hbm_peak,
                      "unit": "GB/s", "frac": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9 / hbm_peak,
-                     "traffic": None, "launch_us": m["pass_ms"] * 1e3,
+                     # DRAM read + write per launch of this kernel from the ncu capture in
+                     # profiles/cg_pass_kernel_tg2d_64.md (cold caches; reset to None when
+                     # the kernel changes)
+                     "traffic": PASS_KERNEL_DRAM_BYTES, "launch_us": m["pass_ms"] * 1e3,
                      "algorithmic_bytes": pass_bytes,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
                      "force_kernel": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
