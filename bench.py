@@ -304,9 +304,8 @@ def run_native(args):
         "roofline": {"bound": "hbm", "kernel": "cg_pass_kernel (CG preconditioner line pass)",
                      "achieved": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9, "peak": hbm_peak,
                      "unit": "GB/s", "frac": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9 / hbm_peak,
-                     # DRAM read + write per launch of this kernel from the ncu capture in
-                     # profiles/cg_pass_kernel_tg2d_64.md (cold caches; reset to None when
-                     # the kernel changes)
+                     # DRAM read + write per launch of this kernel from an ncu capture on
+                     # this workload (cold caches; reset to None when the kernel changes)
                      "traffic": PASS_KERNEL_DRAM_BYTES, "launch_us": m["pass_ms"] * 1e3,
                      "algorithmic_bytes": pass_bytes,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
