@@ -176,7 +176,9 @@ typedef struct lh_batch_stats {
 /* Launch shape of the batched kernels.  threads: 256, 512 or 1024 (2D only)
  * threads per CTA; with one thread per quadrature point, the force and energy
  * tiles hold threads / nq^dim elements and the mass tiles threads /
- * (dim (k+1)^dim).  ctas_per_sm: 0 = as many as fit.  smem_lines: where the
+ * (dim (k+1)^dim); qpt: quadrature points per thread in the force tiles (1,
+ * or 2 for 2D: a team of nq^dim / 2 threads per element, twice the elements per
+ * tile; 0 = 1).  ctas_per_sm: 0 = as many as fit.  smem_lines: where the
  * node-line solves of the velocity CG run: 2 = every component staged in
  * shared memory and solved together (needs 8 x dim x nodes of the largest
  * instance), 1 = one component at a time (8 x nodes), 0 = in place in device
@@ -185,6 +187,7 @@ typedef struct lh_batch_tuning {
   int32_t threads;
   int32_t ctas_per_sm;
   int32_t smem_lines;
+  int32_t qpt;
 } lh_batch_tuning;
 
 typedef struct lh_ctx lh_ctx;
@@ -403,7 +406,8 @@ LH_API lh_status lh_batch_force_sampled(lh_batch* b, const int64_t* list_off,
                                         double* FTv_local, double* dt_est);
 /* Autotuner (not a step of the paper): times the stage kernel on the current
  * states for every launch shape that fits the device (threads per CTA, CTAs
- * per SM, node-line staging), reps launches each, keeps the fastest and
+ * per SM, node-line staging, quadrature points per thread), reps launches
+ * each, keeps the fastest and
  * returns it in *chosen (may be NULL).  The states and control blocks are
  * left as they were. */
 LH_API lh_status lh_batch_autotune(lh_batch* b, int32_t reps, lh_batch_tuning* chosen);

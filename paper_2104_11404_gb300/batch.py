@@ -29,6 +29,7 @@ class Batch:
             tun.threads = int(tuning.get("threads", 0))
             tun.ctas_per_sm = int(tuning.get("ctas_per_sm", 0))
             tun.smem_lines = int(tuning.get("smem_lines", 1))
+            tun.qpt = int(tuning.get("qpt", 1))
         self.b = L.lh_batch_create(meshes, disc, physs, self.precision, self.stream.cuda_stream,
                                    tun)
         off_v, off_e, info = L.lh_batch_layout(self.b, self.n)
@@ -113,8 +114,10 @@ class Batch:
 
     def autotune(self, reps=2):
         t = lagh.lh_batch_autotune(self.b, reps)
-        return dict(threads=t.threads, ctas_per_sm=t.ctas_per_sm, smem_lines=t.smem_lines)
+        return dict(threads=t.threads, ctas_per_sm=t.ctas_per_sm, smem_lines=t.smem_lines,
+                    qpt=t.qpt)
 
     def tuning(self):
         t = lagh.lh_batch_tuning_get(self.b)
-        return dict(threads=t.threads, ctas_per_sm=t.ctas_per_sm, smem_lines=t.smem_lines)
+        return dict(threads=t.threads, ctas_per_sm=t.ctas_per_sm, smem_lines=t.smem_lines,
+                    qpt=t.qpt)

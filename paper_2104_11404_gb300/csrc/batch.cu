@@ -17,8 +17,10 @@ namespace lagh {
 // Launch shapes built per (dim, order, precision): threads per CTA.
 static const int kThreadChoices[3] = {256, 512, 1024};
 
-static bool get_ops(int dim, int k, bool mixed, int ntt, BOps* out) {
-  return dim == 2 ? get_batch_ops_2d(k, mixed, ntt, out) : get_batch_ops_3d(k, mixed, ntt, out);
+static bool get_ops(int dim, int k, bool mixed, int ntt, int qpt, BOps* out) {
+  if (dim == 3) return get_batch_ops_3d(k, mixed, ntt, qpt, out);
+  return qpt == 2 ? get_batch_ops_2d_q2(k, mixed, ntt, qpt, out)
+                  : get_batch_ops_2d_q1(k, mixed, ntt, qpt, out);
 }
 
 }  // namespace lagh
@@ -131,7 +133,7 @@ static cudaError_t set_smem(const void* fn, size_t bytes) {
 // shape does not fit the device.
 static lh_status apply_tuning(lh_batch* b, const lh_batch_tuning& t) {
   BOps o;
-  if (!get_ops(b->dim, b->k, b->precision == LH_MIXED, t.threads, &o))
+  if (!get_ops(b->dim, b->k, b->precision == LH_MIXED, t.threads, t.qpt > 0 ? t.qpt : 1, &o))
     return bset_error(b, LH_EUNSUPPORTED, "launch shape not built for this dimension and order");
   const size_t bytes = o.stage_bytes(b->max_nnodes, t.smem_lines);
   if (bytes > b->smem_optin)
@@ -148,6 +150,7 @@ static lh_status apply_tuning(lh_batch* b, const lh_batch_tuning& t) {
   if (occ < 1) return bset_error(b, LH_EUNSUPPORTED, "launch shape does not fit an SM");
   lh_batch_tuning tt = t;
   if (tt.ctas_per_sm <= 0 || tt.ctas_per_sm > occ) tt.ctas_per_sm = occ;
+  tt.qpt = o.qpt;
   b->ops = o;
   b->stage_smem = bytes;
   b->tune = tt;
@@ -539,6 +542,7 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
         t.threads = kThreadChoices[ti];
         t.ctas_per_sm = 0;
         t.smem_lines = sl;
+        t.qpt = 1;
         st = apply_tuning(b, t);
       }
   }
@@ -779,6 +783,7 @@ extern "C" lh_status lh_batch_autotune(lh_batch* b, int32_t reps, lh_batch_tunin
   if ((st = begin_run(b, 1e300, INT64_MAX / 2, 0, nullptr)) != LH_OK) return st;
   float best = 1e30f;
   lh_batch_tuning best_t = keep;
+  for (int qpt = 1; qpt <= 2; ++qpt)
   for (int ti = 0; ti < 3; ++ti)
     for (int sl = 2; sl >= 0; --sl)
       for (int cps = 1; cps <= 4; ++cps) {
@@ -787,6 +792,7 @@ extern "C" lh_status lh_batch_autotune(lh_batch* b, int32_t reps, lh_batch_tunin
         t.threads = kThreadChoices[ti];
         t.smem_lines = sl;
         t.ctas_per_sm = cps;
+        t.qpt = qpt;
         if (apply_tuning(b, t) != LH_OK) continue;
         if (b->tune.ctas_per_sm != cps) continue;  // more than fit
         if ((int64_t)b->num_sms * cps > b->slots) continue;

@@ -155,10 +155,11 @@ __device__ void tensor_solve(const Geom& g, const double* __restrict__ fac,
 }
 
 // Shared-memory plan of the stage kernel (bytes of each phase; the phases
-// reuse one dynamic buffer).
-template <int DIM, int K, bool MIXED, int NTT>
+// reuse one dynamic buffer).  QPT: quadrature points per thread of the force
+// tiles.
+template <int DIM, int K, bool MIXED, int NTT, int QPT = 1>
 struct BL {
-  using F = FL<DIM, K, MIXED, NTT>;
+  using F = FL<DIM, K, MIXED, NTT, QPT>;
   using E = EL<DIM, K, MIXED, NTT>;
   static constexpr int P = K + 1, ND1 = ipow(P, DIM), ND2 = ipow(K, DIM), NQD = ipow(2 * K, DIM);
   static constexpr int CGT = (NTT / (DIM * ND1)) > 0 ? NTT / (DIM * ND1) : 1;  // elements per mass tile
@@ -333,10 +334,10 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
 
 // One RK2-average stage of every unfinished instance (stage 0: S^n ->
 // S^{n+1/2}; stage 1: S^{n+1/2} -> candidate S^{n+1}, control, commit).
-template <int DIM, int K, bool MIXED, int NTT>
+template <int DIM, int K, bool MIXED, int NTT, int QPT>
 __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, const Basis1D bas,
                                                           int stage) {
-  using F = FL<DIM, K, MIXED, NTT>;
+  using F = FL<DIM, K, MIXED, NTT, QPT>;
   using E = EL<DIM, K, MIXED, NTT>;
   constexpr int ND1 = F::ND1;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -378,10 +379,10 @@ __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, con
     fa.tau_bits = &s_tau;
     fa.status = &s_status;
     fa.mode = kForceFull;
-    force_tables<DIM, K, MIXED, NTT>(bas, smem);
+    force_tables<DIM, K, MIXED, NTT, QPT>(bas, smem);
     __syncthreads();
     for (int64_t el0 = 0; el0 < g.nelem; el0 += F::EPB)
-      force_tile<DIM, K, MIXED, NTT>(g, sI.ph, bas, fa, rho0K, smem, el0);
+      force_tile<DIM, K, MIXED, NTT, QPT>(g, sI.ph, bas, fa, rho0K, smem, el0);
     __syncthreads();
     if (tid == 0) {
       ctl->tau_bits[stage] = s_tau;
@@ -601,9 +602,10 @@ __global__ void __launch_bounds__(NTT) batch_energy_kernel(const BatchArgs a, co
   }
 }
 
-// Kernels of one launch shape (threads per CTA) and their shared memory.
+// Kernels of one launch shape (threads per CTA, points per thread) and their
+// shared memory.
 struct BOps {
-  int ntt;
+  int ntt, qpt;
   size_t (*stage_bytes)(int64_t nnodes_max, int smem_lines);
   size_t energy_bytes;
   const void* stage;
@@ -612,15 +614,16 @@ struct BOps {
   const void* energy;
 };
 
-template <int DIM, int K, bool MIXED, int NTT>
+template <int DIM, int K, bool MIXED, int NTT, int QPT = 1>
 static BOps make_batch_ops() {
-  using L = BL<DIM, K, MIXED, NTT>;
+  using L = BL<DIM, K, MIXED, NTT, QPT>;
   BOps o;
   o.ntt = NTT;
+  o.qpt = QPT;
   o.stage_bytes = &L::bytes;
   constexpr int P = K + 1, ND1 = ipow(P, DIM);
   o.energy_bytes = (size_t)(4 * L::CGT * DIM * ND1 + P * P) * sizeof(double);
-  o.stage = (const void*)batch_stage_kernel<DIM, K, MIXED, NTT>;
+  o.stage = (const void*)batch_stage_kernel<DIM, K, MIXED, NTT, QPT>;
   o.estimate = (const void*)batch_estimate_kernel<DIM, K, MIXED, NTT>;
   o.sampled = (const void*)batch_sampled_kernel<DIM, K, MIXED, NTT>;
   o.energy = (const void*)batch_energy_kernel<DIM, K, NTT>;
@@ -629,7 +632,8 @@ static BOps make_batch_ops() {
 
 // Instantiated in batch_2d.cu / batch_3d.cu (one translation unit per
 // dimension, so they compile in parallel).  False if the shape is not built.
-bool get_batch_ops_2d(int k, bool mixed, int ntt, BOps* out);
-bool get_batch_ops_3d(int k, bool mixed, int ntt, BOps* out);
+bool get_batch_ops_2d_q1(int k, bool mixed, int ntt, int qpt, BOps* out);
+bool get_batch_ops_2d_q2(int k, bool mixed, int ntt, int qpt, BOps* out);
+bool get_batch_ops_3d(int k, bool mixed, int ntt, int qpt, BOps* out);
 
 }  // namespace lagh

@@ -10,13 +10,16 @@
 namespace lagh {
 
 
-template <int DIM, int K, bool MIXED, int NTT = 256>
+// Layout of a force tile: NTT threads, QPT quadrature points per thread (a
+// team of NQD / QPT threads per element), EPB elements.
+template <int DIM, int K, bool MIXED, int NTT = 256, int QPT = 1>
 struct FL {
   using T = typename std::conditional<MIXED, float, double>::type;
   static constexpr int P = K + 1, NQ = 2 * K;
   static constexpr int ND1 = ipow(P, DIM), ND2 = ipow(K, DIM), NQD = ipow(NQ, DIM);
-  static constexpr int EPB = (NTT / NQD) > 0 ? NTT / NQD : 1;
-  static constexpr int NT = EPB * NQD;
+  static constexpr int TEAM = NQD / QPT;
+  static constexpr int EPB = (NTT / TEAM) > 0 ? NTT / TEAM : 1;
+  static constexpr int NT = EPB * TEAM;
   static constexpr int PK = P * K;
   // interpolated nodal fields: x, v and (FP64 path) the test vector
   static constexpr int NF = MIXED ? 2 * DIM : 3 * DIM;
@@ -95,9 +98,9 @@ __device__ __forceinline__ void tile_min_to(unsigned long long v, unsigned long 
 
 // Basis tables of the force tiles, written once into the front of the shared
 // buffer (the caller synchronises the block before the first tile).
-template <int DIM, int K, bool MIXED, int NTT>
+template <int DIM, int K, bool MIXED, int NTT, int QPT = 1>
 __device__ __forceinline__ void force_tables(const Basis1D& bas, unsigned char* smem) {
-  using F = FL<DIM, K, MIXED, NTT>;
+  using F = FL<DIM, K, MIXED, NTT, QPT>;
   using T = typename F::T;
   constexpr int P = F::P, NQ = F::NQ;
   unsigned char* sp = smem;
@@ -127,13 +130,14 @@ __device__ __forceinline__ void force_tables(const Basis1D& bas, unsigned char* 
 // One tile of EPB element slots [slot0, slot0 + EPB) of the force evaluation,
 // by all NTT threads of the block (the grid kernel below uses one tile per
 // block; the batched stage kernel loops over the tiles of an instance).
-template <int DIM, int K, bool MIXED, int NTT>
+template <int DIM, int K, bool MIXED, int NTT, int QPT = 1>
 __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const Basis1D& bas,
                                            const ForceArgs& A, const double* rho0Kp,
                                            unsigned char* smem, int64_t slot0) {
-  using F = FL<DIM, K, MIXED, NTT>;
+  using F = FL<DIM, K, MIXED, NTT, QPT>;
   using T = typename F::T;
   constexpr int P = F::P, NQ = F::NQ, ND1 = F::ND1, ND2 = F::ND2, NQD = F::NQD;
+  constexpr int TEAM = F::TEAM;
   constexpr int NF = F::NF;
   struct Prm { const Phys& ph; const Basis1D& b; const double* rho0K; } prm{ph, bas, rho0Kp};
   unsigned char* sp = smem;
@@ -146,8 +150,8 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
   unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + F::B_TAB + F::EPB * F::B_ELEM);
 
   const int tid = threadIdx.x;
-  const int le = tid / NQD;       // element of this thread's team
-  const int tq = tid - le * NQD;  // quadrature point / team rank
+  const int le = tid / TEAM;       // element of this thread's team
+  const int tq = tid - le * TEAM;  // team rank: quadrature points tq, tq + TEAM, ...
   unsigned char* ep = sp + le * F::B_ELEM;
   T* xs = reinterpret_cast<T*>(ep); ep += F::B_XS;
   T* vs = reinterpret_cast<T*>(ep); ep += F::B_VS;
@@ -173,7 +177,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     for (int c = 0; c < DIM; ++c) x0[c] = MIXED ? A.x[c * g.nnodes + n0] : 0.0;
   }
   if (active) {
-    for (int w = tq; w < DIM * ND1; w += NQD) {
+    for (int w = tq; w < DIM * ND1; w += TEAM) {
       int c = w / ND1, i = w - c * ND1;
       int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
       int64_t node = elem_node<K>(g, E, a, b, cc);
@@ -181,15 +185,12 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
       vs[w] = from_double<T>(A.v[c * g.nnodes + node]);
       if (with_w) ws[w] = A.vtest[c * g.nnodes + node];
     }
-    for (int j = tq; j < ND2; j += NQD) es[j] = from_double<T>(A.e[el * ND2 + j]);
+    for (int j = tq; j < ND2; j += TEAM) es[j] = from_double<T>(A.e[el * ND2 + j]);
   }
-  team_sync<NQD>();
+  team_sync<TEAM>();
 
   // ---- reference gradients at the quadrature points (sum factorisation) ----
   // fields f: [0, DIM) x, [DIM, 2 DIM) v, [2 DIM, 3 DIM) test vector (FP64 path)
-  const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
-  T grad[NF][DIM];
-  T xval[DIM];
   auto field = [&](int f, int i) -> T {
     if (f < DIM) return xs[f * ND1 + i];
     if (f < 2 * DIM) return vs[(f - DIM) * ND1 + i];
@@ -200,7 +201,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     T* TB = scr;
     T* TG = scr + NF * P * NQ;
     if (active)
-      for (int w = tq; w < nf * P * NQ; w += NQD) {
+      for (int w = tq; w < nf * P * NQ; w += TEAM) {
         int x_ = w % NQ, b = (w / NQ) % P, f = w / (NQ * P);
         T sb = T(0), sg = T(0);
         for (int a = 0; a < P; ++a) {
@@ -211,22 +212,6 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         TB[(f * P + b) * NQ + x_] = sb;
         TG[(f * P + b) * NQ + x_] = sg;
       }
-    team_sync<NQD>();
-    if (active)
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        if (f >= nf) break;
-        T d0 = T(0), d1 = T(0), vv = T(0);
-        for (int b = 0; b < P; ++b) {
-          T tb = TB[(f * P + b) * NQ + qx], tg = TG[(f * P + b) * NQ + qx];
-          d0 += Bs[qy * P + b] * tg;
-          d1 += Gs[qy * P + b] * tb;
-          vv += Bs[qy * P + b] * tb;
-        }
-        grad[f][0] = d0;
-        grad[f][1] = d1;
-        if (f < DIM) xval[f] = vv;
-      }
   } else {
     T* TB = scr;
     T* TG = TB + NF * P * P * NQ;
@@ -234,7 +219,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     T* PGB = PBB + NF * P * NQ * NQ;
     T* PBG = PGB + NF * P * NQ * NQ;
     if (active)
-      for (int w = tq; w < nf * P * P * NQ; w += NQD) {
+      for (int w = tq; w < nf * P * P * NQ; w += TEAM) {
         int x_ = w % NQ, r = w / NQ;  // r = (f * P + cz) * P + b
         int b = r % P, fz = r / P;    // fz = f * P + cz
         T sb = T(0), sg = T(0);
@@ -247,9 +232,9 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         TB[r * NQ + x_] = sb;
         TG[r * NQ + x_] = sg;
       }
-    team_sync<NQD>();
+    team_sync<TEAM>();
     if (active)
-      for (int w = tq; w < nf * P * NQ * NQ; w += NQD) {
+      for (int w = tq; w < nf * P * NQ * NQ; w += TEAM) {
         int x_ = w % NQ, y_ = (w / NQ) % NQ, fz = w / (NQ * NQ);
         T bb = T(0), gb = T(0), bg = T(0);
         for (int b = 0; b < P; ++b) {
@@ -262,87 +247,114 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         PGB[w] = gb;
         PBG[w] = bg;
       }
-    team_sync<NQD>();
-    if (active)
-#pragma unroll
-      for (int f = 0; f < NF; ++f) {
-        if (f >= nf) break;
-        T d0 = T(0), d1 = T(0), d2 = T(0), vv = T(0);
-        for (int cz = 0; cz < P; ++cz) {
-          int idx = ((f * P + cz) * NQ + qy) * NQ + qx;
-          d0 += Bs[qz * P + cz] * PGB[idx];
-          d1 += Bs[qz * P + cz] * PBG[idx];
-          d2 += Gs[qz * P + cz] * PBB[idx];
-          vv += Bs[qz * P + cz] * PBB[idx];
-        }
-        grad[f][0] = d0;
-        grad[f][1] = d1;
-        grad[f][2] = d2;
-        if (f < DIM) xval[f] = vv;
-      }
   }
-  team_sync<NQD>();  // scratch is reused below
+  team_sync<TEAM>();
 
-  // ---- quadrature-point physics ----
+  // ---- quadrature-point physics, for each of the thread's QPT points ----
   double tau_q = t_inf<double>();
   int flags = 0;
-  if (active) {
-    T e_q = T(0);
-    for (int j = 0; j < ND2; ++j) {
-      int jx = j % K, jy = (j / K) % K, jz = DIM == 3 ? j / (K * K) : 0;
-      T phi = Ls[qx * K + jx] * Ls[qy * K + jy];
-      if (DIM == 3) phi *= Ls[qz * K + jz];
-      e_q += es[j] * phi;
-    }
-    T J[DIM][DIM], Gv[DIM][DIM], J0i[DIM], sigma[DIM][DIM], tau;
-    for (int c = 0; c < DIM; ++c) {
-      J0i[c] = tab<T>(g.J0inv[c], g.J0invf[c]);
-      for (int m = 0; m < DIM; ++m) {
-        J[c][m] = grad[c][m];
-        Gv[c][m] = grad[DIM + c][m];
+  if (active)
+#pragma unroll
+    for (int qq = 0; qq < QPT; ++qq) {
+      const int q = tq + qq * TEAM;  // quadrature point
+      const int qx = q % NQ, qy = (q / NQ) % NQ, qz = DIM == 3 ? q / (NQ * NQ) : 0;
+      T grad[NF][DIM];
+      T xval[DIM];
+      if constexpr (DIM == 2) {
+        const T* TB = scr;
+        const T* TG = scr + NF * P * NQ;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          if (f >= nf) break;
+          T d0 = T(0), d1 = T(0), vv = T(0);
+          for (int b = 0; b < P; ++b) {
+            T tb = TB[(f * P + b) * NQ + qx], tg = TG[(f * P + b) * NQ + qx];
+            d0 += Bs[qy * P + b] * tg;
+            d1 += Gs[qy * P + b] * tb;
+            vv += Bs[qy * P + b] * tb;
+          }
+          grad[f][0] = d0;
+          grad[f][1] = d1;
+          if (f < DIM) xval[f] = vv;
+        }
+      } else {
+        const T* PBB = scr + 2 * NF * P * P * NQ;
+        const T* PGB = PBB + NF * P * NQ * NQ;
+        const T* PBG = PGB + NF * P * NQ * NQ;
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          if (f >= nf) break;
+          T d0 = T(0), d1 = T(0), d2 = T(0), vv = T(0);
+          for (int cz = 0; cz < P; ++cz) {
+            int idx = ((f * P + cz) * NQ + qy) * NQ + qx;
+            d0 += Bs[qz * P + cz] * PGB[idx];
+            d1 += Bs[qz * P + cz] * PBG[idx];
+            d2 += Gs[qz * P + cz] * PBB[idx];
+            vv += Bs[qz * P + cz] * PBB[idx];
+          }
+          grad[f][0] = d0;
+          grad[f][1] = d1;
+          grad[f][2] = d2;
+          if (f < DIM) xval[f] = vv;
+        }
+      }
+      T e_q = T(0);
+      for (int j = 0; j < ND2; ++j) {
+        int jx = j % K, jy = (j / K) % K, jz = DIM == 3 ? j / (K * K) : 0;
+        T phi = Ls[qx * K + jx] * Ls[qy * K + jy];
+        if (DIM == 3) phi *= Ls[qz * K + jz];
+        e_q += es[j] * phi;
+      }
+      T J[DIM][DIM], Gv[DIM][DIM], J0i[DIM], sigma[DIM][DIM], tau;
+      for (int c = 0; c < DIM; ++c) {
+        J0i[c] = tab<T>(g.J0inv[c], g.J0invf[c]);
+        for (int m = 0; m < DIM; ++m) {
+          J[c][m] = grad[c][m];
+          Gv[c][m] = grad[DIM + c][m];
+        }
+      }
+      const T rho0K = from_double<T>(prm.rho0K[el]);
+      if (A.mode == kForceFull) {
+        const T pref = (MIXED && A.p_ref != nullptr) ? from_double<T>(*A.p_ref) : T(0);
+        flags |= qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, tab<T>(g.ell0, g.ell0f),
+                                        T(1) / T(K), pref, sigma, tau);
+        const double tq_d = to_double(tau);
+        tau_q = tq_d < tau_q ? tq_d : tau_q;
+      } else {
+        // reference pressure only: sigma = -p_ref I
+        const T pref = from_double<T>(*A.p_ref);
+        for (int c = 0; c < DIM; ++c)
+          for (int n = 0; n < DIM; ++n) sigma[c][n] = (c == n) ? -pref : T(0);
+      }
+      const T alphaT = DIM == 3 ? Wt[qx] * Wt[qy] * Wt[qz] : Wt[qx] * Wt[qy];
+      T Aj[DIM][DIM];
+      adj_of<T, DIM>(J, Aj);
+      for (int c = 0; c < DIM; ++c)
+        for (int m = 0; m < DIM; ++m) {
+          T acc = T(0);
+          for (int n = 0; n < DIM; ++n) acc += sigma[c][n] * Aj[m][n];
+          dq[(c * DIM + m) * NQD + q] = alphaT * acc;
+        }
+      if (!MIXED && A.D != nullptr)
+        for (int cm = 0; cm < DIM * DIM; ++cm)
+          A.D[(el * DIM * DIM + cm) * NQD + q] = (double)dq[cm * NQD + q];
+      if (!MIXED && with_w) {
+        double gsum = 0.0;
+        for (int c = 0; c < DIM; ++c)
+          for (int m = 0; m < DIM; ++m)
+            gsum += (double)dq[(c * DIM + m) * NQD + q] * (double)grad[2 * DIM + c][m];
+        gq[q] = gsum;
+      }
+      if (A.srcE != nullptr && DIM == 2) {
+        const double alpha = Wd[qx] * Wd[qy];
+        double X = x0[0] + to_double(xval[0]), Y = x0[1] + to_double(xval[1]);
+        gq[NQD + q] = alpha * prm.rho0K[el] * tg_source(X, Y, prm.ph.gamma);
       }
     }
-    const T rho0K = from_double<T>(prm.rho0K[el]);
-    if (A.mode == kForceFull) {
-      const T pref = (MIXED && A.p_ref != nullptr) ? from_double<T>(*A.p_ref) : T(0);
-      flags = qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, tab<T>(g.ell0, g.ell0f),
-                                     T(1) / T(K), pref, sigma, tau);
-      tau_q = to_double(tau);
-    } else {
-      // reference pressure only: sigma = -p_ref I
-      const T pref = from_double<T>(*A.p_ref);
-      for (int c = 0; c < DIM; ++c)
-        for (int n = 0; n < DIM; ++n) sigma[c][n] = (c == n) ? -pref : T(0);
-    }
-    const T alphaT = DIM == 3 ? Wt[qx] * Wt[qy] * Wt[qz] : Wt[qx] * Wt[qy];
-    T Aj[DIM][DIM];
-    adj_of<T, DIM>(J, Aj);
-    for (int c = 0; c < DIM; ++c)
-      for (int m = 0; m < DIM; ++m) {
-        T acc = T(0);
-        for (int n = 0; n < DIM; ++n) acc += sigma[c][n] * Aj[m][n];
-        dq[(c * DIM + m) * NQD + tq] = alphaT * acc;
-      }
-    if (!MIXED && A.D != nullptr)
-      for (int cm = 0; cm < DIM * DIM; ++cm)
-        A.D[(el * DIM * DIM + cm) * NQD + tq] = (double)dq[cm * NQD + tq];
-    if (!MIXED && with_w) {
-      double gsum = 0.0;
-      for (int c = 0; c < DIM; ++c)
-        for (int m = 0; m < DIM; ++m)
-          gsum += (double)dq[(c * DIM + m) * NQD + tq] * (double)grad[2 * DIM + c][m];
-      gq[tq] = gsum;
-    }
-    if (A.srcE != nullptr && DIM == 2) {
-      const double alpha = Wd[qx] * Wd[qy];
-      double X = x0[0] + to_double(xval[0]), Y = x0[1] + to_double(xval[1]);
-      gq[NQD + tq] = alpha * prm.rho0K[el] * tg_source(X, Y, prm.ph.gamma);
-    }
-  }
   // time-step estimate and error flags of the block
   if (A.tau_bits != nullptr) tile_min_to<NTT>(tau_to_bits(tau_q), red, A.tau_bits);
   if (flags && A.status != nullptr) atomicOr(A.status, flags);
-  team_sync<NQD>();
+  team_sync<TEAM>();
 
   // ---- transposed contractions ----
   if constexpr (!MIXED) {
@@ -352,16 +364,16 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     if constexpr (DIM == 2) {
       T* Y = scr;
       if (active)
-        for (int w = tq; w < DIM * DIM * P * NQ; w += NQD) {
+        for (int w = tq; w < DIM * DIM * P * NQ; w += TEAM) {
           int x_ = w % NQ, b = (w / NQ) % P, cm = w / (NQ * P), m = cm % DIM;
           const T* X = (m == 1) ? Gs : Bs;
           T s = T(0);
           for (int y_ = 0; y_ < NQ; ++y_) s += X[y_ * P + b] * dq[cm * NQD + y_ * NQ + x_];
           Y[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < DIM * ND1; w += NQD) {
+        for (int w = tq; w < DIM * ND1; w += TEAM) {
           int c = w / ND1, i = w - c * ND1, a = i % P, b = i / P;
           T s = T(0);
           for (int m = 0; m < DIM; ++m) {
@@ -375,7 +387,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
       T* Y = scr;
       T* Z = scr + DIM * DIM * P * NQ * NQ;
       if (active)
-        for (int w = tq; w < DIM * DIM * P * NQ * NQ; w += NQD) {
+        for (int w = tq; w < DIM * DIM * P * NQ * NQ; w += TEAM) {
           int x_ = w % NQ, y_ = (w / NQ) % NQ, cz = (w / (NQ * NQ)) % P, cm = w / (NQ * NQ * P);
           int m = cm % DIM;
           const T* X = (m == 2) ? Gs : Bs;
@@ -384,9 +396,9 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[z_ * P + cz] * dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
           Y[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < DIM * DIM * P * P * NQ; w += NQD) {
+        for (int w = tq; w < DIM * DIM * P * P * NQ; w += TEAM) {
           int x_ = w % NQ, b = (w / NQ) % P, cz = (w / (NQ * P)) % P, cm = w / (NQ * P * P);
           int m = cm % DIM;
           const T* X = (m == 1) ? Gs : Bs;
@@ -395,9 +407,9 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[y_ * P + b] * Y[((cm * P + cz) * NQ + y_) * NQ + x_];
           Z[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < DIM * ND1; w += NQD) {
+        for (int w = tq; w < DIM * ND1; w += TEAM) {
           int c = w / ND1, i = w - c * ND1, a = i % P, b = (i / P) % P, cz = i / (P * P);
           T s = T(0);
           for (int m = 0; m < DIM; ++m) {
@@ -416,7 +428,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     if constexpr (DIM == 2) {
       T* Y = scr;
       if (active)
-        for (int w = tq; w < DIM * DIM * PK * NQ; w += NQD) {
+        for (int w = tq; w < DIM * DIM * PK * NQ; w += TEAM) {
           int x_ = w % NQ, u = (w / NQ) % PK, cm = w / (NQ * PK), m = cm % DIM;
           int b = u / K, jy = u - b * K;
           const T* X = (m == 1) ? Gs : Bs;
@@ -425,9 +437,9 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[y_ * P + b] * Ls[y_ * K + jy] * dq[cm * NQD + y_ * NQ + x_];
           Y[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < DIM * ND1 * ND2; w += NQD) {
+        for (int w = tq; w < DIM * ND1 * ND2; w += TEAM) {
           int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
           int a = i % P, b = i / P, jx = j % K, jy = j / K;
           T s = T(0);
@@ -442,7 +454,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
       T* Y = scr;
       T* Z = scr + DIM * DIM * PK * NQ * NQ;
       if (active)
-        for (int w = tq; w < DIM * DIM * PK * NQ * NQ; w += NQD) {
+        for (int w = tq; w < DIM * DIM * PK * NQ * NQ; w += TEAM) {
           int x_ = w % NQ, y_ = (w / NQ) % NQ, u = (w / (NQ * NQ)) % PK, cm = w / (NQ * NQ * PK);
           int m = cm % DIM, cz = u / K, jz = u - cz * K;
           const T* X = (m == 2) ? Gs : Bs;
@@ -451,9 +463,9 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[z_ * P + cz] * Ls[z_ * K + jz] * dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
           Y[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < DIM * DIM * PK * PK * NQ; w += NQD) {
+        for (int w = tq; w < DIM * DIM * PK * PK * NQ; w += TEAM) {
           int x_ = w % NQ, uy = (w / NQ) % PK, uz = (w / (NQ * PK)) % PK, cm = w / (NQ * PK * PK);
           int m = cm % DIM, b = uy / K, jy = uy - b * K;
           const T* X = (m == 1) ? Gs : Bs;
@@ -462,9 +474,9 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
             s += X[y_ * P + b] * Ls[y_ * K + jy] * Y[((cm * PK + uz) * NQ + y_) * NQ + x_];
           Z[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < DIM * ND1 * ND2; w += NQD) {
+        for (int w = tq; w < DIM * ND1 * ND2; w += TEAM) {
           int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
           int a = i % P, b = (i / P) % P, cz = i / (P * P);
           int jx = j % K, jy = (j / K) % K, jz = j / (K * K);
@@ -479,13 +491,13 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
           fk[w] = s;
         }
     }
-    team_sync<NQD>();
+    team_sync<TEAM>();
     if (active) {
       if (A.FK != nullptr)
-        for (int w = tq; w < DIM * ND1 * ND2; w += NQD) A.FK[el * (DIM * ND1 * ND2) + w] = fk[w];
+        for (int w = tq; w < DIM * ND1 * ND2; w += TEAM) A.FK[el * (DIM * ND1 * ND2) + w] = fk[w];
       // F.1 = row sums: error-free FP32 sums (the rounding errors collected
       // apart), widened to FP64 (the FP32 entries summed to ~2^-48)
-      for (int w = tq; w < DIM * ND1; w += NQD) {
+      for (int w = tq; w < DIM * ND1; w += TEAM) {
         float S = fk[w * ND2], C = 0.0f;
         for (int j = 1; j < ND2; ++j) {
           float s2, e2;
@@ -497,7 +509,7 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
       }
       // F^T w in FP64
       if (with_w)
-        for (int j = tq; j < ND2; j += NQD) {
+        for (int j = tq; j < ND2; j += TEAM) {
           double s = 0.0;
           for (int ci = 0; ci < DIM * ND1; ++ci) s = fma(f2d_exact(fk[ci * ND2 + j]), ws[ci], s);
           A.FTvE[slot * ND2 + j] = s;
@@ -510,20 +522,20 @@ l2_part:
   const bool do_ftv = (!MIXED) && with_w;
   const bool do_src = (A.srcE != nullptr) && DIM == 2;
   if (do_ftv || do_src) {
-    team_sync<NQD>();
+    team_sync<TEAM>();
     // field 0: F^T w integrand, field 1: source integrand
     if constexpr (DIM == 2) {
       double* R1 = l2s;  // [2][K][NQ]
       if (active)
-        for (int w = tq; w < 2 * K * NQ; w += NQD) {
+        for (int w = tq; w < 2 * K * NQ; w += TEAM) {
           int y_ = w % NQ, jx = (w / NQ) % K, fld = w / (NQ * K);
           double s = 0.0;
           for (int x_ = 0; x_ < NQ; ++x_) s += Ld[x_ * K + jx] * gq[fld * NQD + y_ * NQ + x_];
           R1[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < 2 * ND2; w += NQD) {
+        for (int w = tq; w < 2 * ND2; w += TEAM) {
           int fld = w / ND2, j = w - fld * ND2, jx = j % K, jy = j / K;
           if ((fld == 0 && !do_ftv) || (fld == 1 && !do_src)) continue;
           double s = 0.0;
@@ -535,25 +547,25 @@ l2_part:
       double* R1 = l2s;                 // [2][K][NQ][NQ]
       double* R2 = l2s + 2 * K * NQ * NQ;  // [2][K][K][NQ]
       if (active)
-        for (int w = tq; w < 2 * K * NQ * NQ; w += NQD) {
+        for (int w = tq; w < 2 * K * NQ * NQ; w += TEAM) {
           int y_ = w % NQ, z_ = (w / NQ) % NQ, jx = (w / (NQ * NQ)) % K, fld = w / (NQ * NQ * K);
           double s = 0.0;
           for (int x_ = 0; x_ < NQ; ++x_)
             s += Ld[x_ * K + jx] * gq[fld * NQD + (z_ * NQ + y_) * NQ + x_];
           R1[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < 2 * K * K * NQ; w += NQD) {
+        for (int w = tq; w < 2 * K * K * NQ; w += TEAM) {
           int z_ = w % NQ, jx = (w / NQ) % K, jy = (w / (NQ * K)) % K, fld = w / (NQ * K * K);
           double s = 0.0;
           for (int y_ = 0; y_ < NQ; ++y_)
             s += Ld[y_ * K + jy] * R1[((fld * K + jx) * NQ + z_) * NQ + y_];
           R2[w] = s;
         }
-      team_sync<NQD>();
+      team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < 2 * ND2; w += NQD) {
+        for (int w = tq; w < 2 * ND2; w += TEAM) {
           int fld = w / ND2, j = w - fld * ND2, jx = j % K, jy = (j / K) % K, jz = j / (K * K);
           if ((fld == 0 && !do_ftv) || (fld == 1 && !do_src)) continue;
           double s = 0.0;
@@ -564,7 +576,7 @@ l2_part:
         }
     }
   }
-  team_sync<NQD>();  // the team reuses its element area in the next tile
+  team_sync<TEAM>();  // the team reuses its element area in the next tile
 }
 
 template <int DIM, int K, bool MIXED>

@@ -78,7 +78,7 @@ class lh_batch_stats(ctypes.Structure):
 
 class lh_batch_tuning(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("smem_lines", ctypes.c_int32)]
+                ("smem_lines", ctypes.c_int32), ("qpt", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p

@@ -154,10 +154,12 @@ def test_batch_launch_shapes_agree_and_autotune_keeps_state():
     os_, vs, es, xs = _random_batch_state(cfgs, seed=11)
     dts = np.array([1e-3, 1.5e-3, 0.7e-3])
     ref = None
-    for threads in (256, 512, 1024):
-        for sl in (2, 1, 0):
-            b = _batch(cfgs, "mixed", tuning=dict(threads=threads, ctas_per_sm=1, smem_lines=sl))
-            assert b.tuning()["threads"] == threads
+    shapes = [(t, sl, 1) for t in (256, 512, 1024) for sl in (2, 1, 0)]
+    shapes += [(t, 2, 2) for t in (256, 512, 1024)]  # two quadrature points per thread
+    for threads, sl, qpt in shapes:
+            b = _batch(cfgs, "mixed", tuning=dict(threads=threads, ctas_per_sm=1, smem_lines=sl,
+                                                  qpt=qpt))
+            assert b.tuning()["threads"] == threads and b.tuning()["qpt"] == qpt
             b.set_state(dev(_pack(vs)), dev(_pack(es)), dev(_pack(xs)))
             b.step_fixed(dts)
             out = [host(t) for t in b.get_state()]
@@ -173,6 +175,7 @@ def test_batch_launch_shapes_agree_and_autotune_keeps_state():
     q0 = b.query()
     chosen = b.autotune(reps=1)
     assert chosen["threads"] in (256, 512, 1024) and chosen["ctas_per_sm"] >= 1
+    assert chosen["qpt"] in (1, 2)
     after = [host(t) for t in b.get_state()]
     for a, c in zip(before, after):
         assert np.array_equal(a, c)
