@@ -59,7 +59,7 @@ typedef enum lh_status {
   LH_ENONFINITE = 5,   /* NaN or Inf in the state */
   LH_EDTMIN = 6,       /* step size collapsed below dt_min_frac * t_final */
   LH_ECG = 7,          /* CG did not reach cg_rtol within cg_maxit iterations */
-  LH_ETIMEOUT = 8,     /* a device-wide barrier waited longer than its limit */
+  LH_ETIMEOUT = 8,     /* reserved: no kernel of the library waits on another block */
   LH_EUNSUPPORTED = 9, /* valid but not built (order/dimension/quadrature) */
   LH_ETOOLARGE = 10    /* the mesh does not fit the fixed working memory of
                           lh_force_static */

@@ -1,6 +1,7 @@
 // Device helpers shared by the kernels of the library: structured-mesh index
 // arithmetic, deterministic block reductions, the ordered-bits minimum used for
-// the time-step estimate and a bounded grid barrier for cooperative kernels.
+// the time-step estimate, integer-pipe precision conversions and dependent
+// launches.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -242,48 +243,6 @@ __device__ __forceinline__ void block_min_to(unsigned long long v, unsigned long
     __syncthreads();
   }
   if (tid == 0) atomicMin(dst, sh[0]);
-}
-
-// ------------------------------------------------------------- barrier ----
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: after ~2 s it records kDevTimeout in *status and returns
-// false, so the kernel can leave instead of hanging.
-__device__ __forceinline__ bool grid_barrier(Barrier* bar, int* status) {
-  __shared__ int ok_sh;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &bar->gen;
-    unsigned int gen = *vgen;
-    __threadfence();
-    unsigned int arrived = atomicAdd(&bar->count, 1u);
-    int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      unsigned long long t0 = global_ns();
-      while (*vgen == gen) {
-        __nanosleep(40);
-        if (global_ns() - t0 > 2000000000ull) {
-          atomicOr(status, kDevTimeout);
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    ok_sh = ok;
-  }
-  __syncthreads();
-  return ok_sh != 0;
 }
 
 }  // namespace lagh

@@ -97,12 +97,6 @@ struct CgDev {
   unsigned int ticket[8];
 };
 
-// Grid barrier state (cooperative persistent kernels).
-struct Barrier {
-  unsigned int count;
-  unsigned int gen;
-};
-
 // Tensor-product preconditioner: the inverses of the assembled 1D reference
 // mass matrices along each direction, full (variant 0) and without the two end
 // nodes (variant 1, the wall-normal component), truncated to the band
@@ -143,7 +137,6 @@ struct Arrays {
   double *lfac64;               // the same bands in FP64
   double *lchol;                // exact preconditioner: scaled Cholesky rows (FP64)
   CgDev* cg;
-  Barrier* bar;
   Ctl* ctl;
 };
 

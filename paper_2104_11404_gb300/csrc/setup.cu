@@ -296,7 +296,7 @@ extern "C" const char* lh_status_string(lh_status s) {
     case LH_ENONFINITE: return "non-finite state";
     case LH_EDTMIN: return "time step collapsed";
     case LH_ECG: return "CG did not converge";
-    case LH_ETIMEOUT: return "device barrier timed out";
+    case LH_ETIMEOUT: return "device wait timed out";
     case LH_EUNSUPPORTED: return "unsupported configuration";
     case LH_ETOOLARGE: return "mesh exceeds the fixed working memory";
   }
@@ -314,7 +314,6 @@ static void free_all(lh_ctx* c) {
   for (double** p : dptrs)
     if (*p) { cudaFree(*p); *p = nullptr; }
   if (c->a.FK) { cudaFree(c->a.FK); c->a.FK = nullptr; }
-  if (c->a.bar) { cudaFree(c->a.bar); c->a.bar = nullptr; }
   if (c->a.ctl) { cudaFree(c->a.ctl); c->a.ctl = nullptr; }
   if (c->a.cg) { cudaFree(c->a.cg); c->a.cg = nullptr; }
   if (c->a.lfac) { cudaFree(c->a.lfac); c->a.lfac = nullptr; }
@@ -430,7 +429,6 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   if (e == cudaSuccess) e = dalloc(&A.cg, 1);
   if (e == cudaSuccess) e = cudaMemset(A.cg, 0, sizeof(CgDev));
   if (e == cudaSuccess) e = dalloc(&A.aux, 16);
-  if (e == cudaSuccess) e = dalloc(&A.bar, 1);
   if (e == cudaSuccess) e = dalloc(&A.ctl, 1);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->ctl_host, sizeof(Ctl));
   if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
@@ -563,7 +561,6 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   }
   if (e == cudaSuccess)
     e = cudaMemcpy(A.dinv, diag.data(), g.nnodes * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(A.bar, 0, sizeof(Barrier));
   if (e == cudaSuccess) e = cudaMemcpy(A.ctl, &ctl0, sizeof(Ctl), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(A.srcE, 0, ne * sizeof(double));
   if ((st = cuda_check(c, e, "upload")) != LH_OK) return fail(st, c->err);
@@ -766,10 +763,6 @@ lh_status lagh::device_status(lh_ctx* c) {
   lh_status st = cuda_check(c, err, "device status");
   if (st != LH_OK) return st;
   int s = c->ctl_host->status;
-  if (s & kDevTimeout) {
-    cudaMemsetAsync(c->a.bar, 0, sizeof(Barrier), c->stream);
-    return set_error(c, LH_ETIMEOUT, "device barrier wait exceeded its limit");
-  }
   if (s & kDevNonFinite) return set_error(c, LH_ENONFINITE, "non-finite value in the state");
   if (s & kDevDtMin) return set_error(c, LH_EDTMIN, "time step collapsed below dt_min");
   if (s & kDevCG) return set_error(c, LH_ECG, "CG did not converge within cg_maxit");

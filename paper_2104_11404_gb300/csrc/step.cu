@@ -243,10 +243,6 @@ static cudaError_t estimate_into_aux(lh_ctx* c, cudaStream_t s) {
 }
 
 static lh_status status_from(lh_ctx* c, int s) {
-  if (s & kDevTimeout) {
-    cudaMemsetAsync(c->a.bar, 0, sizeof(Barrier), c->work);
-    return set_error(c, LH_ETIMEOUT, "device barrier wait exceeded its limit");
-  }
   if (s & kDevNonFinite) return set_error(c, LH_ENONFINITE, "non-finite value in the state");
   if (s & kDevCG) return set_error(c, LH_ECG, "CG did not converge within cg_maxit");
   if (s & kDevDtMin) return set_error(c, LH_EDTMIN, "time step collapsed below dt_min");
