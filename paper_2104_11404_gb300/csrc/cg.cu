@@ -959,8 +959,14 @@ cudaError_t cg_solve_eager(const lh_ctx* c, const double* rhs, double* out, cuda
   return cudaSuccess;
 }
 
-// Inside a stream capture on s: the init kernels, then a WHILE conditional
-// node whose body (captured on `side`) is one CG iteration.
+// Inside a stream capture on s: the init kernels, the first kUnrolled
+// iterations as plain kernels (each returns at once after convergence; the
+// last update clears the loop condition if the solve has converged), then a
+// WHILE conditional node whose body (captured on `side`) is one CG iteration,
+// for solves that need more.  A conditional node relaunches its body graph
+// per iteration, so the usual iterations run without it.
+constexpr int kUnrolled = 3;
+
 cudaError_t cg_solve_capture(const lh_ctx* c, const double* rhs, double* out, const Ctl* gate,
                              cudaStream_t s, cudaStream_t side) {
   CgArgs a = make_args(c, rhs, out, gate);
@@ -976,6 +982,15 @@ cudaError_t cg_solve_capture(const lh_ctx* c, const double* rhs, double* out, co
   if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
   cudaGraphConditionalHandle h;
   e = cudaGraphConditionalHandleCreate(&h, cap, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return e;
+  const int unrolled = c->tpc.enabled ? kUnrolled : 0;  // Jacobi needs tens of iterations
+  for (int u = 0; u < unrolled; ++u) {
+    CgArgs au = a;
+    au.has_cond = (u == unrolled - 1) ? 1 : 0;
+    au.cond = h;
+    if ((e = cg_body(c, au, s)) != cudaSuccess) return e;
+  }
+  e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &cap, &deps, nullptr, &ndeps);
   if (e != cudaSuccess) return e;
   cudaGraphNodeParams np = {};
   np.type = cudaGraphNodeTypeConditional;
