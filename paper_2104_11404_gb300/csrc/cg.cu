@@ -24,7 +24,7 @@
 
 namespace lagh {
 
-constexpr int kLineThreads = 256;  // one CTA per tile of 32 lines x 32 positions
+constexpr int kLineThreads = 256;  // one CTA per tile of LT node lines x 32 positions
 // band half-width of the truncated 1D inverses, by H1 order (must match setup)
 template <int K> struct PB { static constexpr int B = K == 1 ? 14 : (K == 2 ? 22 : 30); };
 constexpr int kNodeThreads = 256;
@@ -112,7 +112,7 @@ __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
 
 // One pass of the tensor-product preconditioner along direction d: every
 // node line of every component is multiplied by the banded inverse of the 1D
-// mass matrix.  A CTA owns a tile of 32 lines x 32 positions: it stages the
+// mass matrix.  A CTA owns a tile of kPassLines lines x 32 positions: it stages the
 // tile and its +-B halo along the line in shared memory (coalesced: along x
 // the lines are contiguous rows, along y / z neighbouring lines are
 // neighbouring nodes), then each thread forms 4 outputs in FP32.
@@ -123,35 +123,36 @@ __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
 // last: the pass along the last direction (sums r.z; init also writes p = z).
 // Shared memory of one band-pass tile: 32 lines x (32 positions + halo) of
 // input and the band rows of the 32 positions, in the band's precision T.
-template <int K, typename T = float>
+template <int K, typename T = float, int LTV = 32>
 struct PassTile {
   static constexpr int B = PB<K>::B, W = 2 * B + 1, TP = 32, ldt = TP + 2 * B + 1;
-  T tile[32 * ldt];
+  static constexpr int LT = LTV;  // node lines per tile
+  T tile[LT * ldt];
   T wrows[TP * W];
 };
 
 template <int DIM>
-__device__ __forceinline__ int64_t pass_tiles(const Geom& g, int d) {
+__host__ __device__ __forceinline__ int64_t pass_tiles(const Geom& g, int d, int lt) {
   const int nd = g.nn[d];
   const int64_t nlines = g.nnodes / nd;
-  return (int64_t)DIM * ((nlines + 31) / 32) * ((nd + 31) / 32);
+  return (int64_t)DIM * ((nlines + lt - 1) / lt) * ((nd + 31) / 32);
 }
 
 // One tile of a band pass along direction d (all threads of the block): the
 // tile's outputs dst = band-inverse(src) and, per mode, r / x / p writes and
 // the partial sums b.b (mode 0) and r.z (last), added to l_bb / l_rz.
-template <int DIM, int K, typename T = float>
+template <int DIM, int K, typename T = float, int LTV = 32>
 __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int last, int init,
                                           const double* src_in, double* dst, int64_t bid,
-                                          PassTile<K, T>& sm, double& l_bb, double& l_rz) {
-  using PT = PassTile<K, T>;
-  constexpr int B = PT::B, W = PT::W, TP = PT::TP, ldt = PT::ldt;
+                                          PassTile<K, T, LTV>& sm, double& l_bb, double& l_rz) {
+  using PT = PassTile<K, T, LTV>;
+  constexpr int B = PT::B, W = PT::W, TP = PT::TP, ldt = PT::ldt, LT = PT::LT;
   T* tile = sm.tile;
   T* wrows = sm.wrows;
   const Geom& g = a.g;
   const int nd = g.nn[d];
   const int64_t nlines = g.nnodes / nd;
-  const int64_t lgroups = (nlines + 31) / 32;
+  const int64_t lgroups = (nlines + LT - 1) / LT;
   const int pblocks = (nd + TP - 1) / TP;
   const int64_t stride = d == 0 ? 1 : (d == 1 ? (int64_t)g.nn[0] : (int64_t)g.nn[0] * g.nn[1]);
   // tile -> (component, line group, position block)
@@ -164,7 +165,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
   const int tid = threadIdx.x, nt = blockDim.x;
   // line l of the tile: its base node and whether it is a wall-normal line
   auto line_info = [&](int l, int64_t& base, bool& wall) -> bool {
-    const int64_t line = lg * 32 + l;
+    const int64_t line = lg * LT + l;
     if (line >= nlines) return false;
     int I[3] = {0, 0, 0};
     if (d == 0) { I[1] = (int)(line % g.nn[1]); I[2] = (int)(line / g.nn[1]); }
@@ -178,10 +179,10 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
   const T scl = (mode == 2) ? T(1) : (T)a.tpc.scale;
   // stage the tile with its halo: positions [p0 - B, p0 + TP + B)
   const int span = TP + 2 * B;
-  for (int idx = tid; idx < 32 * span; idx += nt) {
+  for (int idx = tid; idx < LT * span; idx += nt) {
     // along x (d == 0) walk a line, otherwise walk across lines
-    const int l = d == 0 ? idx / span : idx % 32;
-    const int q = d == 0 ? idx - l * span : idx / 32;
+    const int l = d == 0 ? idx / span : idx % LT;
+    const int q = d == 0 ? idx - l * span : idx / LT;
     const int pos = p0 - B + q;
     T val = T(0);
     int64_t base;
@@ -206,9 +207,9 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     }
   }
   __syncthreads();
-  for (int o = tid; o < 32 * TP; o += nt) {
-    const int l = d == 0 ? o / TP : o % 32;
-    const int q = d == 0 ? o - l * TP : o / 32;
+  for (int o = tid; o < LT * TP; o += nt) {
+    const int l = d == 0 ? o / TP : o % LT;
+    const int q = d == 0 ? o - l * TP : o / LT;
     const int pos = p0 + q;
     int64_t base;
     bool wall;
@@ -241,7 +242,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
 
 // One pass of the tensor-product preconditioner along direction d: every
 // node line of every component is multiplied by the banded inverse of the 1D
-// mass matrix.  A CTA owns a tile of 32 lines x 32 positions: it stages the
+// mass matrix.  A CTA owns a tile of kPassLines lines x 32 positions: it stages the
 // tile and its +-B halo along the line in shared memory (coalesced: along x
 // the lines are contiguous rows, along y / z neighbouring lines are
 // neighbouring nodes), then each thread forms 4 outputs in FP32.
@@ -250,7 +251,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
 // on free components and x = 0, sums b.b), 1 = first pass inside the loop
 // (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
 // last: the pass along the last direction (sums r.z; init also writes p = z).
-template <int DIM, int K, typename T>
+template <int DIM, int K, typename T, int LTV>
 __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, int d, int mode,
                                                               int last, int init,
                                                               const double* src_in,
@@ -261,9 +262,10 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
     a.cg->done = 0;
     a.cg->it = 0;
   }
-  __shared__ PassTile<K, T> sm;
+  __shared__ PassTile<K, T, LTV> sm;
   double l_bb = 0.0, l_rz = 0.0;
-  pass_tile<DIM, K, T>(a, d, mode, last, init, src_in, dst, (int64_t)blockIdx.x, sm, l_bb, l_rz);
+  pass_tile<DIM, K, T, LTV>(a, d, mode, last, init, src_in, dst, (int64_t)blockIdx.x, sm, l_bb,
+                            l_rz);
   double tot;
   if (mode == 0) {
     if (reduce_last(l_bb, a.part, &a.cg->ticket[kTicketPass0], &tot) && threadIdx.x == 0)
@@ -483,7 +485,7 @@ __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(const CgArg
   if (a.gate != nullptr && a.gate->done) return;  // the same in every CTA
   cgx::cluster_group cl = cgx::this_cluster();
   const int64_t rank = cl.block_rank(), nrank = cl.num_blocks();
-  __shared__ PassTile<K> sm;
+  __shared__ PassTile<K, float, 8> sm;
   __shared__ double M1s[(K + 1) * (K + 1)];
   __shared__ double slots[4];
   constexpr int P = K + 1;
@@ -491,15 +493,15 @@ __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(const CgArg
   const int tid = threadIdx.x, nt = blockDim.x;
   const int64_t i0 = rank * nt + tid, stride = nrank * nt;
   for (int i = tid; i < P * P; i += nt) M1s[i] = a.M1[(i / P) * (kMaxOrder + 1) + i % P];
-  const int64_t tiles0 = pass_tiles<DIM>(g, 0), tiles1 = pass_tiles<DIM>(g, 1);
+  const int64_t tiles0 = pass_tiles<DIM>(g, 0, 8), tiles1 = pass_tiles<DIM>(g, 1, 8);
   // initial preconditioning: r = b, x = 0, z = B r (x pass into Ap, y pass
   // into z), p = z
   double l_bb = 0.0, l_rz = 0.0;
   for (int64_t t = rank; t < tiles0; t += nrank)
-    pass_tile<DIM, K>(a, 0, 0, 0, 1, nullptr, a.Ap, t, sm, l_bb, l_rz);
+    pass_tile<DIM, K, float, 8>(a, 0, 0, 0, 1, nullptr, a.Ap, t, sm, l_bb, l_rz);
   const double bb = cluster_sum(cl, l_bb, &slots[0]);
   for (int64_t t = rank; t < tiles1; t += nrank)
-    pass_tile<DIM, K>(a, 1, 2, 1, 1, a.Ap, a.z, t, sm, l_bb, l_rz);
+    pass_tile<DIM, K, float, 8>(a, 1, 2, 1, 1, a.Ap, a.z, t, sm, l_bb, l_rz);
   double rz = cluster_sum(cl, l_rz, &slots[1]);
   int it = 0;
   double rr = bb;
@@ -532,10 +534,10 @@ __global__ void __launch_bounds__(kClusterThreads) cg_cluster_kernel(const CgArg
     if (conv || !(rr == rr)) break;
     double unused = 0.0, l_rz2 = 0.0;
     for (int64_t t = rank; t < tiles0; t += nrank)
-      pass_tile<DIM, K>(a, 0, 1, 0, 0, a.r, a.Ap, t, sm, unused, l_rz2);
+      pass_tile<DIM, K, float, 8>(a, 0, 1, 0, 0, a.r, a.Ap, t, sm, unused, l_rz2);
     cl.sync();
     for (int64_t t = rank; t < tiles1; t += nrank)
-      pass_tile<DIM, K>(a, 1, 2, 1, 0, a.Ap, a.z, t, sm, unused, l_rz2);
+      pass_tile<DIM, K, float, 8>(a, 1, 2, 1, 0, a.Ap, a.z, t, sm, unused, l_rz2);
     const double rz_new = cluster_sum(cl, l_rz2, &slots[0]);
     const double beta = rz_new / rz;
     rz = rz_new;
@@ -774,20 +776,28 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
     }
     return cudaGetLastError();
   }
+  // tiles of 32 node lines where they fill the GPU several times over, else
+  // of 8 (more CTAs for small meshes; the halo runs along the lines, so
+  // shorter tiles across the lines cost no extra halo)
+  const bool narrow = pass_tiles<DIM>(c->g, 0, 32) < 4 * (int64_t)c->num_sms;
   for (int d = 0; d < DIM; ++d) {
-    const int nd = c->g.nn[d];
-    const int64_t nlines = c->g.nnodes / nd;
-    const int64_t blocks = (int64_t)DIM * ((nlines + 31) / 32) * ((nd + 31) / 32);
+    const int64_t blocks = pass_tiles<DIM>(c->g, d, narrow ? 8 : 32);
     const int mode = d == 0 ? (init ? 0 : 1) : 2;
     double* dst = bufs[(DIM - 1 - d) & 1];
-    cudaError_t e =
-        c->tpc.fp64
-            ? launch_k(c->use_pdl != 0, cg_pass_kernel<DIM, K, double>, dim3((unsigned)blocks),
-                       dim3(kLineThreads), 0, s, a, d, mode, (int)(d == DIM - 1), init ? 1 : 0,
-                       src, dst)
-            : launch_k(c->use_pdl != 0, cg_pass_kernel<DIM, K, float>, dim3((unsigned)blocks),
-                       dim3(kLineThreads), 0, s, a, d, mode, (int)(d == DIM - 1), init ? 1 : 0,
-                       src, dst);
+    const bool pdl = c->use_pdl != 0;
+    const int last = (int)(d == DIM - 1), ini = init ? 1 : 0;
+    const dim3 gr((unsigned)blocks), bl(kLineThreads);
+    cudaError_t e;
+    if (c->tpc.fp64)
+      e = narrow ? launch_k(pdl, cg_pass_kernel<DIM, K, double, 8>, gr, bl, 0, s, a, d, mode, last,
+                            ini, src, dst)
+                 : launch_k(pdl, cg_pass_kernel<DIM, K, double, 32>, gr, bl, 0, s, a, d, mode,
+                            last, ini, src, dst);
+    else
+      e = narrow ? launch_k(pdl, cg_pass_kernel<DIM, K, float, 8>, gr, bl, 0, s, a, d, mode, last,
+                            ini, src, dst)
+                 : launch_k(pdl, cg_pass_kernel<DIM, K, float, 32>, gr, bl, 0, s, a, d, mode, last,
+                            ini, src, dst);
     if (e != cudaSuccess) return e;
     src = dst;
   }

@@ -355,13 +355,16 @@ def test_cluster_cg_matches_kernel_chain(name, n):
     gk = gpu_for(cfg, phys_overrides={"cg_cluster": -1})
     xc, itc, rrc = gc.mass_solve_v(dev(b))
     xk, itk, rrk = gk.mass_solve_v(dev(b))
-    assert itc == itk and rrc <= 1e-14 and rrk <= 1e-14
+    assert abs(itc - itk) <= 1 and rrc <= 1e-14 and rrk <= 1e-14
     assert rel_l2(xo, host(xc)) <= 1e-12 and rel_l2(host(xk), host(xc)) <= 1e-13
     gc.init_state()
     gk.init_state()
     sc = gc.run_to(cfg["t_final"], max_steps=6)
     sk = gk.run_to(cfg["t_final"], max_steps=6)
-    assert sc["steps"] == sk["steps"] and sc["cg_iters"] == sk["cg_iters"]
+    # a solve that converges right at the tolerance may take one more iteration
+    # in either form (the sums differ in rounding order)
+    assert sc["steps"] == sk["steps"]
+    assert abs(sc["cg_iters"] - sk["cg_iters"]) <= 2 * (sc["steps"] + sc["rejects"])
     vc, ec, _, _, _ = gc.get_state()
     vk, ek, _, _, _ = gk.get_state()
     assert rel_l2(host(vk), host(vc)) <= 1e-10 and rel_l2(host(ek), host(ec)) <= 1e-10
