@@ -28,7 +28,9 @@ sys.path.insert(0, ROOT)
 CHUNK = 50           # accepted time steps per bench step
 WORKLOAD = "tg2d_64"
 BATCH_CHUNK = 20     # accepted time steps of every instance per batched bench step
-PASS_KERNEL_DRAM_BYTES = 541867  # mean of 3 captured launches (631 KB, 364 KB, 631 KB read; 0 written)
+# DRAM read + write per launch of the preconditioner kernel on this workload,
+# from an ncu capture (cold caches); None until the current kernel is captured
+PASS_KERNEL_DRAM_BYTES = None
 
 
 def _dist():
@@ -239,7 +241,8 @@ def run_native(args):
             e1.synchronize()
             force_ms = e0.elapsed_time(e1) / reps
             # the CG preconditioner passes (dominant by share in the launch list):
-            # one application = dim pass kernels + one 4-byte memset
+            # one application = precond_kernels launches (the tile kernel, or
+            # one line pass per direction)
             r = torch.randn(nv, dtype=torch.float64, device="cuda")
             z = torch.empty_like(r)
             lagh.lh_precond_apply(g.ctx, r, z)
@@ -250,11 +253,13 @@ def run_native(args):
                 lagh.lh_precond_apply(g.ctx, r, z)
             e1.record(stream)
             e1.synchronize()
-            pass_ms = e0.elapsed_time(e1) / reps / cfg["dim"]
+            pk = g.layout.precond_kernels
+            pass_ms = e0.elapsed_time(e1) / reps / pk
             g.close()
         return dict(dev_ms=max_over_ranks(dev_ms), steps=sum_over_ranks(steps), cg=cg,
                     rejects=rejects, wall=wall, clocks=clocks, e2e_ms=max_over_ranks(e2e_ms),
-                    e2e_steps=sum_over_ranks(e2e_steps), force_ms=force_ms, pass_ms=pass_ms)
+                    e2e_steps=sum_over_ranks(e2e_steps), force_ms=force_ms, pass_ms=pass_ms,
+                    pass_kernels=pk)
 
     res = {p: measure(p) for p in ("mixed", "fp64")}
     batched = None if args.no_batch else measure_batched(args, stream, flush, max_over_ranks,
@@ -270,18 +275,24 @@ def run_native(args):
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, unit counts x clock
     fp64_peak = 1.25                                      # TFLOP/s, GB300 nominal FP64 rate
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    pass_bytes = 16.0 * nv  # one pass reads its input and writes its output (N_V doubles each)
+    # one launch reads its input and writes its output (N_V doubles each): a
+    # line pass along one direction, or the tile kernel's whole application
+    pass_bytes = 16.0 * nv
+    pass_kernel = ("cg_pass2d_kernel (CG band preconditioner, both directions on 16x16 node tiles)"
+                   if m["pass_kernels"] == 1 else "cg_pass_kernel (CG band preconditioner line pass)")
     fl = flops_per_element_force(cfg["dim"], cfg["order"], True) * nel
     achieved = fl / (m["force_ms"] * 1e-3) / 1e12
     fl64 = flops_per_element_force(cfg["dim"], cfg["order"], False) * nel
     achieved64 = fl64 / (f["force_ms"] * 1e-3) / 1e12
-    # kernels launched per attempt: per stage force, node gather, dim initial
-    # preconditioner passes, v/x update and energy update, and per CG iteration
-    # the element apply, node gather, update and dim passes; then control and
-    # commit
-    d = cfg["dim"]
+    # kernels launched per attempt: per stage force, node gather, the initial
+    # preconditioner application (pk kernels), v/x update and energy update,
+    # and per CG iteration the element apply, node gather and a preconditioner
+    # application (the CG update rides on it); then control and commit
+    pk = m["pass_kernels"]
     attempts = m["steps"] + m["rejects"]
-    launches = attempts * (2 * (4 + d) + 2) + m["cg"] * (3 + d)
+    # every solve launches at least its kUnrolled = 3 iterations (a converged
+    # solve's later ones return at once)
+    launches = attempts * (2 * (4 + pk) + 2) + max(m["cg"], 3 * 2 * attempts) * (2 + pk)
     line = {
         "metric": "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error",
         "value": value,
@@ -301,7 +312,7 @@ def run_native(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "fp64": {"value": value64, "ms_per_step": f["dev_ms"] / args.steps,
                  "speedup_mixed_over_fp64": value / value64},
-        "roofline": {"bound": "hbm", "kernel": "cg_pass_kernel (CG preconditioner line pass)",
+        "roofline": {"bound": "hbm", "kernel": pass_kernel,
                      "achieved": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9, "peak": hbm_peak,
                      "unit": "GB/s", "frac": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9 / hbm_peak,
                      # DRAM read + write per launch of this kernel from an ncu capture on

@@ -122,6 +122,10 @@ typedef struct lh_phys_desc {
                             (N_V <= 6,000, tensor preconditioner) runs as one launch of a
                             thread-block cluster when the device allows it; 1: whenever it
                             can (any 2D size); -1: never (one kernel per CG phase) */
+  int32_t cg_tiles;      /* 0 (default): in 2D, where the band preconditioner's line passes
+                            would leave SMs idle, both directions run as one kernel over
+                            16 x 16 node tiles (the same FP32 arithmetic, bitwise); -1:
+                            always one line pass per direction */
 } lh_phys_desc;
 
 /* Velocity CG preconditioners.  With rho0 |J0| the same in every element (every
@@ -148,6 +152,7 @@ typedef struct lh_layout_info {
   int32_t nodes_per_dim[3];
   int32_t precision;     /* lh_precision */
   int64_t n_essential;   /* essential (wall-normal) velocity components */
+  int32_t precond_kernels;  /* kernel launches of one lh_precond_apply (0: Jacobi context) */
 } lh_layout_info;
 
 typedef struct lh_run_stats {

@@ -39,6 +39,7 @@ struct CgArgs {
   const double* lchol;
   const double* rhs;
   double *x, *r, *z, *p, *Ap, *ApE;
+  double* r2;            // second residual buffer of the 2D tile kernel
   const double* dinv;
   const double* rho0K;
   double* part;          // partial sums [5][kMaxPartials]
@@ -49,10 +50,11 @@ struct CgArgs {
   int maxit;
   int has_cond;
   cudaGraphConditionalHandle cond;
+  int standalone;        // a preconditioner application outside a solve: never gated
 };
 
 __device__ __forceinline__ bool gated(const CgArgs& a) {
-  return (a.gate != nullptr && a.gate->done) || a.cg->done;
+  return !a.standalone && ((a.gate != nullptr && a.gate->done) || a.cg->done);
 }
 
 // Sum of the per-block partials by the whole (last) block, in a fixed order:
@@ -65,6 +67,16 @@ __device__ __forceinline__ double sum_partials(const double* part) {
   return block_sum(acc, sh);
 }
 
+// The ticket of a finished block: one GPU-scope acquire-release increment.
+// Its release publishes the partials this thread stored before it; for the
+// last block its acquire, carried to the block's other threads by the
+// following barrier, makes every other block's partials visible.
+__device__ __forceinline__ unsigned int take_ticket(unsigned int* ticket) {
+  unsigned int old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(ticket) : "memory");
+  return old;
+}
+
 // Block partial -> the last block to finish adds all partials (sum_partials).
 // Returns true in every thread of the last block; *total is valid in thread 0.
 __device__ __forceinline__ bool reduce_last(double v, double* part, unsigned int* ticket,
@@ -74,13 +86,10 @@ __device__ __forceinline__ bool reduce_last(double v, double* part, unsigned int
   double s = block_sum(v, sh);
   if (threadIdx.x == 0) {
     part[blockIdx.x] = s;
-    __threadfence();
-    unsigned int t = atomicAdd(ticket, 1u);
-    last = (t == gridDim.x - 1);
+    last = (take_ticket(ticket) == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return false;
-  __threadfence();
   const double tot = sum_partials(part);
   if (threadIdx.x == 0) {
     *total = tot;
@@ -90,14 +99,12 @@ __device__ __forceinline__ bool reduce_last(double v, double* part, unsigned int
   return true;
 }
 
-// Block partial only (the caller's last block reads it back).
+// Block partial only (the caller's last block reads it back); thread 0 then
+// takes its ticket in reduce_last, whose release publishes this store too.
 __device__ __forceinline__ void write_partial(double v, double* part) {
   __shared__ double sh[32];
   double s = block_sum(v, sh);
-  if (threadIdx.x == 0) {
-    part[blockIdx.x] = s;
-    __threadfence();
-  }
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
@@ -106,6 +113,24 @@ __device__ __forceinline__ void report(const CgArgs& a, bool conv, double rr) {
   a.ctl->cg_last_relres = cg->bb > 0.0 ? sqrt(rr / cg->bb) : 0.0;
   a.ctl->cg_iters += cg->it;
   if (!conv) atomicOr(&a.ctl->status, kDevCG);
+}
+
+// The end of CG iteration it (thread 0 of the last block of the kernel that
+// completed |r|^2): counts the iteration and applies the convergence test
+// |r| <= rtol |b|, a NaN guard and the iteration cap; a finished solve sets
+// done, reports, and ends the WHILE loop.  Returns true if it finished.
+__device__ __forceinline__ bool end_iteration(const CgArgs& a, double rr) {
+  CgDev* cg = a.cg;
+  cg->it += 1;
+  const bool conv = rr <= a.rtol * a.rtol * cg->bb;
+  const bool bad = !(rr == rr);
+  if (conv || bad || cg->it >= a.maxit) {
+    cg->done = 1;
+    report(a, conv, rr);
+    if (a.has_cond) cudaGraphSetConditional(a.cond, 0);
+    return true;
+  }
+  return false;
 }
 
 // ---------------------------------------------------- tensor line passes --
@@ -141,10 +166,18 @@ __host__ __device__ __forceinline__ int64_t pass_tiles(const Geom& g, int d, int
 // One tile of a band pass along direction d (all threads of the block): the
 // tile's outputs dst = band-inverse(src) and, per mode, r / x / p writes and
 // the partial sums b.b (mode 0) and r.z (last), added to l_bb / l_rz.
+//
+// upd (loop passes of the band preconditioner) fuses the CG update with the
+// passes: 1 = first pass, stages r - alpha Ap instead of r, adds alpha p to x
+// at its outputs and sums |r - alpha Ap|^2 into l_rr; 2 = last pass, stores
+// r - alpha Ap at its outputs and takes r.z with it.  Both sides form the
+// new residual with the same fused multiply-add, so they agree bitwise.
 template <int DIM, int K, typename T = float, int LTV = 32>
 __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int last, int init,
                                           const double* src_in, double* dst, int64_t bid,
-                                          PassTile<K, T, LTV>& sm, double& l_bb, double& l_rz) {
+                                          PassTile<K, T, LTV>& sm, double& l_bb, double& l_rz,
+                                          int upd = 0, double alpha = 0.0,
+                                          double* l_rr = nullptr) {
   using PT = PassTile<K, T, LTV>;
   constexpr int B = PT::B, W = PT::W, TP = PT::TP, ldt = PT::ldt, LT = PT::LT;
   T* tile = sm.tile;
@@ -188,8 +221,10 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     int64_t base;
     bool wall;
     if (pos >= var && pos < nd - var && line_info(l, base, wall) && !wall) {
-      const double v = src[base + pos * stride];
-      val = (T)v * scl;
+      const int64_t k = base + pos * stride;
+      double v = src[k];
+      if (upd == 1) v = fma(-alpha, a.Ap[k], v);
+      val = from_double<T>(v) * scl;  // integer-pipe conversion (FP64 pipe is narrow)
     }
     tile[l * ldt + q] = val;
   }
@@ -221,8 +256,11 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
       const T* tr = tile + l * ldt + q;  // tile position of offset -B
       T acc = T(0);
 #pragma unroll
-      for (int m = 0; m < W; ++m) acc += wr[m] * tr[m];
-      zv = (double)acc;
+      for (int m = 0; m < W; ++m) {
+        if constexpr (sizeof(T) == 4) acc = __fmaf_rn(wr[m], tr[m], acc);
+        else acc = fma(wr[m], tr[m], acc);
+      }
+      zv = to_double(acc);
     }
     if (mode == 0) {
       const bool ess = wall || pos < var || pos >= nd - var;
@@ -231,9 +269,19 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
       a.x[kk] = 0.0;
       l_bb += bv * bv;
     }
+    if (upd == 1) {
+      const double rv = fma(-alpha, a.Ap[kk], a.r[kk]);
+      a.x[kk] = fma(alpha, a.p[kk], a.x[kk]);
+      *l_rr += rv * rv;
+    }
     dst[kk] = zv;
     if (last) {
-      l_rz += a.r[kk] * zv;
+      double rv = a.r[kk];
+      if (upd == 2) {
+        rv = fma(-alpha, a.Ap[kk], rv);
+        a.r[kk] = rv;
+      }
+      l_rz += rv * zv;
       if (init) a.p[kk] = zv;
     }
   }
@@ -251,22 +299,34 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
 // on free components and x = 0, sums b.b), 1 = first pass inside the loop
 // (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
 // last: the pass along the last direction (sums r.z; init also writes p = z).
+// upd: the CG update fused into the loop passes (see pass_tile); the first
+// pass ends the iteration with the convergence test on |r|^2.
 template <int DIM, int K, typename T, int LTV>
 __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, int d, int mode,
-                                                              int last, int init,
+                                                              int last, int init, int upd,
                                                               const double* src_in,
                                                               double* dst) {
   pdl_enter();
-  if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) return;
+  if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) {
+    if (upd == 1 && a.has_cond && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional(a.cond, 0);
+    return;
+  }
   if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
     a.cg->done = 0;
     a.cg->it = 0;
   }
   __shared__ PassTile<K, T, LTV> sm;
-  double l_bb = 0.0, l_rz = 0.0;
+  double l_bb = 0.0, l_rz = 0.0, l_rr = 0.0;
+  const double alpha = upd != 0 ? a.cg->alpha : 0.0;
   pass_tile<DIM, K, T, LTV>(a, d, mode, last, init, src_in, dst, (int64_t)blockIdx.x, sm, l_bb,
-                            l_rz);
+                            l_rz, upd, alpha, &l_rr);
   double tot;
+  if (upd == 1) {
+    if (reduce_last(l_rr, a.part + 4 * kMaxPartials, &a.cg->ticket[kTicketB], &tot) &&
+        threadIdx.x == 0)
+      end_iteration(a, tot);
+  }
   if (mode == 0) {
     if (reduce_last(l_bb, a.part, &a.cg->ticket[kTicketPass0], &tot) && threadIdx.x == 0)
       a.cg->bb = tot;
@@ -287,6 +347,194 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
         cg->beta = tot / cg->rz;
         cg->rz = tot;
       }
+    }
+  }
+}
+
+// ------------------------------------------------ 2D fused band passes ----
+
+// Both directions of the 2D band preconditioner in one kernel, for meshes
+// whose line passes would leave SMs idle.  A CTA owns a 16 x 16 tile of the
+// nodes of one component.  It stages the input over the tile and a +-B window
+// in both directions, applies the x band to every window row at the tile's 16
+// columns, then the y band to that.  Each output is the same FP32 sum of the
+// same products, in the same order, as the x pass followed by the y pass, so
+// the result is bitwise that of the two line passes (which round the x result
+// to FP64 and back, exactly).
+//
+// mode / init / upd as for cg_pass_kernel, with both passes in this one
+// (first and last): mode 0 initial (b.b and r.z), upd 1 the CG update fused
+// (r.z and |r|^2, then the convergence test), otherwise a plain application
+// (r.z).  With the update fused, a CTA stages r - alpha Ap over its halo while
+// other CTAs form the new residual of their own nodes, so the residual
+// alternates between two buffers by iteration parity: iteration it (counted
+// from 0) reads r[it & 1] and writes r[(it + 1) & 1]; the initial application
+// writes r[0].
+template <int K>
+struct Pass2DTile {
+  static constexpr int B = PB<K>::B, W = 2 * B + 1, TS = 16, WN = TS + 2 * B;
+  static constexpr int ldw = ((WN + 15) / 32) * 32 + 16;  // row stride = 16 (mod 32) banks
+  float win[WN * ldw];   // input window [y][x], positions y0 - B.., x0 - B..
+  float tx[WN * TS];     // x-band result on the window rows at the tile columns
+  float wxT[W * TS];     // x band rows of the tile columns, [m][column]
+  float wy[TS * W];      // y band rows of the tile rows, [row][m]
+};
+
+template <int K>
+__global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a, int mode,
+                                                                int init, int upd,
+                                                                double* dst) {
+  using PT = Pass2DTile<K>;
+  constexpr int B = PT::B, W = PT::W, TS = PT::TS, WN = PT::WN, ldw = PT::ldw;
+  constexpr int NT = kLineThreads;
+  static_assert(TS * TS == NT, "one tile output per thread");
+  pdl_enter();
+  if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) {
+    if (upd == 1 && a.has_cond && blockIdx.x == 0 && threadIdx.x == 0)
+      cudaGraphSetConditional(a.cond, 0);
+    return;
+  }
+  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) {  // a new solve
+    a.cg->done = 0;
+    a.cg->it = 0;
+  }
+  __shared__ PT sm;
+  const Geom& g = a.g;
+  const int n0 = g.nn[0], n1 = g.nn[1];
+  const int tx0 = (n0 + TS - 1) / TS, ty0 = (n1 + TS - 1) / TS;
+  const int tile = (int)(blockIdx.x % (unsigned)(tx0 * ty0));
+  const int c = (int)(blockIdx.x / (unsigned)(tx0 * ty0));
+  const int x0 = (tile % tx0) * TS, y0 = (tile / tx0) * TS;
+  const int tid = threadIdx.x;
+  const int64_t cbase = (int64_t)c * g.nnodes;
+  // free nodes of component c: the end nodes along direction c are essential
+  auto is_free = [&](int x, int y) -> bool {
+    if (x < 0 || x >= n0 || y < 0 || y >= n1) return false;
+    return c == 0 ? (x > 0 && x < n0 - 1) : (y > 0 && y < n1 - 1);
+  };
+  const int it0 = upd == 1 ? a.cg->it : 0;  // iterations completed before this one
+  const double* rin = upd == 1 ? ((it0 & 1) ? a.r2 : a.r) : a.r;
+  double* rout = (upd == 1 && !(it0 & 1)) ? a.r2 : a.r;
+  const double* src = mode == 0 ? a.rhs : rin;
+  const float scl = (float)a.tpc.scale;
+  const double alpha = upd != 0 ? a.cg->alpha : 0.0;
+  // this thread's output node; its operands are loaded now, under the staging
+  const int yl = tid / TS, q = tid - yl * TS;
+  const int xo = x0 + q, yo = y0 + yl;
+  const bool own = xo < n0 && yo < n1;
+  const bool fr = is_free(xo, yo);
+  const int64_t kk = cbase + (int64_t)(own ? yo : 0) * n0 + (own ? xo : 0);
+  double o_r = 0.0, o_ap = 0.0, o_p = 0.0, o_x = 0.0;
+  if (own) {
+    if (mode == 0) {
+      o_r = fr ? a.rhs[kk] : 0.0;
+    } else {
+      o_r = rin[kk];
+      if (upd == 1) {
+        o_ap = a.Ap[kk];
+        o_p = a.p[kk];
+        o_x = a.x[kk];
+      }
+    }
+  }
+#pragma unroll 8
+  for (int idx = tid; idx < WN * WN; idx += NT) {
+    const int wyi = idx / WN, wxi = idx - wyi * WN;
+    const int x = x0 - B + wxi, y = y0 - B + wyi;
+    float val = 0.0f;
+    if (is_free(x, y)) {
+      const int64_t k = cbase + (int64_t)y * n0 + x;
+      double v = src[k];
+      if (upd == 1) v = fma(-alpha, a.Ap[k], v);
+      val = d2f_rn(v) * scl;  // integer-pipe conversion (FP64 pipe is narrow)
+    }
+    sm.win[wyi * ldw + wxi] = val;
+  }
+  // band rows: direction d's rows exclude the end nodes when d == c
+  {
+    const int vx = (c == 0) ? 1 : 0, vy = (c == 1) ? 1 : 0;
+    const float* fx = a.lfac + a.tpc.off[0][vx];
+    const float* fy = a.lfac + a.tpc.off[1][vy];
+#pragma unroll 4
+    for (int idx = tid; idx < TS * W; idx += NT) {
+      const int qq = idx / W, m = idx - qq * W;
+      const int rx = x0 + qq - vx, ry = y0 + qq - vy;
+      sm.wxT[m * TS + qq] = (rx >= 0 && rx < n0 - 2 * vx) ? fx[(int64_t)rx * W + m] : 0.0f;
+      sm.wy[idx] = (ry >= 0 && ry < n1 - 2 * vy) ? fy[(int64_t)ry * W + m] : 0.0f;
+    }
+  }
+  __syncthreads();
+  // x band on the window rows, tile columns (zero off the free set)
+  for (int o = tid; o < WN * TS; o += NT) {
+    const int wyi = o / TS, qq = o - wyi * TS;
+    float acc = 0.0f;
+    if (is_free(x0 + qq, y0 - B + wyi)) {
+      const float* wr = sm.win + wyi * ldw + qq;
+#pragma unroll
+      for (int m = 0; m < W; ++m) acc = __fmaf_rn(sm.wxT[m * TS + qq], wr[m], acc);
+    }
+    sm.tx[o] = acc;
+  }
+  __syncthreads();
+  double l_bb = 0.0, l_rz = 0.0, l_rr = 0.0;
+  if (own) {
+    double zv = 0.0;
+    if (fr) {
+      const float* tr = sm.tx + yl * TS + q;  // window row y - B
+      const float* wr = sm.wy + yl * W;
+      float acc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < W; ++m) acc = __fmaf_rn(wr[m], tr[m * TS], acc);
+      zv = f2d_exact(acc);
+    }
+    double rv = o_r;
+    if (mode == 0) {
+      a.x[kk] = 0.0;
+      l_bb += rv * rv;
+      rout[kk] = rv;
+    } else if (upd == 1) {
+      rv = fma(-alpha, o_ap, o_r);
+      a.x[kk] = fma(alpha, o_p, o_x);
+      l_rr += rv * rv;
+      rout[kk] = rv;
+    }
+    dst[kk] = zv;
+    l_rz += rv * zv;
+    if (init) a.p[kk] = zv;
+  }
+  double tot;
+  if (mode == 0) {
+    write_partial(l_bb, a.part);
+    if (reduce_last(l_rz, a.part + kMaxPartials, &a.cg->ticket[kTicketPassL], &tot)) {
+      const double bb = sum_partials(a.part);
+      if (threadIdx.x != 0) return;
+      CgDev* cg = a.cg;
+      cg->bb = bb;
+      cg->rz = tot;
+      cg->it = 0;
+      cg->beta = 0.0;
+      if (!(bb > 0.0)) {  // zero right-hand side: x = 0 is the solution
+        cg->done = 1;
+        report(a, true, 0.0);
+      }
+    }
+  } else if (upd == 1) {
+    // every block writes its r.z partial before it takes its |r|^2 ticket
+    write_partial(l_rz, a.part + 3 * kMaxPartials);
+    if (reduce_last(l_rr, a.part + 4 * kMaxPartials, &a.cg->ticket[kTicketB], &tot)) {
+      const double rz_new = sum_partials(a.part + 3 * kMaxPartials);
+      if (threadIdx.x != 0) return;
+      CgDev* cg = a.cg;
+      if (!end_iteration(a, tot)) {
+        cg->beta = rz_new / cg->rz;
+        cg->rz = rz_new;
+      }
+    }
+  } else {
+    if (reduce_last(l_rz, a.part + kMaxPartials, &a.cg->ticket[kTicketPassL], &tot) &&
+        threadIdx.x == 0) {
+      a.cg->beta = tot / a.cg->rz;
+      a.cg->rz = tot;
     }
   }
 }
@@ -692,14 +940,7 @@ __global__ void __launch_bounds__(kNodeThreads) cg_update_kernel(const CgArgs a,
     const double rz_new = jacobi ? sum_partials(a.part + 3 * kMaxPartials) : 0.0;
     if (threadIdx.x != 0) return;
     CgDev* cg = a.cg;
-    cg->it += 1;
-    const bool conv = rr <= a.rtol * a.rtol * cg->bb;
-    const bool bad = !(rr == rr);
-    if (conv || bad || cg->it >= a.maxit) {
-      cg->done = 1;
-      report(a, conv, rr);
-      if (a.has_cond) cudaGraphSetConditional(a.cond, 0);
-    } else if (jacobi) {
+    if (!end_iteration(a, rr) && jacobi) {
       cg->beta = rz_new / cg->rz;
       cg->rz = rz_new;
     }
@@ -735,6 +976,7 @@ static CgArgs make_args(const lh_ctx* c, const double* rhs, double* out, const C
   a.rhs = rhs;
   a.x = out;
   a.r = c->a.r;
+  a.r2 = c->a.r2;
   a.z = c->a.z;
   a.p = c->a.p;
   a.Ap = c->a.Ap;
@@ -749,6 +991,7 @@ static CgArgs make_args(const lh_ctx* c, const double* rhs, double* out, const C
   a.maxit = c->cg_maxit;
   a.has_cond = 0;
   a.cond = 0;
+  a.standalone = 0;
   return a;
 }
 
@@ -756,12 +999,34 @@ static size_t line_smem(const lh_ctx* c, int d) {
   return (size_t)kLineGroup * (c->g.nn[d] | 1) * sizeof(double);
 }
 
+// Tiles of 32 node lines where they fill the GPU several times over, else of
+// 8 (more CTAs for small meshes; the halo runs along the lines, so shorter
+// tiles across the lines cost no extra halo).
+template <int DIM>
+static bool narrow_passes(const lh_ctx* c) {
+  return pass_tiles<DIM>(c->g, 0, 32) < 4 * (int64_t)c->num_sms;
+}
+
+// Whether the CG update rides on the band passes: where the passes are
+// narrow the solve is a chain of latency-bound kernels and one launch fewer
+// per iteration pays; on large meshes the separate streaming update is cheaper
+// than re-reading Ap with the passes' halos.
+template <int DIM>
+static bool fuse_update(const lh_ctx* c) {
+  return narrow_passes<DIM>(c);
+}
+
+// fuse: loop passes of the band preconditioner with the CG update folded in
+// (pass_tile's upd); Ap is then still needed by the last pass, so the
+// intermediate direction results go to ApE (free after the node gather, and
+// at least as long as a velocity vector).
 template <int DIM, int K>
-static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, cudaStream_t s) {
+static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, cudaStream_t s,
+                                  bool fuse = false) {
   // out of place: r -> z (d = 0), then alternate between Ap (free here) and z
   // so that the last direction writes z
   const double* src = a.r;
-  double* bufs[2] = {a.z, a.Ap};
+  double* bufs[2] = {a.z, fuse ? a.ApE : a.Ap};
   if (c->tpc.exact) {
     for (int d = 0; d < DIM; ++d) {
       const int64_t nlines = c->g.nnodes / c->g.nn[d];
@@ -776,28 +1041,33 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
     }
     return cudaGetLastError();
   }
-  // tiles of 32 node lines where they fill the GPU several times over, else
-  // of 8 (more CTAs for small meshes; the halo runs along the lines, so
-  // shorter tiles across the lines cost no extra halo)
-  const bool narrow = pass_tiles<DIM>(c->g, 0, 32) < 4 * (int64_t)c->num_sms;
+  const bool narrow = narrow_passes<DIM>(c);
+  if (DIM == 2 && narrow && !c->tpc.fp64 && c->cg_tiles) {  // both directions in one kernel
+    const int64_t blocks = 2 * (int64_t)((c->g.nn[0] + 15) / 16) * ((c->g.nn[1] + 15) / 16);
+    cudaError_t e = launch_k(c->use_pdl != 0, cg_pass2d_kernel<K>, dim3((unsigned)blocks),
+                             dim3(kLineThreads), 0, s, a, init ? 0 : 1, init ? 1 : 0,
+                             fuse ? 1 : 0, a.z);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   for (int d = 0; d < DIM; ++d) {
     const int64_t blocks = pass_tiles<DIM>(c->g, d, narrow ? 8 : 32);
     const int mode = d == 0 ? (init ? 0 : 1) : 2;
     double* dst = bufs[(DIM - 1 - d) & 1];
     const bool pdl = c->use_pdl != 0;
     const int last = (int)(d == DIM - 1), ini = init ? 1 : 0;
+    const int upd = !fuse ? 0 : (d == 0 ? 1 : (last ? 2 : 0));
     const dim3 gr((unsigned)blocks), bl(kLineThreads);
     cudaError_t e;
     if (c->tpc.fp64)
       e = narrow ? launch_k(pdl, cg_pass_kernel<DIM, K, double, 8>, gr, bl, 0, s, a, d, mode, last,
-                            ini, src, dst)
+                            ini, upd, src, dst)
                  : launch_k(pdl, cg_pass_kernel<DIM, K, double, 32>, gr, bl, 0, s, a, d, mode,
-                            last, ini, src, dst);
+                            last, ini, upd, src, dst);
     else
       e = narrow ? launch_k(pdl, cg_pass_kernel<DIM, K, float, 8>, gr, bl, 0, s, a, d, mode, last,
-                            ini, src, dst)
+                            ini, upd, src, dst)
                  : launch_k(pdl, cg_pass_kernel<DIM, K, float, 32>, gr, bl, 0, s, a, d, mode, last,
-                            ini, src, dst);
+                            ini, upd, src, dst);
     if (e != cudaSuccess) return e;
     src = dst;
   }
@@ -822,9 +1092,11 @@ static cudaError_t cg_body_dk(const lh_ctx* c, const CgArgs& a, cudaStream_t s) 
   cudaError_t e = launch_k(pdl, cg_elem_kernel<DIM, K>, dim3(eblocks), dim3(256), 0, s, a);
   if (e == cudaSuccess)
     e = launch_k(pdl, cg_gather_kernel<DIM, K>, dim3(node_grid(c)), dim3(kNodeThreads), 0, s, a);
-  if (e == cudaSuccess)
-    e = launch_k(pdl, cg_update_kernel<DIM, K>, dim3(node_grid(c)), dim3(kNodeThreads), 0, s, a,
-                 c->tpc.enabled ? 0 : 1);
+  if (e != cudaSuccess) return e;
+  if (c->tpc.enabled && !c->tpc.exact && fuse_update<DIM>(c))
+    return precond_passes<DIM, K>(c, a, false, s, true);
+  e = launch_k(pdl, cg_update_kernel<DIM, K>, dim3(node_grid(c)), dim3(kNodeThreads), 0, s, a,
+               c->tpc.enabled ? 0 : 1);
   if (e != cudaSuccess) return e;
   if (c->tpc.enabled) {
     if ((e = precond_passes<DIM, K>(c, a, false, s)) != cudaSuccess) return e;
@@ -871,13 +1143,19 @@ static cudaError_t precond_apply_dk(const lh_ctx* c, const double* in, double* o
   CgArgs a = make_args(c, nullptr, nullptr, nullptr);
   a.r = const_cast<double*>(in);
   a.z = out;
-  cudaError_t e = cudaMemsetAsync(&c->a.cg->done, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
+  a.standalone = 1;
   return precond_passes<DIM, K>(c, a, false, s);
 }
 
 cudaError_t precond_apply(const lh_ctx* c, const double* in, double* out, cudaStream_t s) {
   LAGH_DISPATCH_CG(precond_apply_dk, c, in, out, s);
+}
+
+int precond_kernels(const lh_ctx* c) {
+  if (!c->tpc.enabled) return 0;
+  const int d = c->g.dim;
+  const bool narrow = d == 2 ? narrow_passes<2>(c) : narrow_passes<3>(c);
+  return (d == 2 && narrow && !c->tpc.fp64 && !c->tpc.exact && c->cg_tiles) ? 1 : d;
 }
 
 // The cluster-resident solve: one launch of a cluster of c->cg_cluster CTAs.

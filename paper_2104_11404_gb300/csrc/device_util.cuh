@@ -128,9 +128,9 @@ __device__ __forceinline__ double f2d_exact(float f) {
   return __longlong_as_double((long long)bits);
 }
 
-// FP64 -> FP32 rounded to nearest, ties to even (as a C cast), for results in
-// the normal FP32 range; results below it flush to a signed zero, above it
-// round to infinity, NaN stays NaN.
+// FP64 -> FP32 rounded to nearest, ties to even (as a C cast), with integer
+// operations only: results in the FP32 subnormal range are rounded to its
+// 2^-149 grid, results above the range round to infinity, NaN stays NaN.
 __device__ __forceinline__ float d2f_rn(double d) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(d);
   const unsigned s = (unsigned)(b >> 32) & 0x80000000u;
@@ -138,7 +138,15 @@ __device__ __forceinline__ float d2f_rn(double d) {
   const unsigned long long m = b & 0xfffffffffffffull;
   if (ex == 0x7ff) return __uint_as_float(s | 0x7f800000u | (m ? 0x400000u : 0u));
   int fe = ex - 896;  // FP32 biased exponent
-  if (fe <= 0) return __uint_as_float(s);
+  if (fe <= 0) {  // subnormal result: the 53-bit significand in units of 2^-149
+    const int sh = 30 - fe;
+    if (ex == 0 || sh > 54) return __uint_as_float(s);  // below half of 2^-149
+    const unsigned long long M = m | (1ull << 52);
+    unsigned r = (unsigned)(M >> sh);
+    const unsigned long long rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (r & 1u))) ++r;  // may carry into 2^-126
+    return __uint_as_float(s | r);
+  }
   unsigned r = (unsigned)(m >> 29);
   const unsigned rem = (unsigned)(m & 0x1fffffffull);
   if (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) {

@@ -122,6 +122,7 @@ struct Arrays {
   double *F1E;                  // element-local F.1 [nelem][dim][nd1]
   double *rhs, *acc;            // CG right-hand side and solution
   double *r, *z, *p, *Ap;       // CG vectors
+  double *r2;                   // the residual's second buffer (2D tile preconditioner)
   double *ApE;                  // element-local M p [nelem][dim][nd1]
   double *D;                    // FP64 path: stress weights [nelem][dim*dim][nqe]
   float *FK;                    // mixed path: element force matrices [nelem][dim*nd1][nd2]
@@ -162,6 +163,7 @@ struct lh_ctx {
   int graph_ready;            // 1: graph built, -1: capture unsupported (eager launches)
   int use_pdl;                // programmatic dependent launch between the step's kernels
   int cg_cluster;             // CTAs of the cluster-resident CG (0: kernel chain)
+  int cg_tiles;               // 1: 2D band passes as one 16 x 16 tile kernel where narrow
   cudaEvent_t ev0, ev1;
   std::string err;
 };
@@ -266,5 +268,6 @@ cudaError_t prepare_kernels(const lh_ctx* c);
 cudaError_t cg_prepare(const lh_ctx* c);
 // Cluster size the cluster-resident CG can use on this device (16 or 8), 0 if none.
 int cg_cluster_choose(const lh_ctx* c);
+int precond_kernels(const lh_ctx* c);  // launches of one preconditioner application
 
 }  // namespace lagh

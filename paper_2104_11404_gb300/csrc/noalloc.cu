@@ -57,6 +57,7 @@ extern "C" lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_des
   memset(&c.a, 0, sizeof(c.a));
   c.use_pdl = 0;
   c.cg_cluster = 0;
+  c.cg_tiles = 0;
   {
     lh_status gs = make_geom(mesh, disc, &c.g, nullptr);
     if (gs != LH_OK) return gs;

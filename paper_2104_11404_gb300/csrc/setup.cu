@@ -308,7 +308,8 @@ extern "C" const char* lh_last_error(const lh_ctx* c) { return c ? c->err.c_str(
 static void free_all(lh_ctx* c) {
   double** dptrs[] = {&c->a.v, &c->a.e, &c->a.x, &c->a.vh, &c->a.eh, &c->a.xh, &c->a.vn,
                       &c->a.en, &c->a.xn, &c->a.vbar, &c->a.F1E, &c->a.rhs, &c->a.acc,
-                      &c->a.r, &c->a.z, &c->a.p, &c->a.Ap, &c->a.ApE, &c->a.D, &c->a.srcE,
+                      &c->a.r, &c->a.r2, &c->a.z, &c->a.p, &c->a.Ap, &c->a.ApE, &c->a.D,
+                      &c->a.srcE,
                       &c->a.rho0K, &c->a.rho0Kinv, &c->a.dinv, &c->a.partials, &c->a.tmpE, &c->a.tmpV,
                       &c->a.aux};
   for (double** p : dptrs)
@@ -409,7 +410,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   const size_t nv = g.nv, ne = g.ne, nelem = g.nelem;
   cudaError_t e = cudaSuccess;
   double** vecs_v[] = {&A.v, &A.x, &A.vh, &A.xh, &A.vn, &A.xn, &A.vbar, &A.rhs, &A.acc,
-                       &A.r, &A.z, &A.p, &A.Ap, &A.tmpV};
+                       &A.r, &A.r2, &A.z, &A.p, &A.Ap, &A.tmpV};
   for (double** p : vecs_v)
     if (e == cudaSuccess) e = dalloc(p, nv);
   double** vecs_e[] = {&A.e, &A.eh, &A.en, &A.srcE, &A.tmpE};
@@ -550,6 +551,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   if (phys->cg_cluster >= 0 && d == 2 && c->tpc.enabled && !c->tpc.exact && !c->tpc.fp64 &&
       (phys->cg_cluster == 1 || g.nv <= 6000))
     c->cg_cluster = cg_cluster_choose(c);
+  c->cg_tiles = phys->cg_tiles >= 0 ? 1 : 0;
   Ctl ctl0;
   memset(&ctl0, 0, sizeof(ctl0));
   e = cudaMemcpy(A.rho0K, rho0K.data(), nelem * sizeof(double), cudaMemcpyHostToDevice);
@@ -594,6 +596,7 @@ extern "C" lh_status lh_layout(const lh_ctx* c, lh_layout_info* info) {
     ness += 2 * other;
   }
   info->n_essential = ness;
+  info->precond_kernels = precond_kernels(c);
   return LH_OK;
 }
 

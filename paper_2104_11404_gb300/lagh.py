@@ -50,7 +50,7 @@ class lh_phys_desc(ctypes.Structure):
                 ("gamma_dt", ctypes.c_double), ("q1", ctypes.c_double), ("q2", ctypes.c_double),
                 ("cg_rtol", ctypes.c_double), ("dt_min_frac", ctypes.c_double),
                 ("cg_precond", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
-                ("cg_cluster", ctypes.c_int32)]
+                ("cg_cluster", ctypes.c_int32), ("cg_tiles", ctypes.c_int32)]
 
 
 class lh_layout_info(ctypes.Structure):
@@ -59,7 +59,7 @@ class lh_layout_info(ctypes.Structure):
                 ("dim", ctypes.c_int32), ("order", ctypes.c_int32), ("nq", ctypes.c_int32),
                 ("ndof_h1", ctypes.c_int32), ("ndof_l2", ctypes.c_int32), ("nqe", ctypes.c_int32),
                 ("nodes_per_dim", ctypes.c_int32 * 3), ("precision", ctypes.c_int32),
-                ("n_essential", ctypes.c_int64)]
+                ("n_essential", ctypes.c_int64), ("precond_kernels", ctypes.c_int32)]
 
 
 class lh_run_stats(ctypes.Structure):

@@ -8,7 +8,9 @@ that contain conditional nodes, which is how the library normally runs).
 --batch runs the 512-instance point-blast sweep through the batched form
 instead (its attempt graph holds kernel nodes only, so profilers see them);
 --tuning threads,ctas_per_sm,smem_lines fixes the launch shape (no autotuner
-launches before the profiled ones).
+launches before the profiled ones).  --apply N instead applies the CG
+preconditioner N times to a random vector (the plain band passes, as bench.py
+times them for its roofline line).
 """
 import argparse
 import json
@@ -28,6 +30,8 @@ def main():
     ap.add_argument("--tuning", default="", help="threads,ctas_per_sm,smem_lines")
     ap.add_argument("--precond", type=int, default=-1,
                     help="cg_precond (0 Jacobi, 1 tensor bands, 2 exact); default: the library's")
+    ap.add_argument("--apply", type=int, default=0,
+                    help="apply the CG preconditioner this many times instead of stepping")
     args = ap.parse_args()
     if args.batch:
         return run_batch(args)
@@ -44,6 +48,19 @@ def main():
         over["cg_precond"] = args.precond
     g = Hydro(cfg, precision=args.precision, phys_overrides=over or None)
     g.init_state()
+    if args.apply:
+        from . import lagh
+        nv = g.get_state()[0].numel()
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        r = torch.randn(nv, dtype=torch.float64, device="cuda", generator=gen)
+        z = torch.empty_like(r)
+        for _ in range(args.apply):
+            lagh.lh_precond_apply(g.ctx, r, z)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": args.workload, "applied": args.apply,
+                          "z_norm": float(z.norm())}))
+        g.close()
+        return 0
     if args.warmup:
         g.run_to(cfg["t_final"], max_steps=args.warmup)
     st = g.run_to(cfg["t_final"], max_steps=args.steps)
