@@ -224,7 +224,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
       const int64_t k = base + pos * stride;
       double v = src[k];
       if (upd == 1) v = fma(-alpha, a.Ap[k], v);
-      val = from_double<T>(v) * scl;  // integer-pipe conversion (FP64 pipe is narrow)
+      val = (T)v * scl;
     }
     tile[l * ldt + q] = val;
   }
@@ -260,7 +260,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
         if constexpr (sizeof(T) == 4) acc = __fmaf_rn(wr[m], tr[m], acc);
         else acc = fma(wr[m], tr[m], acc);
       }
-      zv = to_double(acc);
+      zv = (double)acc;
     }
     if (mode == 0) {
       const bool ess = wall || pos < var || pos >= nd - var;
@@ -354,13 +354,15 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
 // ------------------------------------------------ 2D fused band passes ----
 
 // Both directions of the 2D band preconditioner in one kernel, for meshes
-// whose line passes would leave SMs idle.  A CTA owns a 16 x 16 tile of the
-// nodes of one component.  It stages the input over the tile and a +-B window
-// in both directions, applies the x band to every window row at the tile's 16
-// columns, then the y band to that.  Each output is the same FP32 sum of the
-// same products, in the same order, as the x pass followed by the y pass, so
-// the result is bitwise that of the two line passes (which round the x result
-// to FP64 and back, exactly).
+// whose line passes would leave SMs idle.  A CTA owns a tile of the nodes of
+// one component: 16 x 16, where a last tile along a direction takes the
+// remaining node lines (1 to 16; a single remaining line, as for any mesh of
+// 16m elements per direction, joins the tile before it, 17 wide).  It stages
+// the input over the tile and a +-B window in both directions, applies the x
+// band to every window row at the tile's columns, then the y band to that.
+// Each output is the same FP32 sum of the same products, in the same order,
+// as the x pass followed by the y pass, so the result is bitwise that of the
+// two line passes (which round the x result to FP64 and back, exactly).
 //
 // mode / init / upd as for cg_pass_kernel, with both passes in this one
 // (first and last): mode 0 initial (b.b and r.z), upd 1 the CG update fused
@@ -372,22 +374,27 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, i
 // writes r[0].
 template <int K>
 struct Pass2DTile {
-  static constexpr int B = PB<K>::B, W = 2 * B + 1, TS = 16, WN = TS + 2 * B;
+  static constexpr int B = PB<K>::B, W = 2 * B + 1, TS = 16, TM = TS + 1, WN = TM + 2 * B;
   static constexpr int ldw = ((WN + 15) / 32) * 32 + 16;  // row stride = 16 (mod 32) banks
   float win[WN * ldw];   // input window [y][x], positions y0 - B.., x0 - B..
-  float tx[WN * TS];     // x-band result on the window rows at the tile columns
-  float wxT[W * TS];     // x band rows of the tile columns, [m][column]
-  float wy[TS * W];      // y band rows of the tile rows, [row][m]
+  float tx[WN * TM];     // x-band result on the window rows at the tile columns
+  float wxT[W * TM];     // x band rows of the tile columns, [m][column]
+  float wy[TM * W];      // y band rows of the tile rows, [row][m]
 };
+
+// Tiles along a line of n nodes: 16 wide, the last one ragged or 17 wide.
+__host__ __device__ __forceinline__ int pass2d_tiles(int n) {
+  const int t = (n + 15) / 16;
+  return (n % 16 == 1 && t > 1) ? t - 1 : t;
+}
 
 template <int K>
 __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a, int mode,
                                                                 int init, int upd,
                                                                 double* dst) {
   using PT = Pass2DTile<K>;
-  constexpr int B = PT::B, W = PT::W, TS = PT::TS, WN = PT::WN, ldw = PT::ldw;
+  constexpr int B = PT::B, W = PT::W, TS = PT::TS, TM = PT::TM, WN = PT::WN, ldw = PT::ldw;
   constexpr int NT = kLineThreads;
-  static_assert(TS * TS == NT, "one tile output per thread");
   pdl_enter();
   if (init ? (a.gate != nullptr && a.gate->done) : gated(a)) {
     if (upd == 1 && a.has_cond && blockIdx.x == 0 && threadIdx.x == 0)
@@ -401,10 +408,13 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
   __shared__ PT sm;
   const Geom& g = a.g;
   const int n0 = g.nn[0], n1 = g.nn[1];
-  const int tx0 = (n0 + TS - 1) / TS, ty0 = (n1 + TS - 1) / TS;
-  const int tile = (int)(blockIdx.x % (unsigned)(tx0 * ty0));
-  const int c = (int)(blockIdx.x / (unsigned)(tx0 * ty0));
-  const int x0 = (tile % tx0) * TS, y0 = (tile / tx0) * TS;
+  const int ntx = pass2d_tiles(n0), nty = pass2d_tiles(n1);
+  const int tile = (int)(blockIdx.x % (unsigned)(ntx * nty));
+  const int c = (int)(blockIdx.x / (unsigned)(ntx * nty));
+  const int tix = tile % ntx, tiy = tile / ntx;
+  const int x0 = tix * TS, y0 = tiy * TS;
+  const int wx = tix == ntx - 1 ? n0 - x0 : TS, wy = tiy == nty - 1 ? n1 - y0 : TS;  // <= TM
+  const int wnx = wx + 2 * B, wny = wy + 2 * B;  // window extent, <= WN
   const int tid = threadIdx.x;
   const int64_t cbase = (int64_t)c * g.nnodes;
   // free nodes of component c: the end nodes along direction c are essential
@@ -418,35 +428,16 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
   const double* src = mode == 0 ? a.rhs : rin;
   const float scl = (float)a.tpc.scale;
   const double alpha = upd != 0 ? a.cg->alpha : 0.0;
-  // this thread's output node; its operands are loaded now, under the staging
-  const int yl = tid / TS, q = tid - yl * TS;
-  const int xo = x0 + q, yo = y0 + yl;
-  const bool own = xo < n0 && yo < n1;
-  const bool fr = is_free(xo, yo);
-  const int64_t kk = cbase + (int64_t)(own ? yo : 0) * n0 + (own ? xo : 0);
-  double o_r = 0.0, o_ap = 0.0, o_p = 0.0, o_x = 0.0;
-  if (own) {
-    if (mode == 0) {
-      o_r = fr ? a.rhs[kk] : 0.0;
-    } else {
-      o_r = rin[kk];
-      if (upd == 1) {
-        o_ap = a.Ap[kk];
-        o_p = a.p[kk];
-        o_x = a.x[kk];
-      }
-    }
-  }
 #pragma unroll 8
   for (int idx = tid; idx < WN * WN; idx += NT) {
     const int wyi = idx / WN, wxi = idx - wyi * WN;
     const int x = x0 - B + wxi, y = y0 - B + wyi;
     float val = 0.0f;
-    if (is_free(x, y)) {
+    if (wxi < wnx && wyi < wny && is_free(x, y)) {
       const int64_t k = cbase + (int64_t)y * n0 + x;
       double v = src[k];
       if (upd == 1) v = fma(-alpha, a.Ap[k], v);
-      val = d2f_rn(v) * scl;  // integer-pipe conversion (FP64 pipe is narrow)
+      val = (float)v * scl;  // the cast measured faster here than the integer-pipe form
     }
     sm.win[wyi * ldw + wxi] = val;
   }
@@ -455,48 +446,56 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
     const int vx = (c == 0) ? 1 : 0, vy = (c == 1) ? 1 : 0;
     const float* fx = a.lfac + a.tpc.off[0][vx];
     const float* fy = a.lfac + a.tpc.off[1][vy];
-#pragma unroll 4
-    for (int idx = tid; idx < TS * W; idx += NT) {
+    for (int idx = tid; idx < TM * W; idx += NT) {
       const int qq = idx / W, m = idx - qq * W;
       const int rx = x0 + qq - vx, ry = y0 + qq - vy;
-      sm.wxT[m * TS + qq] = (rx >= 0 && rx < n0 - 2 * vx) ? fx[(int64_t)rx * W + m] : 0.0f;
-      sm.wy[idx] = (ry >= 0 && ry < n1 - 2 * vy) ? fy[(int64_t)ry * W + m] : 0.0f;
+      sm.wxT[m * TM + qq] =
+          (qq < wx && rx >= 0 && rx < n0 - 2 * vx) ? fx[(int64_t)rx * W + m] : 0.0f;
+      sm.wy[idx] = (qq < wy && ry >= 0 && ry < n1 - 2 * vy) ? fy[(int64_t)ry * W + m] : 0.0f;
     }
   }
   __syncthreads();
   // x band on the window rows, tile columns (zero off the free set)
-  for (int o = tid; o < WN * TS; o += NT) {
-    const int wyi = o / TS, qq = o - wyi * TS;
+  for (int o = tid; o < WN * TM; o += NT) {
+    const int wyi = o / TM, qq = o - wyi * TM;
     float acc = 0.0f;
-    if (is_free(x0 + qq, y0 - B + wyi)) {
+    if (qq < wx && wyi < wny && is_free(x0 + qq, y0 - B + wyi)) {
       const float* wr = sm.win + wyi * ldw + qq;
 #pragma unroll
-      for (int m = 0; m < W; ++m) acc = __fmaf_rn(sm.wxT[m * TS + qq], wr[m], acc);
+      for (int m = 0; m < W; ++m) acc = __fmaf_rn(sm.wxT[m * TM + qq], wr[m], acc);
     }
     sm.tx[o] = acc;
   }
   __syncthreads();
   double l_bb = 0.0, l_rz = 0.0, l_rr = 0.0;
-  if (own) {
+  for (int o = tid; o < TM * TM; o += NT) {
+    const int yl = o / TM, q = o - yl * TM;
+    if (q >= wx || yl >= wy) continue;
+    const int x = x0 + q, y = y0 + yl;
+    const int64_t kk = cbase + (int64_t)y * n0 + x;
+    const bool fr = is_free(x, y);
     double zv = 0.0;
     if (fr) {
-      const float* tr = sm.tx + yl * TS + q;  // window row y - B
+      const float* tr = sm.tx + yl * TM + q;  // window row y - B
       const float* wr = sm.wy + yl * W;
       float acc = 0.0f;
 #pragma unroll
-      for (int m = 0; m < W; ++m) acc = __fmaf_rn(wr[m], tr[m * TS], acc);
-      zv = f2d_exact(acc);
+      for (int m = 0; m < W; ++m) acc = __fmaf_rn(wr[m], tr[m * TM], acc);
+      zv = (double)acc;
     }
-    double rv = o_r;
+    double rv;
     if (mode == 0) {
+      rv = fr ? a.rhs[kk] : 0.0;
       a.x[kk] = 0.0;
       l_bb += rv * rv;
       rout[kk] = rv;
     } else if (upd == 1) {
-      rv = fma(-alpha, o_ap, o_r);
-      a.x[kk] = fma(alpha, o_p, o_x);
+      rv = fma(-alpha, a.Ap[kk], rin[kk]);
+      a.x[kk] = fma(alpha, a.p[kk], a.x[kk]);
       l_rr += rv * rv;
       rout[kk] = rv;
+    } else {
+      rv = rin[kk];
     }
     dst[kk] = zv;
     l_rz += rv * zv;
@@ -1043,7 +1042,7 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
   }
   const bool narrow = narrow_passes<DIM>(c);
   if (DIM == 2 && narrow && !c->tpc.fp64 && c->cg_tiles) {  // both directions in one kernel
-    const int64_t blocks = 2 * (int64_t)((c->g.nn[0] + 15) / 16) * ((c->g.nn[1] + 15) / 16);
+    const int64_t blocks = 2 * (int64_t)pass2d_tiles(c->g.nn[0]) * pass2d_tiles(c->g.nn[1]);
     cudaError_t e = launch_k(c->use_pdl != 0, cg_pass2d_kernel<K>, dim3((unsigned)blocks),
                              dim3(kLineThreads), 0, s, a, init ? 0 : 1, init ? 1 : 0,
                              fuse ? 1 : 0, a.z);

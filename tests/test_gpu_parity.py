@@ -123,10 +123,11 @@ def test_precond_apply_approximates_mass_inverse(dim, k, n):
     assert rel_l2(xo, ze) <= 1e-13
 
 
-# 2D meshes whose band passes are narrow (tile kernel), with ragged 16 x 16 tiles;
-# 64 x 64 Q2 is the Taylor-Green size (162 CTAs, halos shared across many)
+# 2D meshes whose band passes are narrow (tile kernel): ragged last tiles and
+# 17-wide ones (16m + 1 node lines); 64 x 64 Q2 is the Taylor-Green size (128
+# CTAs, halos shared across many)
 TILED = [(1, (9, 7, 1)), (2, (5, 7, 1)), (3, (3, 5, 1)), (2, (40, 23, 1)), (3, (21, 9, 1)),
-         (2, (64, 64, 1))]
+         (1, (32, 16, 1)), (2, (64, 64, 1))]
 
 
 @pytest.mark.parametrize("k,n", TILED)
