@@ -286,13 +286,16 @@ def run_native(args):
     achieved64 = fl64 / (f["force_ms"] * 1e-3) / 1e12
     # kernels launched per attempt: per stage force, node gather, the initial
     # preconditioner application (pk kernels), v/x update and energy update,
-    # and per CG iteration the element apply, node gather and a preconditioner
-    # application (the CG update rides on it); then control and commit
+    # and per CG iteration M p (element apply + node gather, one tile kernel
+    # where the preconditioner is the tile kernel, pk == 1) and a
+    # preconditioner application (the CG update rides on it); then control
+    # and commit
     pk = m["pass_kernels"]
+    per_it = (1 if pk == 1 else 2) + pk
     attempts = m["steps"] + m["rejects"]
     # every solve launches at least its kUnrolled = 3 iterations (a converged
     # solve's later ones return at once)
-    launches = attempts * (2 * (4 + pk) + 2) + max(m["cg"], 3 * 2 * attempts) * (2 + pk)
+    launches = attempts * (2 * (4 + pk) + 2) + max(m["cg"], 3 * 2 * attempts) * per_it
     line = {
         "metric": "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error",
         "value": value,

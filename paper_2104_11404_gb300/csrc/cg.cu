@@ -946,6 +946,120 @@ __global__ void __launch_bounds__(kNodeThreads) cg_update_kernel(const CgArgs a,
   }
 }
 
+// ------------------------------------------- 2D fused element apply ----
+
+// The element PA apply and the node gather of M p in one kernel, over the
+// same 16 x 16 (last 17) node tiles as cg_pass2d_kernel, for the same narrow
+// 2D meshes.  A CTA owns the nodes of one tile and one component.  It stages
+// p = z + beta p_old over the elements that touch its nodes (the tile's own
+// elements and a ring of one element below and to the left, shared with the
+// neighbouring tiles), applies rho0K (M1 x M1) to every one of them, and sums
+// the element values at its nodes in the gather's element order.  Each
+// element product, each rho0K scaling and each node sum is the operation the
+// element kernel and the gather kernel perform, in the same order (no fused
+// multiply-add across them), so Ap and p are bitwise theirs; only the block
+// partials of p.Ap are added over another tiling.
+template <int K>
+struct Apply2DTile {
+  static constexpr int P = K + 1, ND1 = P * P, TS = 16;
+  static constexpr int NE1 = (TS + 1 + K - 1) / K + 1;  // elements touching 17 node lines
+  static constexpr int NPN = K * NE1 + 1;                // their node lines
+  double M1[P * P];
+  double u[NPN * NPN];      // p = z + beta p_old on the patch of nodes [y][x]
+  double t[NE1 * NE1 * ND1];
+  double y[NE1 * NE1 * ND1];
+};
+
+template <int K>
+__global__ void __launch_bounds__(kLineThreads) cg_apply2d_kernel(const CgArgs a) {
+  using AT = Apply2DTile<K>;
+  constexpr int P = AT::P, ND1 = AT::ND1, TS = AT::TS, NPN = AT::NPN;
+  constexpr int NT = kLineThreads;
+  pdl_enter();
+  if (gated(a)) return;
+  __shared__ AT sm;
+  const Geom& g = a.g;
+  const int n0 = g.nn[0], n1 = g.nn[1];
+  const int ntx = pass2d_tiles(n0), nty = pass2d_tiles(n1);
+  const int tile = (int)(blockIdx.x % (unsigned)(ntx * nty));
+  const int c = (int)(blockIdx.x / (unsigned)(ntx * nty));
+  const int tix = tile % ntx, tiy = tile / ntx;
+  const int x0 = tix * TS, y0 = tiy * TS;
+  const int wx = tix == ntx - 1 ? n0 - x0 : TS, wy = tiy == nty - 1 ? n1 - y0 : TS;
+  // elements touching nodes [x0, x0 + wx) x [y0, y0 + wy)
+  const int ex0 = x0 > 0 ? (x0 - 1) / K : 0, ey0 = y0 > 0 ? (y0 - 1) / K : 0;
+  const int ex1 = min(g.n[0] - 1, (x0 + wx - 1) / K), ey1 = min(g.n[1] - 1, (y0 + wy - 1) / K);
+  const int nex = ex1 - ex0 + 1, ney = ey1 - ey0 + 1;  // <= NE1
+  const int npx = K * nex + 1, npy = K * ney + 1;       // <= NPN
+  const int px0 = K * ex0, py0 = K * ey0;
+  const int tid = threadIdx.x;
+  const int64_t cbase = (int64_t)c * g.nnodes;
+  const double beta = a.cg->beta;
+  for (int i = tid; i < P * P; i += NT) sm.M1[i] = a.M1[(i / P) * (kMaxOrder + 1) + i % P];
+  for (int idx = tid; idx < npx * npy; idx += NT) {
+    const int py = idx / npx, px = idx - py * npx;
+    const int64_t k = cbase + (int64_t)(py0 + py) * n0 + (px0 + px);
+    sm.u[py * NPN + px] = a.z[k] + beta * a.p[k];  // as the element kernel forms it
+  }
+  __syncthreads();
+  const int items = nex * ney * ND1;
+  // contract along x: t[e][b][a'] = sum_a M1[a'][a] u_e[b][a]
+  for (int w = tid; w < items; w += NT) {
+    const int le = w / ND1, i = w - le * ND1, ap = i % P, b = i / P;
+    const int lex = le % nex, ley = le / nex;
+    const double* ur = sm.u + (K * ley + b) * NPN + K * lex;
+    double s = 0.0;
+    for (int aa = 0; aa < P; ++aa) s = fma(sm.M1[ap * P + aa], ur[aa], s);
+    sm.t[w] = s;
+  }
+  __syncthreads();
+  // along y: y[e][b'][a] = sum_b M1[b'][b] t[e][b][a]
+  for (int w = tid; w < items; w += NT) {
+    const int le = w / ND1, i = w - le * ND1, aa = i % P, bp = i / P;
+    const double* tr = sm.t + le * ND1 + aa;
+    double s = 0.0;
+    for (int b = 0; b < P; ++b) s = fma(sm.M1[bp * P + b], tr[b * P], s);
+    sm.y[w] = s;
+  }
+  __syncthreads();
+  double l = 0.0;
+  for (int o = tid; o < (TS + 1) * (TS + 1); o += NT) {
+    const int yl = o / (TS + 1), q = o - yl * (TS + 1);
+    if (q >= wx || yl >= wy) continue;
+    const int X = x0 + q, Y = y0 + yl;
+    // the elements containing the node along x and along y, in increasing
+    // order with the node's local index in each (as node_elems_1d)
+    const int qx = X / K, rx = X - qx * K, qy = Y / K, ry = Y - qy * K;
+    const int fx = (rx == 0 && qx > 0) ? qx - 1 : qx, fy = (ry == 0 && qy > 0) ? qy - 1 : qy;
+    const int nx = (rx == 0 && qx > 0 && qx < g.n[0]) ? 2 : 1;
+    const int ny = (ry == 0 && qy > 0 && qy < g.n[1]) ? 2 : 1;
+    double sacc = 0.0;
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky) {
+      if (ky >= ny) break;
+      const int ey = fy + ky, ly = Y - K * ey;
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        if (kx >= nx) break;
+        const int ex = fx + kx, lx = X - K * ex;
+        const int le = (ex - ex0) + nex * (ey - ey0);
+        const int64_t el = (int64_t)ex + (int64_t)g.n[0] * ey;
+        sacc = __dadd_rn(sacc, __dmul_rn(a.rho0K[el], sm.y[le * ND1 + lx + P * ly]));
+      }
+    }
+    const bool ess = c == 0 ? (X == 0 || X == n0 - 1) : (Y == 0 || Y == n1 - 1);
+    const double ap = ess ? 0.0 : sacc;
+    const double pv = sm.u[(Y - py0) * NPN + (X - px0)];
+    const int64_t k = cbase + (int64_t)Y * n0 + X;
+    a.p[k] = pv;
+    a.Ap[k] = ap;
+    l += pv * ap;
+  }
+  double tot;
+  if (reduce_last(l, a.part + 2 * kMaxPartials, &a.cg->ticket[kTicketA], &tot) && threadIdx.x == 0)
+    a.cg->alpha = a.cg->rz / tot;
+}
+
 __global__ void cg_reset_kernel(CgDev* cg, const Ctl* gate) {
   pdl_enter();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1006,6 +1120,14 @@ static bool narrow_passes(const lh_ctx* c) {
   return pass_tiles<DIM>(c->g, 0, 32) < 4 * (int64_t)c->num_sms;
 }
 
+// The 2D tile kernels (cg_pass2d_kernel, cg_apply2d_kernel): narrow 2D
+// meshes with the FP32 band preconditioner, unless the context turned them off.
+template <int DIM>
+static bool tiles_2d(const lh_ctx* c) {
+  return DIM == 2 && c->cg_tiles && c->tpc.enabled && !c->tpc.exact && !c->tpc.fp64 &&
+         narrow_passes<DIM>(c);
+}
+
 // Whether the CG update rides on the band passes: where the passes are
 // narrow the solve is a chain of latency-bound kernels and one launch fewer
 // per iteration pays; on large meshes the separate streaming update is cheaper
@@ -1041,7 +1163,7 @@ static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, c
     return cudaGetLastError();
   }
   const bool narrow = narrow_passes<DIM>(c);
-  if (DIM == 2 && narrow && !c->tpc.fp64 && c->cg_tiles) {  // both directions in one kernel
+  if (tiles_2d<DIM>(c)) {  // both directions in one kernel
     const int64_t blocks = 2 * (int64_t)pass2d_tiles(c->g.nn[0]) * pass2d_tiles(c->g.nn[1]);
     cudaError_t e = launch_k(c->use_pdl != 0, cg_pass2d_kernel<K>, dim3((unsigned)blocks),
                              dim3(kLineThreads), 0, s, a, init ? 0 : 1, init ? 1 : 0,
@@ -1088,9 +1210,16 @@ static cudaError_t cg_body_dk(const lh_ctx* c, const CgArgs& a, cudaStream_t s) 
   using L = ML<DIM, K>;
   const int eblocks = (int)((c->g.nelem + L::EPB - 1) / L::EPB);
   const bool pdl = c->use_pdl != 0;
-  cudaError_t e = launch_k(pdl, cg_elem_kernel<DIM, K>, dim3(eblocks), dim3(256), 0, s, a);
-  if (e == cudaSuccess)
-    e = launch_k(pdl, cg_gather_kernel<DIM, K>, dim3(node_grid(c)), dim3(kNodeThreads), 0, s, a);
+  cudaError_t e;
+  if (tiles_2d<DIM>(c)) {  // element apply and gather in one kernel over node tiles
+    const int64_t blocks = 2 * (int64_t)pass2d_tiles(c->g.nn[0]) * pass2d_tiles(c->g.nn[1]);
+    e = launch_k(pdl, cg_apply2d_kernel<K>, dim3((unsigned)blocks), dim3(kLineThreads), 0, s, a);
+  } else {
+    e = launch_k(pdl, cg_elem_kernel<DIM, K>, dim3(eblocks), dim3(256), 0, s, a);
+    if (e == cudaSuccess)
+      e = launch_k(pdl, cg_gather_kernel<DIM, K>, dim3(node_grid(c)), dim3(kNodeThreads), 0, s,
+                   a);
+  }
   if (e != cudaSuccess) return e;
   if (c->tpc.enabled && !c->tpc.exact && fuse_update<DIM>(c))
     return precond_passes<DIM, K>(c, a, false, s, true);
@@ -1153,8 +1282,7 @@ cudaError_t precond_apply(const lh_ctx* c, const double* in, double* out, cudaSt
 int precond_kernels(const lh_ctx* c) {
   if (!c->tpc.enabled) return 0;
   const int d = c->g.dim;
-  const bool narrow = d == 2 ? narrow_passes<2>(c) : narrow_passes<3>(c);
-  return (d == 2 && narrow && !c->tpc.fp64 && !c->tpc.exact && c->cg_tiles) ? 1 : d;
+  return (d == 2 && tiles_2d<2>(c)) ? 1 : d;
 }
 
 // The cluster-resident solve: one launch of a cluster of c->cg_cluster CTAs.

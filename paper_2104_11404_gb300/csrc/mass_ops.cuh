@@ -26,7 +26,7 @@ __device__ __forceinline__ void kron_mass(const double* M1, double* u, double* t
   for (int w = threadIdx.x; w < items; w += blockDim.x) {
     int ap = w % P, base = w - ap;
     double s = 0.0;
-    for (int a = 0; a < P; ++a) s += M1[ap * P + a] * u[base + a];
+    for (int a = 0; a < P; ++a) s = fma(M1[ap * P + a], u[base + a], s);
     t[w] = s;
   }
   __syncthreads();
@@ -34,21 +34,21 @@ __device__ __forceinline__ void kron_mass(const double* M1, double* u, double* t
     for (int w = threadIdx.x; w < items; w += blockDim.x) {
       int i = w % ND1, base = w - i, a = i % P, bp = i / P;
       double s = 0.0;
-      for (int b = 0; b < P; ++b) s += M1[bp * P + b] * t[base + b * P + a];
+      for (int b = 0; b < P; ++b) s = fma(M1[bp * P + b], t[base + b * P + a], s);
       y[w] = s;
     }
   } else {
     for (int w = threadIdx.x; w < items; w += blockDim.x) {
       int i = w % ND1, base = w - i, a = i % P, bp = (i / P) % P, cz = i / (P * P);
       double s = 0.0;
-      for (int b = 0; b < P; ++b) s += M1[bp * P + b] * t[base + (cz * P + b) * P + a];
+      for (int b = 0; b < P; ++b) s = fma(M1[bp * P + b], t[base + (cz * P + b) * P + a], s);
       u[w] = s;  // u is free again
     }
     __syncthreads();
     for (int w = threadIdx.x; w < items; w += blockDim.x) {
       int i = w % ND1, base = w - i, ab = i % (P * P), czp = i / (P * P);
       double s = 0.0;
-      for (int cz = 0; cz < P; ++cz) s += M1[czp * P + cz] * u[base + cz * P * P + ab];
+      for (int cz = 0; cz < P; ++cz) s = fma(M1[czp * P + cz], u[base + cz * P * P + ab], s);
       y[w] = s;
     }
   }
