@@ -428,9 +428,49 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
   const double* src = mode == 0 ? a.rhs : rin;
   const float scl = (float)a.tpc.scale;
   const double alpha = upd != 0 ? a.cg->alpha : 0.0;
-  // stage the window: each thread issues its loads 8 at a time into registers
-  // before it converts and stores them (a guarded load per loop iteration was
-  // measured to cost 2.4 us more per launch: the loads ran one after another)
+  // Every global load is issued before the shared-memory stores that would
+  // otherwise order it (a guarded load per loop iteration ran the loads one
+  // after another: 2.4 us more per launch for the window alone).  First the
+  // band rows (direction d's rows exclude the end nodes when d == c) and the
+  // operands of this thread's outputs, then the window in batches of 8.
+  constexpr int PB_ = (TM * W + NT - 1) / NT, PO = (TM * TM + NT - 1) / NT;
+  const int vx = (c == 0) ? 1 : 0, vy = (c == 1) ? 1 : 0;
+  float bxv[PB_], byv[PB_];
+  {
+    const float* fx = a.lfac + a.tpc.off[0][vx];
+    const float* fy = a.lfac + a.tpc.off[1][vy];
+#pragma unroll
+    for (int j = 0; j < PB_; ++j) {
+      const int idx = tid + j * NT;
+      const int qq = idx / W, m = idx - qq * W;
+      const int rx = x0 + qq - vx, ry = y0 + qq - vy;
+      const bool inb = idx < TM * W;
+      bxv[j] = (inb && qq < wx && rx >= 0 && rx < n0 - 2 * vx) ? fx[(int64_t)rx * W + m] : 0.0f;
+      byv[j] = (inb && qq < wy && ry >= 0 && ry < n1 - 2 * vy) ? fy[(int64_t)ry * W + m] : 0.0f;
+    }
+  }
+  double o_r[PO], o_ap[PO], o_p[PO], o_x[PO];
+#pragma unroll
+  for (int j = 0; j < PO; ++j) {
+    const int o = tid + j * NT;
+    const int yl = o / TM, q = o - yl * TM;
+    const bool own = o < TM * TM && q < wx && yl < wy;
+    const int x = x0 + q, y = y0 + yl;
+    const int64_t kk = own ? cbase + (int64_t)y * n0 + x : 0;
+    o_r[j] = o_ap[j] = o_p[j] = o_x[j] = 0.0;
+    if (own) {
+      if (mode == 0) {
+        o_r[j] = is_free(x, y) ? a.rhs[kk] : 0.0;
+      } else {
+        o_r[j] = rin[kk];
+        if (upd == 1) {
+          o_ap[j] = a.Ap[kk];
+          o_p[j] = a.p[kk];
+          o_x[j] = a.x[kk];
+        }
+      }
+    }
+  }
   {
     constexpr int PER = (WN * WN + NT - 1) / NT;
     constexpr int CH = 8;
@@ -458,17 +498,13 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
       }
     }
   }
-  // band rows: direction d's rows exclude the end nodes when d == c
-  {
-    const int vx = (c == 0) ? 1 : 0, vy = (c == 1) ? 1 : 0;
-    const float* fx = a.lfac + a.tpc.off[0][vx];
-    const float* fy = a.lfac + a.tpc.off[1][vy];
-    for (int idx = tid; idx < TM * W; idx += NT) {
+#pragma unroll
+  for (int j = 0; j < PB_; ++j) {
+    const int idx = tid + j * NT;
+    if (idx < TM * W) {
       const int qq = idx / W, m = idx - qq * W;
-      const int rx = x0 + qq - vx, ry = y0 + qq - vy;
-      sm.wxT[m * TM + qq] =
-          (qq < wx && rx >= 0 && rx < n0 - 2 * vx) ? fx[(int64_t)rx * W + m] : 0.0f;
-      sm.wy[idx] = (qq < wy && ry >= 0 && ry < n1 - 2 * vy) ? fy[(int64_t)ry * W + m] : 0.0f;
+      sm.wxT[m * TM + qq] = bxv[j];
+      sm.wy[idx] = byv[j];
     }
   }
   __syncthreads();
@@ -485,9 +521,11 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
   }
   __syncthreads();
   double l_bb = 0.0, l_rz = 0.0, l_rr = 0.0;
-  for (int o = tid; o < TM * TM; o += NT) {
+#pragma unroll
+  for (int j = 0; j < PO; ++j) {
+    const int o = tid + j * NT;
     const int yl = o / TM, q = o - yl * TM;
-    if (q >= wx || yl >= wy) continue;
+    if (o >= TM * TM || q >= wx || yl >= wy) continue;
     const int x = x0 + q, y = y0 + yl;
     const int64_t kk = cbase + (int64_t)y * n0 + x;
     const bool fr = is_free(x, y);
@@ -500,19 +538,16 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
       for (int m = 0; m < W; ++m) acc = __fmaf_rn(wr[m], tr[m * TM], acc);
       zv = (double)acc;
     }
-    double rv;
+    double rv = o_r[j];
     if (mode == 0) {
-      rv = fr ? a.rhs[kk] : 0.0;
       a.x[kk] = 0.0;
       l_bb += rv * rv;
       rout[kk] = rv;
     } else if (upd == 1) {
-      rv = fma(-alpha, a.Ap[kk], rin[kk]);
-      a.x[kk] = fma(alpha, a.p[kk], a.x[kk]);
+      rv = fma(-alpha, o_ap[j], o_r[j]);
+      a.x[kk] = fma(alpha, o_p[j], o_x[j]);
       l_rr += rv * rv;
       rout[kk] = rv;
-    } else {
-      rv = rin[kk];
     }
     dst[kk] = zv;
     l_rz += rv * zv;
