@@ -1017,6 +1017,7 @@ struct Apply2DTile {
   static constexpr int NE1 = (TS + 1 + K - 1) / K + 1;  // elements touching 17 node lines
   static constexpr int NPN = K * NE1 + 1;                // their node lines
   double M1[P * P];
+  double r0[NE1 * NE1];     // rho0 |J0| of the patch's elements
   double u[NPN * NPN];      // p = z + beta p_old on the patch of nodes [y][x]
   double t[NE1 * NE1 * ND1];
   double y[NE1 * NE1 * ND1];
@@ -1025,7 +1026,7 @@ struct Apply2DTile {
 template <int K>
 __global__ void __launch_bounds__(kLineThreads) cg_apply2d_kernel(const CgArgs a) {
   using AT = Apply2DTile<K>;
-  constexpr int P = AT::P, ND1 = AT::ND1, TS = AT::TS, NPN = AT::NPN;
+  constexpr int P = AT::P, ND1 = AT::ND1, TS = AT::TS, NE1 = AT::NE1, NPN = AT::NPN;
   constexpr int NT = kLineThreads;
   pdl_enter();
   if (gated(a)) return;
@@ -1049,8 +1050,15 @@ __global__ void __launch_bounds__(kLineThreads) cg_apply2d_kernel(const CgArgs a
   const double beta = a.cg->beta;
   for (int i = tid; i < P * P; i += NT) sm.M1[i] = a.M1[(i / P) * (kMaxOrder + 1) + i % P];
   {  // the patch's loads all issued before its stores
-    constexpr int PER = (NPN * NPN + NT - 1) / NT;
-    double zv[PER], pv[PER];
+    constexpr int PER = (NPN * NPN + NT - 1) / NT, PR = (NE1 * NE1 + NT - 1) / NT;
+    double zv[PER], pv[PER], rv[PR];
+#pragma unroll
+    for (int j = 0; j < PR; ++j) {
+      const int idx = tid + j * NT;
+      const bool ok = idx < nex * ney;
+      const int ly = ok ? idx / nex : 0, lx = ok ? idx - ly * nex : 0;
+      rv[j] = ok ? a.rho0K[(int64_t)(ex0 + lx) + (int64_t)g.n[0] * (ey0 + ly)] : 0.0;
+    }
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
       const int idx = tid + j * NT;
@@ -1068,6 +1076,9 @@ __global__ void __launch_bounds__(kLineThreads) cg_apply2d_kernel(const CgArgs a
         sm.u[py * NPN + px] = zv[j] + beta * pv[j];  // as the element kernel forms it
       }
     }
+#pragma unroll
+    for (int j = 0; j < PR; ++j)
+      if (tid + j * NT < nex * ney) sm.r0[tid + j * NT] = rv[j];
   }
   __syncthreads();
   const int items = nex * ney * ND1;
@@ -1111,8 +1122,7 @@ __global__ void __launch_bounds__(kLineThreads) cg_apply2d_kernel(const CgArgs a
         if (kx >= nx) break;
         const int ex = fx + kx, lx = X - K * ex;
         const int le = (ex - ex0) + nex * (ey - ey0);
-        const int64_t el = (int64_t)ex + (int64_t)g.n[0] * ey;
-        sacc = __dadd_rn(sacc, __dmul_rn(a.rho0K[el], sm.y[le * ND1 + lx + P * ly]));
+        sacc = __dadd_rn(sacc, __dmul_rn(sm.r0[le], sm.y[le * ND1 + lx + P * ly]));
       }
     }
     const bool ess = c == 0 ? (X == 0 || X == n0 - 1) : (Y == 0 || Y == n1 - 1);

@@ -177,15 +177,37 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     for (int c = 0; c < DIM; ++c) x0[c] = MIXED ? A.x[c * g.nnodes + n0] : 0.0;
   }
   if (active) {
-    for (int w = tq; w < DIM * ND1; w += TEAM) {
-      int c = w / ND1, i = w - c * ND1;
-      int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
-      int64_t node = elem_node<K>(g, E, a, b, cc);
-      xs[w] = from_double<T>(A.x[c * g.nnodes + node] - x0[c]);
-      vs[w] = from_double<T>(A.v[c * g.nnodes + node]);
-      if (with_w) ws[w] = A.vtest[c * g.nnodes + node];
+    // every load issued before the shared-memory stores (a load per loop
+    // iteration behind the previous iteration's stores runs one at a time)
+    constexpr int PS = (DIM * ND1 + TEAM - 1) / TEAM, PE = (ND2 + TEAM - 1) / TEAM;
+    double xv[PS], vv[PS], wv[PS], ev[PE];
+#pragma unroll
+    for (int j = 0; j < PS; ++j) {
+      const int w = tq + j * TEAM;
+      xv[j] = vv[j] = wv[j] = 0.0;
+      if (w < DIM * ND1) {
+        const int c = w / ND1, i = w - c * ND1;
+        const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+        const int64_t k = c * g.nnodes + elem_node<K>(g, E, a, b, cc);
+        xv[j] = A.x[k];
+        vv[j] = A.v[k];
+        if (with_w) wv[j] = A.vtest[k];
+      }
     }
-    for (int j = tq; j < ND2; j += TEAM) es[j] = from_double<T>(A.e[el * ND2 + j]);
+#pragma unroll
+    for (int j = 0; j < PE; ++j) ev[j] = tq + j * TEAM < ND2 ? A.e[el * ND2 + tq + j * TEAM] : 0.0;
+#pragma unroll
+    for (int j = 0; j < PS; ++j) {
+      const int w = tq + j * TEAM;
+      if (w < DIM * ND1) {
+        xs[w] = from_double<T>(xv[j] - x0[w / ND1]);
+        vs[w] = from_double<T>(vv[j]);
+        if (with_w) ws[w] = wv[j];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < PE; ++j)
+      if (tq + j * TEAM < ND2) es[tq + j * TEAM] = from_double<T>(ev[j]);
   }
   team_sync<TEAM>();
 
@@ -828,13 +850,24 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   int E[3] = {0, 0, 0};
   elem_ijk(g, active ? el : 0, E);
   const int nstage = (pref != 0.0) ? 2 * DIM * ND1 : DIM * ND1;
-  if (active)
-    for (int w = tq; w < nstage; w += NQD) {
-      const int f = w / ND1, i = w - f * ND1;
-      const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
-      const int64_t node = elem_node<K>(g, E, a, b, cc);
-      ws[w] = f < DIM ? A.w[f * g.nnodes + node] : A.x[(f - DIM) * g.nnodes + node];
+  if (active) {  // loads first, then the shared-memory stores
+    constexpr int PS = (2 * DIM * ND1 + NQD - 1) / NQD;
+    double sv[PS];
+#pragma unroll
+    for (int j = 0; j < PS; ++j) {
+      const int w = tq + j * NQD;
+      sv[j] = 0.0;
+      if (w < nstage) {
+        const int f = w / ND1, i = w - f * ND1;
+        const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+        const int64_t node = elem_node<K>(g, E, a, b, cc);
+        sv[j] = f < DIM ? A.w[f * g.nnodes + node] : A.x[(f - DIM) * g.nnodes + node];
+      }
     }
+#pragma unroll
+    for (int j = 0; j < PS; ++j)
+      if (tq + j * NQD < nstage) ws[tq + j * NQD] = sv[j];
+  }
   team_sync<NQD>();
 
   if constexpr (MIXED) {
