@@ -243,11 +243,15 @@ __device__ double cta_mass_colored(const Geom& g, const double* M1s, double rho0
 
 // In-CTA preconditioned CG: M_V x = b on the free components, b in R (the
 // essential entries of b are zero), x in X.  Returns the iteration count;
-// *relres = ||r|| / ||b||; *conv = converged.
+// *relres = ||r|| / ||b||; *conv = converged.  R, X, Z, Pv, AP and ApE are
+// disjoint (slices of the CTA's scratch slot, and its element buffer), which
+// lets the vector loops issue later iterations' loads ahead of their stores.
 template <int DIM, int K, int NTT>
-__device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, double* Z,
-                      double* Pv, double* AP, double* ApE, const double* rho0K,
-                      unsigned char* smem, const double* M1, double* relres, bool* conv) {
+__device__ int cta_cg(const BatchArgs& a, const BInst& I, double* __restrict__ R,
+                      double* __restrict__ X, double* __restrict__ Z, double* __restrict__ Pv,
+                      double* __restrict__ AP, double* __restrict__ ApE,
+                      const double* __restrict__ rho0K, unsigned char* smem, const double* M1,
+                      double* relres, bool* conv) {
   using L = BL<DIM, K, false, NTT>;
   constexpr int P = K + 1, ND1 = ipow(P, DIM), CGT = L::CGT;
   const Geom& g = I.g;
@@ -260,6 +264,7 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
   double* lines = a.smem_lines ? y + CGT * DIM * ND1 : nullptr;
   for (int i = tid; i < P * P; i += NTT) M1s[i] = M1[(i / P) * (kMaxOrder + 1) + i % P];
   double bb = 0.0;
+#pragma unroll 4
   for (int64_t k = tid; k < nv; k += NTT) {
     const double bv = R[k];
     X[k] = 0.0;
@@ -273,6 +278,7 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
   }
   tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines, a.smem_lines);
   double rz = 0.0;
+#pragma unroll 4
   for (int64_t k = tid; k < nv; k += NTT) {
     const double zv = Z[k];
     Pv[k] = zv;
@@ -309,7 +315,8 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
     }
     const double alpha = rz / pap;
     double lrr = 0.0;
-    for (int64_t k = tid; k < nv; k += NTT) {
+#pragma unroll 4
+  for (int64_t k = tid; k < nv; k += NTT) {
       X[k] += alpha * Pv[k];
       const double rv = R[k] - alpha * AP[k];
       R[k] = rv;
@@ -320,11 +327,13 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* R, double* X, 
     if (ok || !(rr == rr) || it >= a.maxit) break;
     tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines, a.smem_lines);
     double lrz = 0.0;
-    for (int64_t k = tid; k < nv; k += NTT) lrz += R[k] * Z[k];
+#pragma unroll 4
+  for (int64_t k = tid; k < nv; k += NTT) lrz += R[k] * Z[k];
     const double rz_new = cta_sum(lrz);
     const double beta = rz_new / rz;
     rz = rz_new;
-    for (int64_t k = tid; k < nv; k += NTT) Pv[k] = Z[k] + beta * Pv[k];
+#pragma unroll 4
+  for (int64_t k = tid; k < nv; k += NTT) Pv[k] = Z[k] + beta * Pv[k];
     __syncthreads();
   }
   *relres = sqrt(rr / bb);
