@@ -73,6 +73,15 @@ __device__ __forceinline__ double tg_source(double X, double Y, double gam) {
          (cos(3.0 * pi * X) * cos(pi * Y) - cos(pi * X) * cos(3.0 * pi * Y));
 }
 
+// The same in FP32 for the mixed path, where the source is a right-hand-side
+// term evaluated like the stress (four FP64 cosines per point would keep the
+// narrow FP64 pipe busy for most of the force kernel).
+__device__ __forceinline__ float tg_source_f(float X, float Y, float gam) {
+  const float pi = 3.14159265358979f;
+  return 0.25f * pi / (gam - 1.0f) *
+         (cosf(3.0f * pi * X) * cosf(pi * Y) - cosf(pi * X) * cosf(3.0f * pi * Y));
+}
+
 // Synchronisation of one element's team.  A team of at most 32 threads that
 // divides 32 lies inside one warp, so a warp barrier orders its shared-memory
 // traffic and the warps of the block run their elements independently;
@@ -130,7 +139,10 @@ __device__ __forceinline__ void force_tables(const Basis1D& bas, unsigned char* 
 // One tile of EPB element slots [slot0, slot0 + EPB) of the force evaluation,
 // by all NTT threads of the block (the grid kernel below uses one tile per
 // block; the batched stage kernel loops over the tiles of an instance).
-template <int DIM, int K, bool MIXED, int NTT, int QPT = 1>
+// SRC32: the mixed path evaluates the Taylor-Green energy source in FP32
+// (the grid kernel); otherwise it is evaluated in FP64 (the batched kernel,
+// whose point-blast instances carry no source, keeps its code unchanged).
+template <int DIM, int K, bool MIXED, int NTT, int QPT = 1, bool SRC32 = false>
 __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const Basis1D& bas,
                                            const ForceArgs& A, const double* rho0Kp,
                                            unsigned char* smem, int64_t slot0) {
@@ -368,9 +380,15 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
         gq[q] = gsum;
       }
       if (A.srcE != nullptr && DIM == 2) {
-        const double alpha = Wd[qx] * Wd[qy];
-        double X = x0[0] + to_double(xval[0]), Y = x0[1] + to_double(xval[1]);
-        gq[NQD + q] = alpha * prm.rho0K[el] * tg_source(X, Y, prm.ph.gamma);
+        if constexpr (MIXED && SRC32) {
+          const float X = __fadd_rn(from_double<float>(x0[0]), xval[0]);
+          const float Y = __fadd_rn(from_double<float>(x0[1]), xval[1]);
+          gq[NQD + q] = to_double(alphaT * rho0K * tg_source_f(X, Y, prm.ph.gammaf));
+        } else {
+          const double alpha = Wd[qx] * Wd[qy];
+          double X = x0[0] + to_double(xval[0]), Y = x0[1] + to_double(xval[1]);
+          gq[NQD + q] = alpha * prm.rho0K[el] * tg_source(X, Y, prm.ph.gamma);
+        }
       }
     }
   // time-step estimate and error flags of the block
@@ -610,8 +628,8 @@ force_kernel(const ForceKParams prm) {
   extern __shared__ __align__(16) unsigned char smem[];
   force_tables<DIM, K, MIXED, F::NT>(prm.b, smem);
   __syncthreads();
-  force_tile<DIM, K, MIXED, F::NT>(prm.g, prm.ph, prm.b, prm.a, prm.rho0K, smem,
-                                   (int64_t)blockIdx.x * F::EPB);
+  force_tile<DIM, K, MIXED, F::NT, 1, true>(prm.g, prm.ph, prm.b, prm.a, prm.rho0K, smem,
+                                            (int64_t)blockIdx.x * F::EPB);
 }
 
 // ------------------------------------------------------------- gather ----
