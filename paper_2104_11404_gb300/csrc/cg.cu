@@ -154,6 +154,8 @@ struct PassTile {
   static constexpr int LT = LTV;  // node lines per tile
   T tile[LT * ldt];
   T wrows[TP * W];
+  int64_t lbase[LT];  // first entry of each tile line
+  int lflag[LT];      // 0: past the last line, 1: free line, 2: wall-normal line (all zero)
 };
 
 template <int DIM>
@@ -210,23 +212,43 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
   };
   const double* src = mode == 0 ? a.rhs : src_in;
   const T scl = (mode == 2) ? T(1) : (T)a.tpc.scale;
-  // stage the tile with its halo: positions [p0 - B, p0 + TP + B)
-  const int span = TP + 2 * B;
-  for (int idx = tid; idx < LT * span; idx += nt) {
-    // along x (d == 0) walk a line, otherwise walk across lines
-    const int l = d == 0 ? idx / span : idx % LT;
-    const int q = d == 0 ? idx - l * span : idx / LT;
-    const int pos = p0 - B + q;
-    T val = T(0);
-    int64_t base;
-    bool wall;
-    if (pos >= var && pos < nd - var && line_info(l, base, wall) && !wall) {
-      const int64_t k = base + pos * stride;
-      double v = src[k];
-      if (upd == 1) v = fma(-alpha, a.Ap[k], v);
-      val = (T)v * scl;
+  // the tile's lines, once (their 64-bit index arithmetic stays out of the loops)
+  for (int l = tid; l < LT; l += nt) {
+    int64_t base = 0;
+    bool wall = false;
+    const bool ok = line_info(l, base, wall);
+    sm.lbase[l] = base;
+    sm.lflag[l] = ok ? (wall ? 2 : 1) : 0;
+  }
+  __syncthreads();
+  // stage the tile with its halo: positions [p0 - B, p0 + TP + B); each thread
+  // issues its loads CH at a time into registers before it stores them (one
+  // guarded load per iteration behind the previous store runs them serially)
+  constexpr int span = TP + 2 * B, CH = 4;
+  for (int i0 = tid; i0 < LT * span; i0 += CH * nt) {
+    double v[CH];
+    bool ok[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int idx = i0 + j * nt;
+      // along x (d == 0) walk a line, otherwise walk across lines
+      const int l = d == 0 ? idx / span : idx % LT;
+      const int q = d == 0 ? idx - l * span : idx / LT;
+      const int pos = p0 - B + q;
+      ok[j] = idx < LT * span && pos >= var && pos < nd - var && sm.lflag[l] == 1;
+      const int64_t k = ok[j] ? sm.lbase[l] + pos * stride : 0;
+      v[j] = ok[j] ? src[k] : 0.0;
+      if (upd == 1 && ok[j]) v[j] = fma(-alpha, a.Ap[k], v[j]);
     }
-    tile[l * ldt + q] = val;
+#pragma unroll
+    for (int j = 0; j < CH; ++j) {
+      const int idx = i0 + j * nt;
+      if (idx < LT * span) {
+        const int l = d == 0 ? idx / span : idx % LT;
+        const int q = d == 0 ? idx - l * span : idx / LT;
+        tile[l * ldt + q] = ok[j] ? (T)v[j] * scl : T(0);
+      }
+    }
   }
   {
     const int nrow = nd - 2 * var;  // rows of the band (interior positions)
@@ -246,10 +268,10 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     const int l = d == 0 ? o / TP : o % LT;
     const int q = d == 0 ? o - l * TP : o / LT;
     const int pos = p0 + q;
-    int64_t base;
-    bool wall;
-    if (pos >= nd || !line_info(l, base, wall)) continue;
-    const int64_t kk = base + pos * stride;
+    const int fl = sm.lflag[l];
+    if (pos >= nd || fl == 0) continue;
+    const bool wall = fl == 2;
+    const int64_t kk = sm.lbase[l] + pos * stride;
     double zv = 0.0;
     if (!wall && pos >= var && pos < nd - var) {
       const T* wr = wrows + q * W;
@@ -302,7 +324,7 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
 // upd: the CG update fused into the loop passes (see pass_tile); the first
 // pass ends the iteration with the convergence test on |r|^2.
 template <int DIM, int K, typename T, int LTV>
-__global__ void __launch_bounds__(kLineThreads) cg_pass_kernel(const CgArgs a, int d, int mode,
+__global__ void __launch_bounds__(kLineThreads, 4) cg_pass_kernel(const CgArgs a, int d, int mode,
                                                               int last, int init, int upd,
                                                               const double* src_in,
                                                               double* dst) {
