@@ -40,6 +40,20 @@ def _dist():
     return world, rank, local
 
 
+def rank_reduce(x, op, world, device):
+    """Max ("max") or sum ("sum") of a scalar over the ranks of the process
+    group, through a tensor on `device` ("cuda" with NCCL, "cpu" with gloo);
+    the value itself at world size 1."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    red = torch.distributed.ReduceOp.MAX if op == "max" else torch.distributed.ReduceOp.SUM
+    torch.distributed.all_reduce(t, op=red)
+    return float(t.item())
+
+
+
 class Clocks:
     """nvidia-smi samples of SM clock and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -160,18 +174,10 @@ def run_native(args):
             torch.distributed.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return rank_reduce(x, "max", world, "cuda")
 
     def sum_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        return float(t.item())
+        return rank_reduce(x, "sum", world, "cuda")
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
