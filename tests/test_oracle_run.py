@@ -236,3 +236,61 @@ def test_step_counts_sanity_band():
     v, e, x = o.init_state()
     stats, _, _ = o.run(0.8, v, e, x)
     assert 100 < stats["steps"] < 2000
+
+
+@pytest.mark.parametrize("dim,k,lo,hi", [(2, 1, (0.0, 0.0, 0.0), (1.0, 1.0, 1.0)),
+                                         (2, 3, (-0.5, -0.5, 0.0), (0.5, 1.5, 1.0)),
+                                         (3, 2, (0.0, 0.0, 0.0), (2.0, 1.0, 0.5))])
+def test_total_mass_closed_form(dim, k, lo, hi):
+    """With rho0 = 1: 1.M_V.1 = d |Omega| (each component's basis sums to
+    one) and 1.M_E.1 = |Omega|, on boxes that are not the unit square, so a
+    Jacobian scale or a dropped quadrature weight shows."""
+    o = O.Oracle(dim=dim, nx=3, ny=2, nz=2, order=k, problem=O.SEDOV, lo=list(lo), hi=list(hi))
+    vol = float(np.prod([hi[i] - lo[i] for i in range(dim)]))
+    one_v, one_e = np.ones(o.nv), np.ones(o.ne)
+    assert abs(one_v @ o.mass_apply_v(one_v) - dim * vol) <= 1e-13 * dim * vol
+    assert abs(one_e @ o.mass_apply_e(one_e) - vol) <= 1e-13 * vol
+
+
+def test_taylor_green_half_turn_symmetry():
+    """The Taylor-Green velocity, pressure and energy source are invariant under
+    the half turn (x, y) -> (1 - x, 1 - y) of the unit square, which maps the
+    velocity vector to minus itself.  So is the discrete state after steps with
+    viscosity: node (i, j) -> (n-1-i, n-1-j), v -> -v, and each element's
+    energy dofs reversed.  A reversed basis, a swapped index or a sign error in
+    one direction breaks it."""
+    n = 6
+    o = O.Oracle(dim=2, nx=n, ny=n, order=2, problem=O.TAYLOR_GREEN, gamma=5.0 / 3.0, visc=1,
+                 source=1, cfl=0.1)
+    v, e, x = o.init_state()
+    stats, _, st = o.run(0.05, v, e, x)
+    assert st == O.OK and stats["steps"] > 10
+    nn = 2 * n + 1
+    V, X = v.reshape(2, nn, nn), x.reshape(2, nn, nn)  # [c][y][x]
+    vmax = np.abs(V).max()
+    assert vmax > 0.5
+    assert np.abs(V[:, ::-1, ::-1] + V).max() <= 1e-11 * vmax
+    assert np.abs(X[:, ::-1, ::-1] - (1.0 - X)).max() <= 1e-12
+    E = e.reshape(n, n, 2, 2)  # [ey, ex, jy, jx]
+    assert np.abs(E[::-1, ::-1, ::-1, ::-1] - E).max() <= 1e-11 * np.abs(e).max()
+    # the swap x <-> y maps the flow to its time reversal, not to itself: the
+    # energy after the steps is not swap-symmetric (the test tells them apart)
+    assert np.abs(E - E.transpose(1, 0, 3, 2)).max() > 1e-9 * np.abs(e).max()
+
+
+def test_gresho_quarter_turn_symmetry():
+    """The vortex on the centred square is invariant under the quarter turn
+    (x, y) -> (-y, x), which rotates the velocity vector: node (i, j) ->
+    (n-1-j, i), v_x -> -v_y, v_y -> v_x."""
+    n = 4
+    o = O.Oracle(dim=2, nx=n, ny=n, order=3, problem=O.GRESHO, gamma=5.0 / 3.0, visc=0,
+                 lo=[-0.5, -0.5, 0], hi=[0.5, 0.5, 1])
+    v, e, x = o.init_state()
+    stats, _, st = o.run(0.15, v, e, x)
+    assert st == O.OK and stats["steps"] > 10
+    nn = 3 * n + 1
+    V = v.reshape(2, nn, nn)  # [c][y][x]
+    vmax = np.abs(V).max()
+    assert vmax > 0.5
+    assert np.abs(V[0][:, ::-1].T + V[1]).max() <= 1e-11 * vmax
+    assert np.abs(V[1][:, ::-1].T - V[0]).max() <= 1e-11 * vmax
