@@ -119,7 +119,7 @@ typedef struct lh_phys_desc {
                             kernels launched one by one, with a host poll of the CG
                             between iteration batches (for kernel profilers) */
   int32_t cg_cluster;    /* 0 (default): the whole velocity solve of a small 2D problem
-                            (N_V <= 6,000, tensor preconditioner) runs as one launch of a
+                            (N_V <= 1,500, tensor preconditioner) runs as one launch of a
                             thread-block cluster when the device allows it; 1: whenever it
                             can (any 2D size); -1: never (one kernel per CG phase) */
   int32_t cg_tiles;      /* 0 (default): in 2D, where the band preconditioner's line passes

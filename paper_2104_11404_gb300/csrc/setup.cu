@@ -544,12 +544,13 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     e = cudaMemcpy(A.lchol, lc.data(), lc.size() * sizeof(double), cudaMemcpyHostToDevice);
   if ((st = cuda_check(c, e, "preconditioner")) != LH_OK) return fail(st, c->err);
   if ((st = cuda_check(c, cg_prepare(c), "cg attributes")) != LH_OK) return fail(st, c->err);
-  // cluster-resident CG: small 2D problems with the band preconditioner (measured
-  // faster than the kernel chain up to N_V ~ 8k; slower from ~30k, where the
-  // solve needs more than the cluster's 16 SMs)
+  // cluster-resident CG: small 2D problems with the band preconditioner.  Against
+  // the kernel chain with its 2D tile kernels it was measured 10% faster at
+  // N_V = 578 (8 x 8 Q2) and 6-7% slower at 2,178 and 4,802 (16^2, 24^2), so
+  // only the smallest solves take it.
   c->cg_cluster = 0;
   if (phys->cg_cluster >= 0 && d == 2 && c->tpc.enabled && !c->tpc.exact && !c->tpc.fp64 &&
-      (phys->cg_cluster == 1 || g.nv <= 6000))
+      (phys->cg_cluster == 1 || g.nv <= 1500))
     c->cg_cluster = cg_cluster_choose(c);
   c->cg_tiles = phys->cg_tiles >= 0 ? 1 : 0;
   Ctl ctl0;

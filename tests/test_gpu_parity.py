@@ -397,7 +397,7 @@ def test_cluster_cg_matches_kernel_chain(name, n):
     rng = np.random.default_rng(17)
     b = rng.normal(size=o.nv)
     xo, _, _, _ = o.mass_solve_v(b)
-    gc = gpu_for(cfg)                                          # cluster form (auto)
+    gc = gpu_for(cfg, phys_overrides={"cg_cluster": 1})       # cluster form (forced)
     gk = gpu_for(cfg, phys_overrides={"cg_cluster": -1})
     xc, itc, rrc = gc.mass_solve_v(dev(b))
     xk, itk, rrk = gk.mass_solve_v(dev(b))
