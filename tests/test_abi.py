@@ -68,3 +68,49 @@ def test_layout_sizes_match_oracle():
         o = O.Oracle(dim=cfg["dim"], nx=cfg["n"][0], ny=cfg["n"][1], nz=cfg["n"][2],
                      order=cfg["order"], problem=O.UNIFORM)
         assert (o.nv, o.ne, o.nelem) == (nv, ne, nel)
+
+
+STRUCTS = ["lh_mesh_desc", "lh_disc_desc", "lh_phys_desc", "lh_layout_info", "lh_run_stats",
+           "lh_batch_stats", "lh_batch_tuning"]
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and
+    field offsets (a field added to one side only, or out of order, shows)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2104_11404_gb300 import lagh
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lagh.h"', "int main(void) {"]
+    for s in STRUCTS:
+        lines.append('  printf("%s sizeof %%zu\\n", sizeof(%s));' % (s, s))
+        for name, _ in getattr(lagh, s)._fields_:
+            lines.append('  printf("%s %s %%zu\\n", offsetof(%s, %s));' % (s, name, s, name))
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    seen = set()
+    for line in out.splitlines():
+        s, field, val = line.split()
+        cls = getattr(lagh, s)
+        if field == "sizeof":
+            assert ctypes.sizeof(cls) == int(val), s
+        else:
+            assert getattr(cls, field).offset == int(val), (s, field)
+        seen.add(s)
+    assert seen == set(STRUCTS)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No CPU fallback: with the shared library missing, loading raises."""
+    from paper_2104_11404_gb300 import lagh
+    monkeypatch.setattr(lagh, "_lib", None)
+    monkeypatch.setattr(lagh, "LIB_PATH", str(tmp_path / "missing" / "liblagh.so"))
+    with pytest.raises(RuntimeError):
+        lagh.load()
