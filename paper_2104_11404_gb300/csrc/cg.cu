@@ -137,17 +137,19 @@ __device__ __forceinline__ bool end_iteration(const CgArgs& a, double rr) {
 
 // One pass of the tensor-product preconditioner along direction d: every
 // node line of every component is multiplied by the banded inverse of the 1D
-// mass matrix.  A CTA owns a tile of kPassLines lines x 32 positions: it stages the
-// tile and its +-B halo along the line in shared memory (coalesced: along x
-// the lines are contiguous rows, along y / z neighbouring lines are
-// neighbouring nodes), then each thread forms 4 outputs in FP32.
+// mass matrix.  A CTA owns a tile of LT (8 or 32) node lines x 32 positions:
+// it stages the tile and its +-B halo along the line in shared memory
+// (coalesced: along x the lines are contiguous rows, along y / z neighbouring
+// lines are neighbouring nodes), then each of its 256 threads forms LT / 8
+// outputs in FP32.
 //
 // mode: 0 = first pass of the initial preconditioning (reads rhs, writes r = b
 // on free components and x = 0, sums b.b), 1 = first pass inside the loop
 // (reads r), 2 = later pass (reads z, writes z2 / z alternately, see caller).
 // last: the pass along the last direction (sums r.z; init also writes p = z).
-// Shared memory of one band-pass tile: 32 lines x (32 positions + halo) of
-// input and the band rows of the 32 positions, in the band's precision T.
+// Shared memory of one band-pass tile: LT lines x (32 positions + halo) of
+// input, the band rows of the 32 positions in the band's precision T, and the
+// first entry and kind of each of the tile's lines.
 template <int K, typename T = float, int LTV = 32>
 struct PassTile {
   static constexpr int B = PB<K>::B, W = 2 * B + 1, TP = 32, ldt = TP + 2 * B + 1;
@@ -310,12 +312,9 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
   __syncthreads();  // the tile buffers are reused by the next tile
 }
 
-// One pass of the tensor-product preconditioner along direction d: every
-// node line of every component is multiplied by the banded inverse of the 1D
-// mass matrix.  A CTA owns a tile of kPassLines lines x 32 positions: it stages the
-// tile and its +-B halo along the line in shared memory (coalesced: along x
-// the lines are contiguous rows, along y / z neighbouring lines are
-// neighbouring nodes), then each thread forms 4 outputs in FP32.
+// One pass of the tensor-product preconditioner along direction d over one
+// tile per CTA (pass_tile), at most 4 CTAs of 256 threads per SM (64
+// registers).
 //
 // mode: 0 = first pass of the initial preconditioning (reads rhs, writes r = b
 // on free components and x = 0, sums b.b), 1 = first pass inside the loop
@@ -1244,8 +1243,9 @@ static bool fuse_update(const lh_ctx* c) {
 template <int DIM, int K>
 static cudaError_t precond_passes(const lh_ctx* c, const CgArgs& a, bool init, cudaStream_t s,
                                   bool fuse = false) {
-  // out of place: r -> z (d = 0), then alternate between Ap (free here) and z
-  // so that the last direction writes z
+  // out of place: r -> z (d = 0), then alternate between Ap (free here; ApE
+  // when the update is fused) and z so that the last direction writes z; the
+  // 2D tile kernel goes from r to z in one launch
   const double* src = a.r;
   double* bufs[2] = {a.z, fuse ? a.ApE : a.Ap};
   if (c->tpc.exact) {
