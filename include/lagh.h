@@ -124,8 +124,11 @@ typedef struct lh_phys_desc {
                             can (any 2D size); -1: never (one kernel per CG phase) */
   int32_t cg_tiles;      /* 0 (default): in 2D, where the band preconditioner's line passes
                             would leave SMs idle, both directions run as one kernel over
-                            16 x 16 node tiles (the same FP32 arithmetic, bitwise); -1:
-                            always one line pass per direction */
+                            16 x 16 node tiles, and M p (element apply and node gather) as
+                            another over the same tiles: the preconditioner output and
+                            M p are bitwise those of the line passes and the element /
+                            gather pair, only the CG dot products add their partial sums
+                            over another tiling; -1: one kernel per pass and phase */
 } lh_phys_desc;
 
 /* Velocity CG preconditioners.  With rho0 |J0| the same in every element (every
@@ -260,9 +263,11 @@ LH_API lh_status lh_mass_apply_v(lh_ctx* ctx, const double* in, double* out);
 LH_API lh_status lh_mass_solve_v(lh_ctx* ctx, const double* rhs, double* out,
                           int32_t* iters, double* relres);
 /* out = P^{-1} in (device pointers, N_V): one application of the velocity CG's
- * tensor-product preconditioner, the banded inverses of the 1D mass matrices
- * along every direction (an FP32 approximation of M_V^{-1} on the
- * non-essential components; essential entries of out are zero).
+ * tensor-product preconditioner along every direction, on the non-essential
+ * components (essential entries of out are zero): the 1D inverses truncated
+ * to a band in FP32 (TENSOR, an approximation of M_V^{-1}) or FP64
+ * (TENSOR64), or the exact inverse by banded Cholesky solves (EXACT).
+ * Launches lh_layout_info.precond_kernels kernels on the context's stream.
  * LH_EUNSUPPORTED if the context uses the Jacobi preconditioner. */
 LH_API lh_status lh_precond_apply(lh_ctx* ctx, const double* in, double* out);
 /* out = M_E^{-1} rhs (device pointers, N_E), block diagonal per element. */
