@@ -294,3 +294,47 @@ def test_gresho_quarter_turn_symmetry():
     assert vmax > 0.5
     assert np.abs(V[0][:, ::-1].T + V[1]).max() <= 1e-11 * vmax
     assert np.abs(V[1][:, ::-1].T - V[0]).max() <= 1e-11 * vmax
+
+
+def _element_density_and_radius(x, n):
+    """Per element of an n x n Q2 mesh of the unit square (rho0 = 1): density
+    as initial mass over the current area (polygon of the 8 boundary nodes),
+    and the radius of the element's centre node."""
+    nn = 2 * n + 1
+    X, Y = x[:nn * nn].reshape(nn, nn), x[nn * nn:].reshape(nn, nn)
+    ring = [(0, 0), (1, 0), (2, 0), (2, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+    rho, rc = np.zeros((n, n)), np.zeros((n, n))
+    for ey in range(n):
+        for ex in range(n):
+            px = np.array([X[2 * ey + j, 2 * ex + i] for i, j in ring])
+            py = np.array([Y[2 * ey + j, 2 * ex + i] for i, j in ring])
+            area = 0.5 * np.sum(px * np.roll(py, -1) - np.roll(px, -1) * py)
+            rho[ey, ex] = (1.0 / n) ** 2 / area
+            rc[ey, ex] = np.hypot(X[2 * ey + 1, 2 * ex + 1], Y[2 * ey + 1, 2 * ex + 1])
+    return rho, rc
+
+
+def test_sedov_shock_radius_matches_the_similarity_solution():
+    """The blast of energy 0.25 in the corner of the reflecting quarter domain
+    is the full-plane cylindrical blast of E = 1.  Sedov's similarity solution
+    puts its shock at R = xi0 (E t^2 / rho0)^(1/4), xi0 = 1.004 for gamma = 1.4
+    (textbook value, not from the paper): R(0.8) = 0.898.  On 16 x 16 Q2
+    elements the front (where the density falls half-way back from its peak,
+    along the wall) must lie within half an initial element width of it, and
+    the peak compression below the strong-shock limit (gamma+1)/(gamma-1) = 6."""
+    n = 16
+    o = _sedov(n)
+    v, e, x = o.init_state()
+    stats, _, st = o.run(0.8, v, e, x)
+    assert st == O.OK
+    rho, rc = _element_density_and_radius(x, n)
+    R = 1.004 * (1.0 * 0.8 ** 2 / 1.0) ** 0.25
+    row, r = rho[0], rc[0]                      # the elements along the wall y = 0
+    k = int(np.argmax(row))
+    assert 3.0 < row[k] < 6.0
+    half = 0.5 * (row[k] + 1.0)
+    j = next(i for i in range(k, n - 1) if row[i] >= half > row[i + 1])
+    front = r[j] + (row[j] - half) / (row[j] - row[j + 1]) * (r[j + 1] - r[j])
+    assert abs(front - R) <= 0.5 / n
+    # the unshocked gas ahead of the front is at rest at the initial density
+    assert abs(row[-1] - 1.0) < 0.05
