@@ -114,3 +114,20 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(lagh, "LIB_PATH", str(tmp_path / "missing" / "liblagh.so"))
     with pytest.raises(RuntimeError):
         lagh.load()
+
+
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++17")])
+def test_header_compiles_strictly_as_c_and_cpp(tmp_path, lang, std):
+    """The boundary header is plain C: it compiles as C99 and as C++ with
+    every warning an error, for callers outside this package."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no compiler")
+    src = tmp_path / ("use.c" if lang == "c" else "use.cpp")
+    src.write_text('#include "lagh.h"\n'
+                   "int main(void) { lh_phys_desc p; lh_default_phys(&p); return p.cg_maxit < 0; }\n")
+    subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                    os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use.o")],
+                   check=True)
