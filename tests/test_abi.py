@@ -131,3 +131,20 @@ def test_header_compiles_strictly_as_c_and_cpp(tmp_path, lang, std):
     subprocess.run([cc, std, "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
                     os.path.join(ROOT, "include"), "-c", str(src), "-o", str(tmp_path / "use.o")],
                    check=True)
+
+
+def test_library_c_exports_are_exactly_the_header_entry_points():
+    """Every exported C-linkage symbol of the library is an lh_* entry point of
+    include/lagh.h, and every one of those is exported (names from nm)."""
+    import shutil
+    import subprocess
+    from paper_2104_11404_gb300 import build
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("no nm")
+    path = build.build()
+    out = subprocess.run([nm, "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    names = [f[-1] for f in (l.split() for l in out.splitlines()) if len(f) >= 3]
+    c_names = sorted(n for n in names if not n.startswith("_Z"))
+    assert c_names == _declared()
