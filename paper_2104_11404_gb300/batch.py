@@ -5,13 +5,18 @@ import numpy as np
 import torch
 
 from . import lagh
-from .hydro import descriptors
+from .hydro import descriptors, precision_id
 
 
 class Batch:
     def __init__(self, cfgs, precision="mixed", stream=None, cg_rtol=None, cg_maxit=None,
                  tuning=None, phys_overrides=None):
         L = lagh
+        self.precision = precision_id(precision)
+        if tuning is not None:
+            unknown = set(tuning) - {"threads", "ctas_per_sm", "smem_lines", "qpt"}
+            if unknown:
+                raise KeyError("unknown tuning keys %s" % sorted(unknown))
         self.cfgs = [dict(c) for c in cfgs]
         meshes, physs = [], []
         disc = None
@@ -21,7 +26,6 @@ class Batch:
             physs.append(p)
             disc = disc or d
         self.n = len(self.cfgs)
-        self.precision = L.LH_MIXED if precision == "mixed" else L.LH_FP64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         tun = None
         if tuning is not None:

@@ -6,8 +6,18 @@ import torch
 from . import lagh
 
 
+def precision_id(precision):
+    """The lh_precision of "fp64" or "mixed" (anything else is an error)."""
+    ids = {"fp64": lagh.LH_FP64, "mixed": lagh.LH_MIXED}
+    if precision not in ids:
+        raise ValueError("precision must be 'fp64' or 'mixed', not %r" % (precision,))
+    return ids[precision]
+
+
 def descriptors(cfg, cg_rtol=None, cg_maxit=None, phys_overrides=None):
-    """(mesh, disc, phys) descriptors of a configuration dict."""
+    """(mesh, disc, phys) descriptors of a configuration dict.  phys_overrides
+    names fields of lh_phys_desc; an unknown name is an error (it would
+    otherwise be a Python attribute that never reaches the library)."""
     L = lagh
     mesh = L.lh_mesh_desc()
     mesh.dim = cfg["dim"]
@@ -30,7 +40,10 @@ def descriptors(cfg, cg_rtol=None, cg_maxit=None, phys_overrides=None):
         phys.cg_rtol = cg_rtol
     if cg_maxit is not None:
         phys.cg_maxit = cg_maxit
+    fields = {name for name, _ in L.lh_phys_desc._fields_}
     for k, v in (phys_overrides or {}).items():
+        if k not in fields:
+            raise KeyError("lh_phys_desc has no field %r" % (k,))
         setattr(phys, k, v)
     return mesh, disc, phys
 
@@ -40,8 +53,8 @@ class Hydro:
                  phys_overrides=None):
         L = lagh
         self.cfg = dict(cfg)
+        self.precision = precision_id(precision)
         mesh, disc, phys = descriptors(cfg, cg_rtol, cg_maxit, phys_overrides)
-        self.precision = L.LH_MIXED if precision == "mixed" else L.LH_FP64
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.ctx = L.lh_create(mesh, disc, phys, self.precision, self.stream.cuda_stream)
         self.layout = L.lh_layout(self.ctx)

@@ -148,3 +148,26 @@ def test_library_c_exports_are_exactly_the_header_entry_points():
     names = [f[-1] for f in (l.split() for l in out.splitlines()) if len(f) >= 3]
     c_names = sorted(n for n in names if not n.startswith("_Z"))
     assert c_names == _declared()
+
+
+def test_wrappers_reject_unknown_precision_overrides_and_tuning_keys():
+    """Misspelt options fail at once, before any device call (a ctypes struct
+    would otherwise take an unknown name as a plain Python attribute)."""
+    from paper_2104_11404_gb300 import lagh
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.batch import Batch
+    from paper_2104_11404_gb300.hydro import Hydro, descriptors, precision_id
+    cfg = W.CONFIGS["sedov2d_8"]
+    assert precision_id("fp64") == lagh.LH_FP64 and precision_id("mixed") == lagh.LH_MIXED
+    with pytest.raises(ValueError):
+        precision_id("fp32")
+    with pytest.raises(ValueError):
+        Hydro(cfg, precision="fp32")
+    _, _, phys = descriptors(cfg, phys_overrides={"cg_tiles": -1, "cg_cluster": 1})
+    assert phys.cg_tiles == -1 and phys.cg_cluster == 1
+    with pytest.raises(KeyError):
+        descriptors(cfg, phys_overrides={"cg_tile": -1})
+    with pytest.raises(KeyError):
+        Batch([cfg], tuning={"thread": 256})
+    with pytest.raises(ValueError):
+        Batch([cfg], precision="single")
