@@ -250,6 +250,11 @@ def test_total_mass_closed_form(dim, k, lo, hi):
     one_v, one_e = np.ones(o.nv), np.ones(o.ne)
     assert abs(one_v @ o.mass_apply_v(one_v) - dim * vol) <= 1e-13 * dim * vol
     assert abs(one_e @ o.mass_apply_e(one_e) - vol) <= 1e-13 * vol
+    # total energy of a uniform state: (|u|^2 / 2 + e) |Omega|
+    u = np.array([0.3, -1.1, 0.7][:dim])
+    v = np.repeat(u, o.nv // dim)
+    E = o.total_energy(v, 2.5 * one_e)
+    assert abs(E - (0.5 * u @ u + 2.5) * vol) <= 1e-13 * E
 
 
 def test_taylor_green_half_turn_symmetry():
