@@ -68,8 +68,11 @@ typedef enum lh_status {
 typedef enum lh_precision {
   LH_FP64 = 0,  /* every step in double precision */
   LH_MIXED = 1  /* quadrature-point stress and the element force matrix in
-                   FP32; positions, time integration, CG residuals and dot
-                   products, F.1 / F^T.v contractions and energy in FP64 */
+                   FP32; the F.1 row sums and F^T.v contractions of its FP32
+                   entries accumulated with error-free FP32 transformations
+                   (about 2^-48 relative) and widened once to FP64; positions,
+                   time integration, CG iterates, residuals and dot products
+                   and the energy in FP64 */
 } lh_precision;
 
 typedef enum lh_problem_id {
@@ -299,9 +302,9 @@ LH_API lh_status lh_run_to(lh_ctx* ctx, double t_final, int64_t max_steps,
  * allocate, this does not.
  * Computes what lh_force computes for F1 and dt_est, in FP64: F1 (device, N_V)
  * = F.1 of the state (v, e, x: device pointers, layouts as above) with the
- * essential components set to zero, and dt_est (host, may be NULL) = the
- * minimum of eq:adaptive-timestep over all quadrature points.  rho0 = 1 as in
- * every problem of Section 6.1.
+ * essential components set to zero, and dt_est (host, may be NULL) = the same
+ * time-step estimate lh_force returns.  rho0 = 1, as in every problem the
+ * library builds.
  * Working memory: one file-scope device array of 4 Mi doubles (32 MiB) that
  * every GPU which loads the library holds until the process exits.  A mesh
  * fits when 16 + n_e (1 + dim (k+1)^dim) <= 4194304 doubles (for example
@@ -313,9 +316,10 @@ LH_API lh_status lh_run_to(lh_ctx* ctx, double t_final, int64_t max_steps,
  * (the estimate and flag slots are reset at the start of each call); calls
  * whose work overlaps on the GPU (different streams, or threads) race on it:
  * order them on one stream.  No cudaMalloc, cudaFree or allocating library
- * routine is called.  Synchronizes stream when dt_est != NULL.  Errors:
- * LH_EINVAL / LH_EUNSUPPORTED (descriptors), LH_ETOOLARGE, LH_ECUDA,
- * LH_ETANGLED, LH_ENONFINITE. */
+ * routine is called.  Always synchronizes stream: the state checks (inverted
+ * element, non-finite value) are read back and reported by this call, whether
+ * or not dt_est is given.  Errors: LH_EINVAL / LH_EUNSUPPORTED (descriptors),
+ * LH_ETOOLARGE, LH_ECUDA, LH_ETANGLED, LH_ENONFINITE. */
 LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* disc,
                                  const lh_phys_desc* phys, const double* v, const double* e,
                                  const double* x, double* F1, double* dt_est, void* stream);
@@ -323,8 +327,9 @@ LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* d
 /* Self-check of the library's FP32 <-> FP64 conversions (a service of the
  * library, not a step of the paper; the FP32 paths convert on the integer
  * pipes because the FP64 pipe of this GPU is narrow): f_out[i] = in[i] rounded
- * to FP32 (nearest, ties to even; results below the normal FP32 range flush
- * to zero), d_out[i] = f_out[i] widened back to FP64 exactly, and (if
+ * to FP32 (nearest, ties to even, as the IEEE cast: results below the normal
+ * FP32 range round to the subnormal grid, below half the smallest subnormal to
+ * zero), d_out[i] = f_out[i] widened back to FP64 exactly, and (if
  * split_out != NULL) split_out[i] = hi + lo of the two-float split of in[i]
  * used by the FP32 energy accumulations (|in - split_out| <= 2^-48 |in| in
  * the normal range).  Device pointers, n entries, on stream (cudaStream_t as

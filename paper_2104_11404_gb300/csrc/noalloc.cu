@@ -123,16 +123,17 @@ extern "C" lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_des
   f.mode = kForceFull;
   if (launch_force(&c, f, s) != cudaSuccess) return LH_ECUDA;
   if (launch_gather(&c, F1E, F1, 1.0, 1, nullptr, s) != cudaSuccess) return LH_ECUDA;
-  if (dt_est) {
-    double hb[2];
-    if (cudaMemcpyAsync(hb, scratch, sizeof(hb), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-      return LH_ECUDA;
-    memcpy(dt_est, &hb[0], sizeof(double));
-    int fl;
-    memcpy(&fl, &hb[1], sizeof(int));
-    if (fl & kDevNonFinite) return LH_ENONFINITE;
-    if (fl & kDevTangled) return LH_ETANGLED;
-  }
+  // The estimate and the state-check flags are read back on every call: with
+  // no context there is no later call that could report a tangled or
+  // non-finite state, so the call always synchronizes.
+  double hb[2];
+  if (cudaMemcpyAsync(hb, scratch, sizeof(hb), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return LH_ECUDA;
+  if (dt_est) memcpy(dt_est, &hb[0], sizeof(double));
+  int fl;
+  memcpy(&fl, &hb[1], sizeof(int));
+  if (fl & kDevNonFinite) return LH_ENONFINITE;
+  if (fl & kDevTangled) return LH_ETANGLED;
   return LH_OK;
 }

@@ -1,0 +1,128 @@
+"""Checkpoint / resume and run-to-run determinism of the time loop.
+
+Every sum of the library adds its terms in a fixed order (node gathers in
+element order, block partial sums in block order, the CG dot products
+likewise) and the time-step minimum is an exact, order-free integer minimum,
+so a run is a deterministic function of its state and step-control state
+(t, dt).  Two identical runs must agree bit for bit, and a run cut in two
+through lh_get_state / lh_set_state, its second half in a fresh context, must
+equal the uncut run bit for bit (the RK2-average step of eq:RK2-avg and the
+step control of Section 2.2.3 carry no other state across steps)."""
+import numpy as np
+import pytest
+
+from paper_2104_11404_gb300 import workloads as W
+from tests._pair import gpu_for
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _sedov(dim, n, **over):
+    c = dict(dim=dim, n=tuple(n) + (1,) * (3 - len(n)), order=2, problem=W.SEDOV, gamma=1.4,
+             lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), visc=1, blast_energy=0.25)
+    c.update(over)
+    return c
+
+
+CASES = [
+    ("sedov2d_12", _sedov(2, (12, 12)), 0.3, 40),
+    ("sedov3d_5", _sedov(3, (5, 5, 5)), 0.15, 15),
+    ("tg2d_16", dict(W.scaled("tg2d_64", n=(16, 16))), 0.06, 25),
+    ("gresho2d_8_q3", dict(W.scaled("gresho2d_256", n=(8, 8))), 0.05, 12),
+]
+
+
+def _same(a, b):
+    return bool(torch.equal(a, b))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name,cfg,t_final,cut", CASES, ids=[c[0] for c in CASES])
+def test_resume_in_fresh_context_is_bit_identical(name, cfg, t_final, cut, precision):
+    whole = gpu_for(cfg, precision)
+    whole.init_state()
+    st_w = whole.run_to(t_final)
+    vw, ew, xw, tw, dtw = whole.get_state()
+    whole.close()
+    assert st_w["steps"] > cut
+
+    first = gpu_for(cfg, precision)
+    first.init_state()
+    st_a = first.run_to(t_final, max_steps=cut)
+    v, e, x, t, dt = first.get_state()
+    first.close()
+    assert st_a["steps"] == cut and 0.0 < t < t_final
+
+    second = gpu_for(cfg, precision)          # a fresh context: only the checkpoint carries over
+    second.set_state(v, e, x, t=t, dt=dt)
+    st_b = second.run_to(t_final)
+    vr, er, xr, tr, dtr = second.get_state()
+    second.close()
+
+    assert st_a["steps"] + st_b["steps"] == st_w["steps"]
+    assert st_a["rejects"] + st_b["rejects"] == st_w["rejects"]
+    assert tr == tw == t_final and dtr == dtw
+    assert _same(vr, vw) and _same(er, ew) and _same(xr, xw)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_two_identical_runs_agree_bitwise(precision):
+    cfg = _sedov(2, (16, 16))
+    out = []
+    for _ in range(2):
+        g = gpu_for(cfg, precision)
+        g.init_state()
+        st = g.run_to(0.25)
+        out.append((g.get_state(), st))
+        g.close()
+    (a, sa), (b, sb) = out
+    assert sa["steps"] == sb["steps"] and sa["rejects"] == sb["rejects"]
+    assert sa["cg_iters"] == sb["cg_iters"]
+    for u, w in zip(a[:3], b[:3]):
+        assert _same(u, w)
+    assert a[3] == b[3] and a[4] == b[4]
+
+
+def _batch_cfgs():
+    return [_sedov(2, (10, 10), gamma=1.4, blast_energy=0.25),
+            _sedov(2, (7, 9), gamma=1.6, blast_energy=0.7),
+            _sedov(2, (12, 8), gamma=1.33, blast_energy=0.1)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_resume_and_repeat_are_bit_identical(precision):
+    from paper_2104_11404_gb300.batch import Batch
+    cfgs = _batch_cfgs()
+    t_final, cut = 0.2, 20
+
+    def whole_run():
+        b = Batch(cfgs, precision=precision)
+        b.init_state()
+        b.run_to(t_final)
+        s = b.get_state()
+        q = b.query()
+        b.close()
+        return s, q
+
+    (vw, ew, xw), qw = whole_run()
+    (vw2, ew2, xw2), qw2 = whole_run()
+    assert _same(vw, vw2) and _same(ew, ew2) and _same(xw, xw2)
+    assert np.array_equal(qw["steps"], qw2["steps"])
+
+    b = Batch(cfgs, precision=precision)
+    b.init_state()
+    b.run_to(t_final, max_steps=cut)
+    v, e, x = b.get_state()
+    q = b.query()
+    b.close()
+    assert np.all(q["steps"] == cut) and np.all(q["t"] < t_final)
+    b2 = Batch(cfgs, precision=precision)
+    b2.set_state(v, e, x, q["t"], q["dt"])
+    b2.run_to(t_final)
+    vr, er, xr = b2.get_state()
+    qr = b2.query()
+    b2.close()
+    assert np.all(qr["t"] == t_final)
+    assert np.array_equal(qr["steps"] + cut, qw["steps"])
+    assert _same(vr, vw) and _same(er, ew) and _same(xr, xw)

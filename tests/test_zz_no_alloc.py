@@ -59,6 +59,65 @@ def test_force_static_matches_force_twice(dim, k, n):
         assert max_rel(F1o, host(F1)) <= 1e-12
 
 
+def test_force_static_reports_state_checks_without_an_estimate():
+    """With no context, no later call could report a bad state, so every call
+    reads back the flags: an inverted element gives LH_ETANGLED and a NaN
+    LH_ENONFINITE, with or without the estimate, and the next clean call on
+    the same stream returns LH_OK (the flag slot is cleared at each call)."""
+    from paper_2104_11404_gb300 import lagh
+    cfg = dict(dim=2, n=(4, 4, 1), order=2, problem=W.SEDOV, gamma=1.4, lo=(0.0, 0.0, 0.0),
+               hi=(1.0, 1.0, 1.0), visc=1, blast_energy=0.25)
+    o = oracle_for(cfg)
+    g = gpu_for(cfg)
+    mesh, disc, phys = _descs(g)
+    stream = torch.cuda.current_stream().cuda_stream
+    v, e, x = random_state(o, cfg, seed=43)
+    xt = x.copy()
+    xt[0], xt[2] = xt[2], xt[0]           # two corner nodes of element 0 swapped
+    en = e.copy()
+    en[5] = np.nan
+    F1 = torch.zeros(o.nv, dtype=torch.float64, device="cuda")
+    for want_dt in (True, False):
+        with pytest.raises(lagh.LaghError) as ei:
+            lagh.lh_force_static(mesh, disc, phys, dev(v), dev(e), dev(xt), F1, stream,
+                                 want_dt=want_dt)
+        assert ei.value.status == lagh.LH_ETANGLED
+        with pytest.raises(lagh.LaghError) as ei:
+            lagh.lh_force_static(mesh, disc, phys, dev(v), dev(en), dev(x), F1, stream,
+                                 want_dt=want_dt)
+        assert ei.value.status == lagh.LH_ENONFINITE
+        # a clean state right after, on the same stream: no leftover flag
+        F1.fill_(float("nan"))
+        lagh.lh_force_static(mesh, disc, phys, dev(v), dev(e), dev(x), F1, stream,
+                             want_dt=want_dt)
+        torch.cuda.synchronize()
+        F1o, _, _, _ = o.force(v, e, x)
+        assert max_rel(F1o, host(F1)) <= 1e-12
+
+
+def test_force_static_size_limit_is_exact():
+    """2D Q2 needs 16 + 19 n_e doubles: 470 x 469 elements fit the 4 Mi-double
+    array (n_e = 220,430), 471 x 469 (220,899) do not."""
+    from paper_2104_11404_gb300 import lagh
+    cfg = dict(dim=2, n=(470, 469, 1), order=2, problem=W.SEDOV, gamma=1.4,
+               lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0), visc=1, blast_energy=0.25)
+    g = gpu_for(cfg)
+    g.init_state()
+    v, e, x, _, _ = g.get_state()
+    mesh, disc, phys = _descs(g)
+    stream = torch.cuda.current_stream().cuda_stream
+    F1 = torch.full((g.nv,), float("nan"), dtype=torch.float64, device="cuda")
+    dt = lagh.lh_force_static(mesh, disc, phys, v, e, x, F1, stream)
+    F1_ref, _, dt_ref = g.force(v, e, x)
+    assert max_rel(host(F1_ref), host(F1)) <= 1e-12
+    assert abs(dt - dt_ref) <= 1e-12 * dt_ref
+    g.close()
+    mesh.nx = 471
+    with pytest.raises(lagh.LaghError) as ei:
+        lagh.lh_force_static(mesh, disc, phys, v, e, x, F1, stream)
+    assert ei.value.status == lagh.LH_ETOOLARGE
+
+
 def test_force_static_rejects_meshes_beyond_its_memory():
     from paper_2104_11404_gb300 import lagh
     cfg = dict(dim=3, n=(40, 40, 40), order=2, problem=W.SEDOV, gamma=1.4, lo=(0.0, 0.0, 0.0),
