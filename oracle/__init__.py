@@ -3,8 +3,8 @@
 TEST INFRASTRUCTURE ONLY.  The oracle is the correctness reference for the
 CUDA library: the tests, the smoke check and the CPU-baseline leg of the
 benchmark use it; the product path never does.  It follows the semi-discrete
-system of eq:fom, the RK2-average scheme of eq:RK2-avg and the step control of
-Section 2.2.3 of arXiv 2104.11404; the readings of what the paper leaves open
+system of eq:fom, the RK2-average scheme of eq:RK2-avg (or RK4, eq:RK4) and the step control
+of Section 2.2.3 of arXiv 2104.11404; the readings of what the paper leaves open
 are listed at the top of lagh_oracle.c.
 """
 import ctypes
@@ -14,7 +14,8 @@ import numpy as np
 
 from . import build as _build
 
-SEDOV, TAYLOR_GREEN, GRESHO, UNIFORM = 1, 2, 3, 4
+SEDOV, TAYLOR_GREEN, GRESHO, UNIFORM, TRIPLE_POINT = 1, 2, 3, 4, 5
+RK2AVG, RK4 = 0, 1
 OK, EINVAL, ETANGLED, ENONFINITE, EDTMIN, ECG = 0, 1, 4, 5, 6, 7
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -31,7 +32,7 @@ class _Config(ctypes.Structure):
         ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("gamma_dt", ctypes.c_double),
         ("cg_rtol", ctypes.c_double), ("cg_maxit", ctypes.c_int),
         ("dt_min_frac", ctypes.c_double), ("q1", ctypes.c_double), ("q2", ctypes.c_double),
-        ("source", ctypes.c_int),
+        ("source", ctypes.c_int), ("integrator", ctypes.c_int),
     ]
 
 
@@ -66,6 +67,8 @@ def lib():
         L.lho_mass_solve_e.argtypes = [ctypes.c_void_p, _dp, _dp]
         L.lho_step.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp, _dp,
                                ctypes.POINTER(ctypes.c_long)]
+        L.lho_step_rk4.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp, _dp,
+                                   ctypes.POINTER(ctypes.c_long)]
         L.lho_run.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_long,
                               _dp, _dp, _dp, _dp, ctypes.POINTER(_Stats), _dp, ctypes.c_long]
         L.lho_total_energy.restype = ctypes.c_double
@@ -194,6 +197,14 @@ class Oracle:
         its = ctypes.c_long()
         st = lib().lho_step(self._h, float(dt), _p(v), _p(e), _p(x), ctypes.byref(tau),
                             ctypes.byref(its))
+        return tau.value, its.value, st
+
+    def step_rk4(self, dt, v, e, x):
+        """One RK4 step in place; returns (tau, cg_iters, status)."""
+        tau = ctypes.c_double()
+        its = ctypes.c_long()
+        st = lib().lho_step_rk4(self._h, float(dt), _p(v), _p(e), _p(x), ctypes.byref(tau),
+                                ctypes.byref(its))
         return tau.value, its.value, st
 
     def run(self, t_final, v, e, x, t0=0.0, dt=0.0, max_steps=10 ** 9, log_cap=100000):

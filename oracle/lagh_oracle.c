@@ -36,7 +36,17 @@
  *  R11 Sound speed c_s = sqrt(max(0, gamma (gamma-1) e)).
  *  R12 Step control (Section 2.2.3): a step is redone with beta1 dt when
  *     dt >= tau; after an accepted step dt grows to beta2 dt when
- *     dt <= gamma tau.  tau is the minimum over both RK2-average stages.
+ *     dt <= gamma tau.  tau is the minimum over both RK2-average stages
+ *     (over all four stages of RK4).
+ *  R13 Triple point (Section 6.1.4): the three states (rho, p, gamma) are
+ *     constant in each element, the element's state decided by its initial
+ *     centre (x <= 1: rho 1, p 1, gamma 1.5; x > 1, y <= 1.5: rho 1, p 0.1,
+ *     gamma 1.4; x > 1, y > 1.5: rho 1/8, p 0.1, gamma 1.5).  On the box
+ *     [0,7] x [0,3] (x [0,1.5]) with n_x a multiple of 7 and n_y even the
+ *     interfaces lie on element faces and this is the pointwise definition.
+ *  R14 RK4 (eq:RK4, eq:RK4coeff) is applied to the combined right-hand side
+ *     f(S) = (-M_V^{-1} F(S).1, M_E^{-1} (F(S)^T v + source), v) of eq:fom,
+ *     each stage evaluating F, the source and F^T v at its own state.
  */
 #include "lagh_oracle.h"
 
@@ -264,7 +274,47 @@ static double sigma_min(int d, const double* J) {
 
 static double rho0_at(const lho_problem* P, const double* X) {
   (void)P; (void)X;
-  return 1.0; /* all problems of Section 6.1 used here start at rho = 1 */
+  return 1.0; /* every problem but the triple point starts at rho = 1 */
+}
+
+/* Initial centre of element el. */
+static void element_centre(const lho_problem* P, long el, double* Xc) {
+  long r = el;
+  for (int c = 0; c < P->dim; ++c) {
+    int ei = (int)(r % P->n[c]);
+    r /= P->n[c];
+    Xc[c] = P->cfg.lo[c] + (ei + 0.5) * P->h[c];
+  }
+}
+
+/* Triple point, reading R13: state of the element with initial centre Xc. */
+static void triple_state(const double* Xc, double* rho, double* p, double* gam) {
+  int left = Xc[0] <= 1.0, low = Xc[1] <= 1.5;
+  *rho = (left || low) ? 1.0 : 0.125;
+  *p = left ? 1.0 : 0.1;
+  *gam = (left || !low) ? 1.5 : 1.4;
+}
+
+/* rho_0 of element el at the initial point X. */
+static double rho0_el(const lho_problem* P, long el, const double* X) {
+  if (P->cfg.problem == LHO_TRIPLE_POINT) {
+    double Xc[3], rho, p, gam;
+    element_centre(P, el, Xc);
+    triple_state(Xc, &rho, &p, &gam);
+    return rho;
+  }
+  return rho0_at(P, X);
+}
+
+/* Adiabatic index of element el (eq:EOS; per material for the triple point). */
+static double gamma_el(const lho_problem* P, long el) {
+  if (P->cfg.problem == LHO_TRIPLE_POINT) {
+    double Xc[3], rho, p, gam;
+    element_centre(P, el, Xc);
+    triple_state(Xc, &rho, &p, &gam);
+    return gam;
+  }
+  return P->cfg.gamma;
 }
 
 /* Gresho (Section 6.1.1) azimuthal speed and pressure, reading R7. */
@@ -498,7 +548,7 @@ lho_problem* lho_create(const lho_config* cfg) {
       double Xq[3] = {0, 0, 0};
       for (int c = 0; c < d; ++c)
         for (int i = 0; i < P->nd1; ++i) Xq[c] += xl[c][i] * P->H[q * P->nd1 + i];
-      P->rho0detJ0[el * P->nqe + q] = rho0_at(P, Xq) * vol;
+      P->rho0detJ0[el * P->nqe + q] = rho0_el(P, el, Xq) * vol;
     }
   }
 
@@ -582,6 +632,13 @@ int lho_init_state(const lho_problem* P, double* v, double* e, double* x) {
         case LHO_UNIFORM:
           ev = P->cfg.e_uniform;
           break;
+        case LHO_TRIPLE_POINT: {
+          double Xc[3], rho, p, gam;
+          element_centre(P, el, Xc);
+          triple_state(Xc, &rho, &p, &gam);
+          ev = p / ((gam - 1.0) * rho);
+          break;
+        }
         default:
           ev = init_pressure(P, X) / ((P->cfg.gamma - 1.0) * rho0_at(P, X));
           break;
@@ -594,11 +651,10 @@ int lho_init_state(const lho_problem* P, double* v, double* e, double* x) {
 
 /* ------------------------------------------------- quadrature-point physics -- */
 
-int lho_qpoint(const lho_problem* P, const double* J, const double* gradv_ref,
-               double e_q, double rho0detJ0, double* sigma, double* tau,
-               double* mu_out) {
+static int qpoint_gamma(const lho_problem* P, double gam, const double* J,
+                        const double* gradv_ref, double e_q, double rho0detJ0,
+                        double* sigma, double* tau, double* mu_out) {
   int d = P->dim;
-  double gam = P->cfg.gamma;
   double detJ = det_d(d, J);
   if (!(detJ > 0.0)) {
     *tau = 0.0;
@@ -654,6 +710,12 @@ int lho_qpoint(const lho_problem* P, const double* J, const double* gradv_ref,
   return LHO_OK;
 }
 
+int lho_qpoint(const lho_problem* P, const double* J, const double* gradv_ref,
+               double e_q, double rho0detJ0, double* sigma, double* tau,
+               double* mu_out) {
+  return qpoint_gamma(P, P->cfg.gamma, J, gradv_ref, e_q, rho0detJ0, sigma, tau, mu_out);
+}
+
 /* ------------------------------------------------------------------ force -- */
 
 /* Dense F_K of one element; returns the minimum estimate over its points. */
@@ -673,6 +735,7 @@ static int element_force(const lho_problem* P, long el, const double* v,
   for (int r = 0; r < d * nd1 * nd2; ++r) FK[r] = 0.0;
   int status = LHO_OK;
   double tmin = INFINITY;
+  const double gam = gamma_el(P, el);
   for (int q = 0; q < P->nqe; ++q) {
     const double* dh = P->dH + (size_t)q * nd1 * d;
     double J[9], Gv[9];
@@ -689,7 +752,7 @@ static int element_force(const lho_problem* P, long el, const double* v,
     double eq = 0.0;
     for (int j = 0; j < nd2; ++j) eq += el2[j] * P->L[q * nd2 + j];
     double sigma[9], tau;
-    int st = lho_qpoint(P, J, Gv, eq, P->rho0detJ0[el * P->nqe + q], sigma, &tau, NULL);
+    int st = qpoint_gamma(P, gam, J, Gv, eq, P->rho0detJ0[el * P->nqe + q], sigma, &tau, NULL);
     if (st != LHO_OK) { status = st; tmin = 0.0; continue; }
     if (tau < tmin) tmin = tau;
     /* D = alpha_q sigma adj(J)^T */
@@ -1068,6 +1131,77 @@ int lho_step(const lho_problem* P, double dt, double* v, double* e, double* x,
   return st;
 }
 
+/* ----------------------------------------------------------------- RK4 -- */
+
+/* Right-hand side f(S) of eq:fom at the state (v, e, x), reading R14:
+ * dv = -M_V^{-1} F.1, de = M_E^{-1} (F^T v + source(x)), dx = v. */
+static int rate(const lho_problem* P, const double* v, const double* e, const double* x,
+                double* FK, double* F1, double* g, double* src, double* dv, double* de,
+                double* tau, long* its_total) {
+  long nv = P->nv, ne = P->ne;
+  int its;
+  int s = all_element_forces(P, v, e, x, FK, tau);
+  assemble_F1(P, FK, F1);
+  for (long i = 0; i < nv; ++i) F1[i] = -F1[i];
+  int cs = lho_mass_solve_v(P, F1, dv, &its, NULL);
+  *its_total += its;
+  apply_FT(P, FK, v, g);
+  lho_energy_source(P, x, src);
+  for (long i = 0; i < ne; ++i) g[i] += src[i];
+  lho_mass_solve_e(P, g, de);
+  return s != LHO_OK ? s : cs;
+}
+
+int lho_step_rk4(const lho_problem* P, double dt, double* v, double* e, double* x,
+                 double* tau_out, long* cg_iters) {
+  long nv = P->nv, ne = P->ne;
+  size_t blk = (size_t)P->dim * P->nd1 * P->nd2;
+  double* FK = (double*)malloc(sizeof(double) * blk * P->nelem);
+  double* F1 = (double*)malloc(sizeof(double) * nv);
+  double* g = (double*)malloc(sizeof(double) * ne);
+  double* src = (double*)malloc(sizeof(double) * ne);
+  double* kv[4]; double* ke[4]; double* kx[4];
+  for (int s = 0; s < 4; ++s) {
+    kv[s] = (double*)malloc(sizeof(double) * nv);
+    kx[s] = (double*)malloc(sizeof(double) * nv);
+    ke[s] = (double*)malloc(sizeof(double) * ne);
+  }
+  double* vs = (double*)malloc(sizeof(double) * nv);
+  double* es = (double*)malloc(sizeof(double) * ne);
+  double* xs = (double*)malloc(sizeof(double) * nv);
+  /* stage s is evaluated at S^n + c_s dt k_{s-1} (eq:RK4coeff) */
+  const double c[4] = {0.0, 0.5, 0.5, 1.0};
+  int st = LHO_OK;
+  long its = 0;
+  double tau = INFINITY;
+  for (int s = 0; s < 4; ++s) {
+    for (long i = 0; i < nv; ++i) {
+      vs[i] = s == 0 ? v[i] : v[i] + c[s] * dt * kv[s - 1][i];
+      xs[i] = s == 0 ? x[i] : x[i] + c[s] * dt * kx[s - 1][i];
+    }
+    for (long i = 0; i < ne; ++i) es[i] = s == 0 ? e[i] : e[i] + c[s] * dt * ke[s - 1][i];
+    double ts;
+    int r = rate(P, vs, es, xs, FK, F1, g, src, kv[s], ke[s], &ts, &its);
+    for (long i = 0; i < nv; ++i) kx[s][i] = vs[i];
+    if (ts < tau) tau = ts;
+    if (r != LHO_OK && st == LHO_OK) st = r;
+  }
+  /* S^{n+1} = S^n + dt/6 (k1 + 2 k2 + 2 k3 + k4)  (eq:RK4) */
+  for (long i = 0; i < nv; ++i) {
+    v[i] = v[i] + dt / 6.0 * (kv[0][i] + 2.0 * kv[1][i] + 2.0 * kv[2][i] + kv[3][i]);
+    x[i] = x[i] + dt / 6.0 * (kx[0][i] + 2.0 * kx[1][i] + 2.0 * kx[2][i] + kx[3][i]);
+  }
+  for (long i = 0; i < ne; ++i)
+    e[i] = e[i] + dt / 6.0 * (ke[0][i] + 2.0 * ke[1][i] + 2.0 * ke[2][i] + ke[3][i]);
+  *tau_out = tau;
+  if (cg_iters) *cg_iters = its;
+  if (st == LHO_OK && (!all_finite(nv, v) || !all_finite(ne, e) || !all_finite(nv, x)))
+    st = LHO_ENONFINITE;
+  for (int s = 0; s < 4; ++s) { free(kv[s]); free(kx[s]); free(ke[s]); }
+  free(FK); free(F1); free(g); free(src); free(vs); free(es); free(xs);
+  return st;
+}
+
 int lho_run(const lho_problem* P, double t0, double t_final, long max_steps,
             double* v, double* e, double* x, double* dt_io, lho_stats* stats,
             double* dt_log, long dt_log_cap) {
@@ -1095,7 +1229,8 @@ int lho_run(const lho_problem* P, double t0, double t_final, long max_steps,
     memcpy(es, e, sizeof(double) * ne);
     double tau;
     long its = 0;
-    int st = lho_step(P, dt_use, vs, es, xs, &tau, &its);
+    int st = P->cfg.integrator == LHO_RK4 ? lho_step_rk4(P, dt_use, vs, es, xs, &tau, &its)
+                                          : lho_step(P, dt_use, vs, es, xs, &tau, &its);
     S.cg_iters += its;
     if (st == LHO_ETANGLED) tau = 0.0;  /* a tangled stage forces a redo */
     else if (st != LHO_OK) { status = st; break; }

@@ -16,8 +16,8 @@
  *     block F_K[(i,c), j] = sum_q alpha_q phi_j(q) (sigma_q adj(J_q)^T
  *     grad_ref w_i(q))[c]   (quadrature form of  int_K sigma : grad w_(i,c) phi_j);
  *   - the ideal-gas EOS p = (gamma-1) rho e  (eq:EOS);
- *   - the RK2-average scheme (eq:RK2-avg) and the automatic time step control
- *     with the estimate of eq:adaptive-timestep.
+ *   - the RK2-average scheme (eq:RK2-avg), the RK4 scheme (eq:RK4) and the
+ *     automatic time step control with the estimate of eq:adaptive-timestep.
  *
  * Readings of points the paper leaves to its reference [dobrev2012high] (basis,
  * quadrature, artificial viscosity, h_min, initial dt, problem data) are
@@ -36,7 +36,14 @@ enum {
   LHO_SEDOV = 1,
   LHO_TAYLOR_GREEN = 2,
   LHO_GRESHO = 3,
-  LHO_UNIFORM = 4   /* test problem: uniform gas at rest (v = 0, e = e_uniform) */
+  LHO_UNIFORM = 4,  /* test problem: uniform gas at rest (v = 0, e = e_uniform) */
+  LHO_TRIPLE_POINT = 5  /* Section 6.1.4: two materials in three states (reading R13) */
+};
+
+/* Time integrators of Section 2.2. */
+enum {
+  LHO_RK2AVG = 0,   /* eq:RK2-avg */
+  LHO_RK4 = 1       /* eq:RK4 on the combined system (reading R14) */
 };
 
 /* Return codes. */
@@ -67,6 +74,7 @@ typedef struct {
   double dt_min_frac;    /* dt < dt_min_frac * t_final -> LHO_EDTMIN */
   double q1, q2;         /* linear / quadratic viscosity coefficients */
   int source;            /* manufactured energy source on/off (Taylor-Green) */
+  int integrator;        /* LHO_RK2AVG (default) or LHO_RK4, used by lho_run */
 } lho_config;
 
 typedef struct lho_problem lho_problem;
@@ -132,6 +140,11 @@ int lho_mass_solve_e(const lho_problem* P, const double* rhs, double* out);
  * tau = min of the estimate over both stages. */
 int lho_step(const lho_problem* P, double dt, double* v, double* e, double* x,
              double* tau, long* cg_iters);
+
+/* One RK4 step of size dt (eq:RK4, eq:RK4coeff), in place, no step control.
+ * tau = min of the estimate over the four stages. */
+int lho_step_rk4(const lho_problem* P, double dt, double* v, double* e, double* x,
+                 double* tau, long* cg_iters);
 
 /* Runs the automatic time step control of Section 2.2.3 from time t0 with
  * proposed step *dt (if *dt <= 0 the estimate of the state is used) to
