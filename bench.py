@@ -1,15 +1,25 @@
 """Benchmark: Lagrangian step DOF-updates/s of the full-order hydro step.
 
-Workload: the 2D Taylor-Green vortex of Section 6.1.3 on 64x64 Q2/Q1 elements
-(the workload the headline metric is quoted on), synthetic (problem initial
-conditions, no data).  One bench step = CHUNK accepted RK2-average time steps
-of the device-controlled time loop (lh_run_to).  value = (2 N_V + N_E) x
-accepted time steps / device time, for the mixed FP32/FP64 path; the FP64 path
-is measured the same way and reported beside it.
+Headline workload: the batched parameter sweep, 512 independent 2D
+point-blast instances (Section 6.1.2 problem; E0 ~ U[0.1, 1], gamma ~
+U[1.3, 1.67], n x n Q2/Q1 quads with n from {16, 24, 32, 48}; splitmix64 seed
+2104114040), mixed FP32/FP64, one persistent kernel per RK2-average stage,
+the two stage kernels of an attempt one CUDA graph, launch shape autotuned.
+One bench step = the whole sweep: every instance from its initial condition
+to t = 0.8 under its own step control (lh_batch_set_state of the initial
+packed state resident on the device, then lh_batch_run_to).
+value = sum over instances of (2 N_V + N_E) x accepted steps / device time.
+
+Beside it: the same sweep in FP64, the instance mix through the single-problem
+FP64 and mixed paths, the restricted (5% element sample) force, full runs of
+the single-problem workloads (2D blast 8x8 to 0.8, Taylor-Green 64x64 to 0.5,
+3D blast 32^3 to 0.6, Gresho 256^2 Q3 to 0.62) in FP64 and mixed, and the CPU
+oracle on a seeded subset of the sweep on all host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-Under torchrun every rank advances its own instance (independent replicas,
-weak scaling, no collective on the data path); rank 0 prints one JSON line.
+Under torchrun every rank advances its own copy of the sweep (independent
+replicas, weak scaling, no collective on the data path); rank 0 prints one
+JSON line.
 """
 import argparse
 import json
@@ -19,18 +29,22 @@ import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-CHUNK = 50           # accepted time steps per bench step
-WORKLOAD = "tg2d_64"
-BATCH_CHUNK = 20     # accepted time steps of every instance per batched bench step
-# DRAM read + write per launch of the preconditioner kernel on this workload,
-# from an ncu capture (cold caches); None until the current kernel is captured
-PASS_KERNEL_DRAM_BYTES = 437163  # cg_pass2d_kernel on tg2d_64: mean of 3 launches, 0 written
+METRIC = "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error"
+SWEEP_T_FINAL = 0.8
+SWEEP_WORKLOAD = ("batched sweep: 512 independent 2D point-blast instances, E0 U[0.1,1], gamma "
+                  "U[1.3,1.67], n x n Q2/Q1 quads with n from {16,24,32,48}, each from its initial "
+                  "condition to t = 0.8, splitmix64 seed 2104114040")
+# CPU oracle sample of the sweep: the first instances of the seeded list, on
+# every host core
+CPU_SUBSET_PER_CORE = 2
+# DRAM read + write per launch of the batched stage kernel from an ncu capture,
+# or None until the current kernel is captured
+STAGE_KERNEL_DRAM_BYTES = None
 
 
 def _dist():
@@ -51,7 +65,6 @@ def rank_reduce(x, op, world, device):
     red = torch.distributed.ReduceOp.MAX if op == "max" else torch.distributed.ReduceOp.SUM
     torch.distributed.all_reduce(t, op=red)
     return float(t.item())
-
 
 
 class Clocks:
@@ -143,264 +156,6 @@ def flops_per_element_force(dim, k, mixed):
     return 2 * (interp + eq + trans) + phys
 
 
-def _env_info():
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    return peaks
-
-
-def run_native(args):
-    import torch
-    from paper_2104_11404_gb300 import build as libbuild
-    from paper_2104_11404_gb300 import lagh
-    from paper_2104_11404_gb300 import workloads as W
-    from paper_2104_11404_gb300.hydro import Hydro
-
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1 and not torch.distributed.is_initialized():
-        torch.distributed.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
-    libbuild.build()
-    cfg = W.CONFIGS[WORKLOAD]
-    nv, ne, nel = W.sizes(cfg)
-    N = 2 * nv + ne
-    stream = torch.cuda.Stream()
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x):
-        return rank_reduce(x, "max", world, "cuda")
-
-    def sum_over_ranks(x):
-        return rank_reduce(x, "sum", world, "cuda")
-
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    def measure(precision):
-        with torch.cuda.stream(stream):
-            g = Hydro(cfg, precision=precision, stream=stream,
-                      phys_overrides={"direct_launch": 1} if args.direct_launch else None)
-            g.init_state()
-            for _ in range(args.warmup):
-                g.run_to(cfg["t_final"], max_steps=CHUNK)
-            torch.cuda.synchronize()
-            barrier()
-            torch.cuda.synchronize()
-            dev_ms, steps, cg, rejects = 0.0, 0, 0, 0
-            clk = Clocks(local)
-            clk.start()
-            t_wall = time.time()
-            for _ in range(args.steps):
-                flush.fill_(1.0)            # L2 flushed between timed steps
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                st = g.run_to(cfg["t_final"], max_steps=CHUNK)
-                e1.record(stream)
-                e1.synchronize()
-                dev_ms += e0.elapsed_time(e1)
-                steps += st["steps"]
-                cg += st["cg_iters"]
-                rejects += st["rejects"]
-            wall = time.time() - t_wall
-            clocks = clk.stop()
-            torch.cuda.synchronize()
-            barrier()
-            # end to end through the C ABI with pinned host buffers
-            hv = torch.empty(nv, dtype=torch.float64, pin_memory=True)
-            he = torch.empty(ne, dtype=torch.float64, pin_memory=True)
-            hx = torch.empty(nv, dtype=torch.float64, pin_memory=True)
-            lagh.lh_get_state(g.ctx, hv, he, hx)
-            e2e_ms, e2e_steps = 0.0, 0
-            for _ in range(max(1, args.steps // 2)):
-                flush.fill_(1.0)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                t_, dt_ = lagh.lh_get_state(g.ctx, None, None, None)
-                lagh.lh_set_state(g.ctx, hv, he, hx, t_, dt_)
-                st = g.run_to(cfg["t_final"], max_steps=CHUNK)
-                lagh.lh_get_state(g.ctx, hv, he, hx)
-                e1.record(stream)
-                e1.synchronize()
-                e2e_ms += e0.elapsed_time(e1)
-                e2e_steps += st["steps"]
-            # dominant kernel: the force evaluation over all elements, timed
-            # alone with events on the library stream
-            v, e, x, _, _ = g.get_state()
-            ids = torch.arange(nel, dtype=torch.int32, device="cuda")
-            F1 = torch.empty(nel * cfg["dim"] * (cfg["order"] + 1) ** cfg["dim"], dtype=torch.float64,
-                             device="cuda")
-            lagh.lh_force_sampled(g.ctx, ids, nel, v, e, x, F1, want_dt=False)
-            reps = 50
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                lagh.lh_force_sampled(g.ctx, ids, nel, v, e, x, F1, want_dt=False)
-            e1.record(stream)
-            e1.synchronize()
-            force_ms = e0.elapsed_time(e1) / reps
-            # the CG preconditioner passes (dominant by share in the launch list):
-            # one application = precond_kernels launches (the tile kernel, or
-            # one line pass per direction)
-            r = torch.randn(nv, dtype=torch.float64, device="cuda")
-            z = torch.empty_like(r)
-            lagh.lh_precond_apply(g.ctx, r, z)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(reps):
-                lagh.lh_precond_apply(g.ctx, r, z)
-            e1.record(stream)
-            e1.synchronize()
-            pk = g.layout.precond_kernels
-            pass_ms = e0.elapsed_time(e1) / reps / pk
-            g.close()
-        return dict(dev_ms=max_over_ranks(dev_ms), steps=sum_over_ranks(steps), cg=cg,
-                    rejects=rejects, wall=wall, clocks=clocks, e2e_ms=max_over_ranks(e2e_ms),
-                    e2e_steps=sum_over_ranks(e2e_steps), force_ms=force_ms, pass_ms=pass_ms,
-                    pass_kernels=pk)
-
-    res = {p: measure(p) for p in ("mixed", "fp64")}
-    batched = None if args.no_batch else measure_batched(args, stream, flush, max_over_ranks,
-                                                         sum_over_ranks)
-    others = None if (args.no_configs or rank != 0) else measure_configs(stream)
-    if rank != 0:
-        return None
-    m, f = res["mixed"], res["fp64"]
-    value = N * m["steps"] / (m["dev_ms"] * 1e-3)
-    value64 = N * f["steps"] / (f["dev_ms"] * 1e-3)
-    peaks = _env_info()
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12      # TFLOP/s, unit counts x clock
-    fp64_peak = 1.25                                      # TFLOP/s, GB300 nominal FP64 rate
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    # one launch reads its input and writes its output (N_V doubles each): a
-    # line pass along one direction, or the tile kernel's whole application
-    pass_bytes = 16.0 * nv
-    pass_kernel = ("cg_pass2d_kernel (CG band preconditioner, both directions on 16x16 node tiles)"
-                   if m["pass_kernels"] == 1 else "cg_pass_kernel (CG band preconditioner line pass)")
-    fl = flops_per_element_force(cfg["dim"], cfg["order"], True) * nel
-    achieved = fl / (m["force_ms"] * 1e-3) / 1e12
-    fl64 = flops_per_element_force(cfg["dim"], cfg["order"], False) * nel
-    achieved64 = fl64 / (f["force_ms"] * 1e-3) / 1e12
-    # kernels launched per attempt: per stage force, node gather, the initial
-    # preconditioner application (pk kernels), v/x update and energy update,
-    # and per CG iteration M p (element apply + node gather, one tile kernel
-    # where the preconditioner is the tile kernel, pk == 1) and a
-    # preconditioner application (the CG update rides on it); then control
-    # and commit
-    pk = m["pass_kernels"]
-    per_it = (1 if pk == 1 else 2) + pk
-    attempts = m["steps"] + m["rejects"]
-    # every solve launches at least its kUnrolled = 3 iterations (a converged
-    # solve's later ones return at once)
-    launches = attempts * (2 * (4 + pk) + 2) + max(m["cg"], 3 * 2 * attempts) * per_it
-    line = {
-        "metric": "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error",
-        "value": value,
-        "unit": "DOF-updates/s",
-        "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": m["dev_ms"] / args.steps,
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        "dtype": "f32+f64",
-        "data": "synthetic",
-        "config": {"workload": "2D Taylor-Green vortex 64x64 Q2/Q1, AV on, CFL 0.1, mixed FP32/FP64",
-                   "dofs_per_instance": N, "time_steps_per_bench_step": CHUNK,
-                   "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": "replicas" if world > 1 else "single"},
-        "fp64": {"value": value64, "ms_per_step": f["dev_ms"] / args.steps,
-                 "speedup_mixed_over_fp64": value / value64},
-        "roofline": {"bound": "hbm", "kernel": pass_kernel,
-                     "achieved": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9, "peak": hbm_peak,
-                     "unit": "GB/s", "frac": pass_bytes / (m["pass_ms"] * 1e-3) / 1e9 / hbm_peak,
-                     # DRAM read + write per launch of this kernel from an ncu capture on
-                     # this workload (cold caches; reset to None when the kernel changes)
-                     "traffic": PASS_KERNEL_DRAM_BYTES if m["pass_kernels"] == 1 else None, "launch_us": m["pass_ms"] * 1e3,
-                     "algorithmic_bytes": pass_bytes,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                     "force_kernel": {"bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                                      "launch_us": m["force_ms"] * 1e3,
-                                      "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock",
-                                      "fp64_path": {"achieved": achieved64, "peak": fp64_peak,
-                                                    "frac": achieved64 / fp64_peak,
-                                                    "launch_us": f["force_ms"] * 1e3}}},
-        "e2e": {"value": N * m["e2e_steps"] / (m["e2e_ms"] * 1e-3), "unit": "DOF-updates/s",
-                "h2d_bytes_per_step": N * 8, "d2h_bytes_per_step": N * 8},
-        "gpu_launches": int(launches),
-        "clocks": m["clocks"],
-    }
-    if others is not None:
-        line["configs"] = others
-    if batched is not None:
-        batched["config"] = ("512 independent 2D point-blast instances, E0 U[0.1,1], gamma "
-                             "U[1.3,1.67], n x n quads with n from {16,24,32,48}, Q2/Q1, mixed, "
-                             "splitmix64 seed 2104114040")
-        line["batched"] = batched
-    if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, bounded_seconds=12.0)
-    return line
-
-
-CONFIG_WINDOW = {"sedov2d_8": 50, "sedov3d_32": 10, "gresho2d_256": 20}
-
-
-def measure_configs(stream):
-    """The other workloads, each through the single-problem path in both
-    precisions: a window of accepted steps from the initial state after three
-    warm-up steps, device time, throughput, the mixed state's relative L2
-    difference from the FP64 state after the same steps, and the mixed
-    total-energy drift (the problems without an energy source)."""
-    import numpy as np
-    import torch
-    from paper_2104_11404_gb300 import workloads as W
-    from paper_2104_11404_gb300.hydro import Hydro
-    out = {}
-    for name, nsteps in CONFIG_WINDOW.items():
-        cfg = W.CONFIGS[name]
-        res = {}
-        states = {}
-        for prec in ("fp64", "mixed"):
-            with torch.cuda.stream(stream):
-                g = Hydro(cfg, precision=prec, stream=stream)
-                g.init_state()
-                E0 = g.total_energy()
-                g.run_to(cfg["t_final"], max_steps=3)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                st = g.run_to(cfg["t_final"], max_steps=nsteps)
-                e1.record(stream)
-                e1.synchronize()
-                ms = e0.elapsed_time(e1)
-                N = 2 * g.nv + g.ne
-                v, e, x, t, _ = g.get_state()
-                states[prec] = (v.cpu().numpy(), e.cpu().numpy(), t)
-                res[prec] = {"value": N * st["steps"] / (ms * 1e-3), "ms_per_step": ms / st["steps"],
-                             "cg_iters_per_step": st["cg_iters"] / max(1, st["steps"]),
-                             "energy_drift": abs(g.total_energy() - E0) / abs(E0)}
-                g.close()
-        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(a), 1e-300))
-        out[name] = {"dofs": int(N), "time_steps": nsteps + 3,
-                     "fp64": res["fp64"], "mixed": res["mixed"],
-                     "speedup_mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
-                     "mixed_vs_fp64_rel_l2": {"v": rel(states["fp64"][0], states["mixed"][0]),
-                                              "e": rel(states["fp64"][1], states["mixed"][1]),
-                                              "t_diff": abs(states["fp64"][2] - states["mixed"][2])}}
-    return out
-
-
 def batch_fp64_flops(cfgs):
     """Algorithmic FP64 flops of one attempt (two stages) of the batched
     mixed step, summed over instances, with n_e elements and N_V velocity
@@ -418,200 +173,517 @@ def batch_fp64_flops(cfgs):
     return 2 * tot
 
 
-def measure_batched(args, stream, flush, max_over_ranks, sum_over_ranks, sizes_fp64=True):
-    """The 512-instance point-blast sweep (mixed), one bench step = BATCH_CHUNK
-    accepted time steps of every instance (lh_batch_run_to); plus the restricted
-    force on a seeded 5% element sample of every instance, and the plain
-    single-problem paths on the same instance mix for the speed-up."""
+def stage_words(nv, ne, nqp, cg_iters):
+    """Algorithmic FP64 words moved by one RK stage of one problem (the
+    per-stage table of the measurement plan): force in 2 N_V + N_E + N_qp,
+    force out N_V, CG I (6 N_V + N_qp), F^T v and e update 2 N_V + 2 N_E +
+    N_qp, x update 3 N_V."""
+    return (2 * nv + ne + nqp) + nv + cg_iters * (6 * nv + nqp) + (2 * nv + 2 * ne + nqp) + 3 * nv
+
+
+def batch_attempt_bytes(cfgs, cg_iters_per_solve):
+    tot = 0.0
+    for c in cfgs:
+        n = c["n"][0] * c["n"][1]
+        nv = 2 * (2 * c["n"][0] + 1) * (2 * c["n"][1] + 1)
+        tot += 2 * stage_words(nv, 4 * n, 16 * n, cg_iters_per_solve)
+    return 8.0 * tot
+
+
+def _measured_hbm():
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        if p.get("hbm_gbs"):
+            return float(p["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except Exception:
+        pass
+    return 6800.0, "profiling recipe fallback 6.8 TB/s (of fallback)"
+
+
+# ------------------------------------------------------------ CPU oracle pool
+
+def _oracle_worker(conn, cfgs, t_final):
+    """Host worker (spawned): holds a fixed subset of sweep instances in the
+    CPU oracle and advances each by the requested accepted steps, restarting
+    an instance from its initial condition when it reaches t_final."""
+    sys.path.insert(0, ROOT)
+    import oracle as O
+    from tests._pair import oracle_for
+    insts = []
+    for c in cfgs:
+        o = oracle_for(c)
+        v, e, x = o.init_state()
+        insts.append([o, v, e, x, 0.0, 0.0])
+    conn.send(("ready", len(insts)))
+    while True:
+        msg = conn.recv()
+        if msg[0] == "stop":
+            break
+        steps_each = msg[1]
+        upd = 0
+        for rec in insts:
+            o, v, e, x, t, dt = rec
+            if t >= t_final:
+                v, e, x = o.init_state()
+                t, dt = 0.0, 0.0
+                rec[1:4] = [v, e, x]
+            st, _, s = o.run(t_final, v, e, x, t0=t, dt=dt, max_steps=steps_each)
+            if s != O.OK:
+                raise RuntimeError("oracle status %d" % s)
+            rec[4], rec[5] = st["t"], st["dt"]
+            upd += (2 * o.nv + o.ne) * st["steps"]
+        conn.send(("done", upd))
+    conn.close()
+
+
+class OraclePool:
+    """The CPU oracle, as it stands, on every host core: one spawned process
+    per core, each owning a fixed share of the instances."""
+
+    def __init__(self, cfgs, nproc, t_final):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for w in range(nproc):
+            mine = cfgs[w::nproc]
+            if not mine:
+                continue
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, mine, t_final), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            c.recv()
+        self.cores = len(self.procs)
+
+    def advance(self, steps_each):
+        t0 = time.time()
+        for c in self.conns:
+            c.send(("adv", steps_each))
+        upd = sum(c.recv()[1] for c in self.conns)
+        return upd, time.time() - t0
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def _cpu_subset(nproc):
+    from paper_2104_11404_gb300 import workloads as W
+    cfgs = W.batch_instances()
+    return cfgs[:CPU_SUBSET_PER_CORE * nproc]
+
+
+def cpu_baseline_sweep(bounded_seconds=15.0, steps_each=3):
+    """The oracle on a bounded sample of the sweep on all host cores: the
+    first 2 x nproc instances of the seeded list advanced from their initial
+    conditions in rounds of `steps_each` accepted steps each, until about
+    `bounded_seconds` of wall time."""
+    nproc = os.cpu_count() or 1
+    sub = _cpu_subset(nproc)
+    pool = OraclePool(sub, nproc, SWEEP_T_FINAL)
+    try:
+        upd, el, rounds = 0, 0.0, 0
+        while el < bounded_seconds and rounds < 200:
+            u, dt = pool.advance(steps_each)
+            upd += u
+            el += dt
+            rounds += 1
+    finally:
+        pool.close()
+    return {"value": upd / el, "unit": "DOF-updates/s", "cores": pool.cores, "kind": "oracle",
+            "sample": "%d instances of the seeded sweep (the first 2 per core; sizes %s), %d rounds "
+                      "of %d accepted RK2-average steps each from t = 0, single-thread FP64 C "
+                      "oracle per process, %d spawned processes on %d host cores, %.1f s" %
+                      (len(sub), sorted({c["n"][0] for c in sub}), rounds, steps_each,
+                       pool.cores, nproc, el),
+            "nproc": nproc}
+
+
+# ------------------------------------------------------------ native arm
+
+def measure_sweep(args, stream, flush, precision, reduce_max, reduce_sum, steps=None,
+                  warmup=None, autotune=True, e2e=True):
+    """Timed whole sweeps of the batch (see the module docstring)."""
     import numpy as np
     import torch
     from paper_2104_11404_gb300 import lagh
     from paper_2104_11404_gb300 import workloads as W
     from paper_2104_11404_gb300.batch import Batch
-    from paper_2104_11404_gb300.hydro import Hydro
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     cfgs = W.batch_instances()
     out = {}
     with torch.cuda.stream(stream):
-        b = Batch(cfgs, precision="mixed", stream=stream)
+        b = Batch(cfgs, precision=precision, stream=stream)
         b.init_state()
-        t0 = time.time()
-        tune = b.autotune(reps=2)
-        tune_s = time.time() - t0
+        v0, e0, x0 = b.get_state()           # initial packed state, resident on the device
+        zeros = np.zeros(b.n)
+        tune, tune_s = None, 0.0
+        if autotune:
+            t0 = time.time()
+            tune = b.autotune(reps=2)
+            tune_s = time.time() - t0
         dofs = b.dofs()
-        for _ in range(args.warmup):
-            b.run_to(0.8, max_steps=BATCH_CHUNK)
+        for _ in range(warmup):
+            b.set_state(v0, e0, x0, zeros, zeros)
+            b.run_to(SWEEP_T_FINAL)
         torch.cuda.synchronize()
-        dev_ms, dof_upd, steps, rejects, launches = 0.0, 0, 0, 0, 0
-        for _ in range(args.steps):
+        dev_ms, upd, nsteps, rejects, graphs, cg = 0.0, 0, 0, 0, 0, 0
+        clk = Clocks(torch.cuda.current_device())
+        clk.start()
+        for _ in range(steps):
             flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = b.run_to(0.8, max_steps=BATCH_CHUNK)
-            e1.record(stream)
-            e1.synchronize()
-            dev_ms += e0.elapsed_time(e1)
-            dof_upd += st["dof_updates"]
-            steps += st["steps"]
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            b.set_state(v0, e0, x0, zeros, zeros)
+            st = b.run_to(SWEEP_T_FINAL)
+            ev1.record(stream)
+            ev1.synchronize()
+            dev_ms += ev0.elapsed_time(ev1)
+            upd += st["dof_updates"]
+            nsteps += st["steps"]
             rejects += st["rejects"]
-            launches += st["graph_launches"]
-        # replicas: every rank advances its own copy of the sweep
-        value = sum_over_ranks(dof_upd) / (max_over_ranks(dev_ms) * 1e-3)
-        value_rank = dof_upd / (dev_ms * 1e-3)
-        attempt_ms = dev_ms / max(1, launches)
-        # end to end: pinned host state in, run, state out
-        hv = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
-        he = torch.empty(b.ne, dtype=torch.float64, pin_memory=True)
-        hx = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
-        lagh.lh_batch_get_state(b.b, hv, he, hx)
+            graphs += st["graph_launches"]
+            cg += st["cg_iters"]
+        clocks = clk.stop()
         q = b.query()
-        e2e_ms, e2e_upd = 0.0, 0
-        for _ in range(max(1, args.steps // 2)):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            b.set_state(hv, he, hx, q["t"], q["dt"])
-            st = b.run_to(0.8, max_steps=BATCH_CHUNK)
-            lagh.lh_batch_get_state(b.b, hv, he, hx)
-            q = b.query()
-            e1.record(stream)
-            e1.synchronize()
-            e2e_ms += e0.elapsed_time(e1)
-            e2e_upd += st["dof_updates"]
-        # restricted force on 5% of every instance's elements
-        lists = [W.element_sample(c["n"][0] * c["n"][1], frac=0.05, stream=i)
-                 for i, c in enumerate(cfgs)]
-        nsamp = int(sum(len(l) for l in lists))
-        b.force_sampled(lists)
-        reps = 20
-        F1, _, off, _ = b.force_sampled(lists)
-        d_off = torch.from_numpy(off).to("cuda")
-        d_ids = torch.from_numpy(np.concatenate(lists).astype(np.int32)).to("cuda")
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            lagh.lh_batch_force_sampled(b.b, d_off, d_ids, F1)
-        e1.record(stream)
-        e1.synchronize()
-        hr_ms = e0.elapsed_time(e1) / reps
+        assert np.all(q["t"] == SWEEP_T_FINAL) and np.all(q["status"] == 0)
         E_all = b.total_energy()
+        fv, fe, _ = b.get_state()
+        final = (fv.cpu().numpy(), fe.cpu().numpy(), b.off_v.copy(), b.off_e.copy())
+        attempts = nsteps + rejects
+        out = {"dev_ms": dev_ms, "dof_updates": upd, "steps": nsteps, "rejects": rejects,
+               "graph_launches": graphs, "attempt_ms": dev_ms / max(1, graphs),
+               "cg_iters_per_solve": cg / max(1, 2 * attempts), "tuning": tune,
+               "autotune_s": tune_s, "clocks": clocks, "energy_min": float(np.min(E_all)),
+               "value": reduce_sum(upd) / (reduce_max(dev_ms) * 1e-3),
+               "value_rank": upd / (dev_ms * 1e-3), "dofs_total": int(dofs.sum()),
+               "instances": len(cfgs), "sweeps": steps,
+               "steps_per_instance_mean": nsteps / steps / len(cfgs), "final_state": final}
+        if e2e:
+            # end to end through the C ABI: pinned host initial state in, the
+            # whole sweep, the final state out to pinned host memory
+            hv = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
+            he = torch.empty(b.ne, dtype=torch.float64, pin_memory=True)
+            hx = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
+            hv.copy_(v0)
+            he.copy_(e0)
+            hx.copy_(x0)
+            ov = torch.empty_like(hv).pin_memory()
+            oe = torch.empty_like(he).pin_memory()
+            ox = torch.empty_like(hx).pin_memory()
+            e2e_ms, e2e_upd = 0.0, 0
+            for _ in range(max(1, steps // 2)):
+                flush.fill_(1.0)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                b.set_state(hv, he, hx, zeros, zeros)
+                st = b.run_to(SWEEP_T_FINAL)
+                lagh.lh_batch_get_state(b.b, ov, oe, ox)
+                ev1.record(stream)
+                ev1.synchronize()
+                e2e_ms += ev0.elapsed_time(ev1)
+                e2e_upd += st["dof_updates"]
+            out["e2e"] = {"value": reduce_sum(e2e_upd) / (reduce_max(e2e_ms) * 1e-3),
+                          "unit": "DOF-updates/s",
+                          "h2d_bytes_per_step": 8 * (2 * b.nv + b.ne) + 16 * b.n,
+                          "d2h_bytes_per_step": 8 * (2 * b.nv + b.ne)}
         b.close()
-        # plain single-problem paths (one context per problem) on the same mix
-        rates = {}
-        if sizes_fp64:
-            for prec in ("fp64", "mixed"):
-                for n in W.BATCH_SIZES:
-                    c = dict(cfgs[0], n=(n, n, 1), gamma=1.4, blast_energy=0.5)
-                    g = Hydro(c, precision=prec, stream=stream)
-                    g.init_state()
-                    g.run_to(0.8, max_steps=3)
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    stg = g.run_to(0.8, max_steps=BATCH_CHUNK)
-                    e1.record(stream)
-                    e1.synchronize()
-                    N = 2 * g.nv + g.ne
-                    rates[(prec, n)] = N * stg["steps"] / (e0.elapsed_time(e1) * 1e-3)
-                    g.close()
-    per_inst_steps = steps / len(cfgs)
-    out = {"value": value, "unit": "DOF-updates/s", "instances": len(cfgs),
-           "dofs_total": int(dofs.sum()), "ms_per_step": dev_ms / args.steps,
-           "time_steps_per_bench_step": BATCH_CHUNK, "accepted_steps": steps, "rejects": rejects,
-           "attempt_graphs": launches, "attempt_ms": attempt_ms, "tuning": tune,
-           "autotune_s": tune_s,
-           "e2e": {"value": e2e_upd / (e2e_ms * 1e-3), "unit": "DOF-updates/s",
-                   "h2d_bytes_per_step": 8 * (2 * b.nv + b.ne) + 16 * len(cfgs),
-                   "d2h_bytes_per_step": 8 * (2 * b.nv + b.ne)},
-           "hyper_reduced_force": {"sampled_elements": nsamp, "launch_us": hr_ms * 1e3,
-                                   "elements_per_s": nsamp / (hr_ms * 1e-3),
-                                   "sample": "ceil(0.05 n_e) elements per instance, seeded "
-                                             "Fisher-Yates, sorted"},
-           "energy_min": float(np.min(E_all))}
-    fl = batch_fp64_flops(cfgs)
-    out["roofline"] = {"bound": "alu", "kernel": "batch_stage_kernel (both stages of an attempt)",
-                       "achieved": fl / (attempt_ms * 1e-3) / 1e12, "peak": 1.25,
-                       "unit": "TFLOP/s (FP64)",
-                       "frac": fl / (attempt_ms * 1e-3) / 1e12 / 1.25,
-                       "algorithmic_fp64_flops_per_attempt": fl,
-                       "peak_source": "GB300 nominal FP64 rate (1.25 TFLOP/s)"}
-    if rates:
-        # time the same accepted steps would take through one context per problem
-        def seq_time(prec):
-            return sum(dofs[i] * per_inst_steps / rates[(prec, c["n"][0])] for i, c in enumerate(cfgs))
-        out["single_problem_fp64"] = {"value": dofs.sum() * per_inst_steps / seq_time("fp64"),
-                                      "rates_by_size": {str(n): rates[("fp64", n)] for n in W.BATCH_SIZES}}
-        out["single_problem_mixed"] = {"value": dofs.sum() * per_inst_steps / seq_time("mixed"),
-                                       "rates_by_size": {str(n): rates[("mixed", n)] for n in W.BATCH_SIZES}}
-        out["speedup_over_fp64_single_problem"] = value_rank / out["single_problem_fp64"]["value"]
-        out["speedup_over_mixed_single_problem"] = value_rank / out["single_problem_mixed"]["value"]
     return out
 
 
-def cpu_baseline(args, bounded_seconds=12.0, steps=None):
-    """The oracle as it stands (single thread, FP64) on a bounded sample of the
-    same workload: accepted time steps from the initial state."""
-    import oracle as O
+def measure_hyper_reduced(stream):
+    """Restricted force (Section 3.3) on a seeded 5% element sample of every
+    sweep instance, timed alone."""
+    import numpy as np
+    import torch
+    from paper_2104_11404_gb300 import lagh
     from paper_2104_11404_gb300 import workloads as W
-    cfg = W.CONFIGS[WORKLOAD]
-    o = O.Oracle(dim=cfg["dim"], nx=cfg["n"][0], ny=cfg["n"][1], nz=cfg["n"][2],
-                 lo=list(cfg["lo"]), hi=list(cfg["hi"]), order=cfg["order"], problem=cfg["problem"],
-                 gamma=cfg["gamma"], visc=cfg["visc"], source=cfg.get("source", 1),
-                 cfl=cfg.get("cfl", 0.5))
-    v, e, x = o.init_state()
-    N = o.nv * 2 + o.ne
-    total, t0 = 0, time.time()
-    dt = 0.0
-    while time.time() - t0 < bounded_seconds and (steps is None or total < steps):
-        stats, log, st = o.run(cfg["t_final"], v, e, x, dt=dt, max_steps=5)
-        dt = stats["dt"]
-        total += stats["steps"]
-    el = time.time() - t0
-    return {"value": N * total / el, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-            "sample": "%d accepted RK2-average steps of the 64x64 Taylor-Green workload from t = 0, "
-                      "single-thread FP64 C oracle, %.1f s" % (total, el)}
+    from paper_2104_11404_gb300.batch import Batch
+    cfgs = W.batch_instances()
+    with torch.cuda.stream(stream):
+        b = Batch(cfgs, precision="mixed", stream=stream)
+        b.init_state()
+        b.run_to(0.1)
+        lists = [W.element_sample(c["n"][0] * c["n"][1], frac=0.05, stream=i)
+                 for i, c in enumerate(cfgs)]
+        nsamp = int(sum(len(l) for l in lists))
+        F1, _, off, _ = b.force_sampled(lists)
+        d_off = torch.from_numpy(off).to("cuda")
+        d_ids = torch.from_numpy(np.concatenate(lists).astype(np.int32)).to("cuda")
+        reps = 20
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            lagh.lh_batch_force_sampled(b.b, d_off, d_ids, F1)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1) / reps
+        b.close()
+    return {"sampled_elements": nsamp, "launch_us": ms * 1e3, "elements_per_s": nsamp / (ms * 1e-3),
+            "sample": "ceil(0.05 n_e) elements per instance, seeded Fisher-Yates, sorted"}
+
+
+def measure_single_sizes(stream, nsteps=20):
+    """The sweep's mesh sizes through the plain single-problem path (one
+    context per problem), FP64 and mixed: DOF-updates/s over a window."""
+    import torch
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.hydro import Hydro
+    cfg0 = W.batch_instances()[0]
+    rates = {}
+    with torch.cuda.stream(stream):
+        for prec in ("fp64", "mixed"):
+            for n in W.BATCH_SIZES:
+                c = dict(cfg0, n=(n, n, 1), gamma=1.4, blast_energy=0.5)
+                g = Hydro(c, precision=prec, stream=stream)
+                g.init_state()
+                g.run_to(0.8, max_steps=3)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                st = g.run_to(0.8, max_steps=nsteps)
+                ev1.record(stream)
+                ev1.synchronize()
+                rates[(prec, n)] = (2 * g.nv + g.ne) * st["steps"] / (ev0.elapsed_time(ev1) * 1e-3)
+                g.close()
+    return rates
+
+
+FULL_RUNS = ("sedov2d_8", "tg2d_64", "sedov3d_32", "gresho2d_256")
+
+
+def _tg_exact_error(g, v, x):
+    """Relative L2 (nodal) error of the velocity against the steady exact 2D
+    Taylor-Green field, evaluated at the final node positions."""
+    import numpy as np
+    nn = g.nv // 2
+    X, Y = x[:nn], x[nn:]
+    ve = np.concatenate([np.sin(np.pi * X) * np.cos(np.pi * Y), -np.cos(np.pi * X) * np.sin(np.pi * Y)])
+    return float(np.linalg.norm(v - ve) / np.linalg.norm(ve))
+
+
+def measure_full_runs(stream):
+    """Every single-problem workload from its initial condition to its final
+    time, FP64 and mixed: device time of the time loop, steps, throughput,
+    energy drift, the mixed state's relative L2 difference from the FP64 state
+    at the final time (eq:relerrors), and for Taylor-Green the error against
+    the exact solution."""
+    import numpy as np
+    import torch
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.hydro import Hydro
+    out = {}
+    for name in FULL_RUNS:
+        cfg = W.CONFIGS[name]
+        res, states = {}, {}
+        for prec in ("fp64", "mixed"):
+            with torch.cuda.stream(stream):
+                g = Hydro(cfg, precision=prec, stream=stream)
+                g.init_state()
+                E0 = g.total_energy()
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                st = g.run_to(cfg["t_final"])
+                ev1.record(stream)
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1)
+                N = 2 * g.nv + g.ne
+                v, e, x, t, _ = g.get_state()
+                v, e, x = v.cpu().numpy(), e.cpu().numpy(), x.cpu().numpy()
+                states[prec] = (v, e, x)
+                r = {"value": N * st["steps"] / (ms * 1e-3), "run_s": ms * 1e-3,
+                     "ms_per_step": ms / max(1, st["steps"]), "steps": st["steps"],
+                     "rejects": st["rejects"], "t": t,
+                     "cg_iters_per_solve": st["cg_iters"] / max(1, 2 * (st["steps"] + st["rejects"]))}
+                if not cfg.get("source", 0) or cfg["problem"] != W.TAYLOR_GREEN:
+                    r["energy_drift"] = abs(g.total_energy() - E0) / abs(E0)
+                if cfg["problem"] == W.TAYLOR_GREEN:
+                    r["velocity_error_vs_exact"] = _tg_exact_error(g, v, x)
+                res[prec] = r
+                g.close()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(a), 1e-300))
+        out[name] = {"dofs": int(N), "t_final": cfg["t_final"], "fp64": res["fp64"],
+                     "mixed": res["mixed"],
+                     "speedup_mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+                     "mixed_vs_fp64_rel_l2_at_t_final": {
+                         "v": rel(states["fp64"][0], states["mixed"][0]),
+                         "e": rel(states["fp64"][1], states["mixed"][1]),
+                         "x": rel(states["fp64"][2], states["mixed"][2])}}
+    return out
+
+
+def run_native(args):
+    import torch
+    from paper_2104_11404_gb300 import build as libbuild
+    from paper_2104_11404_gb300 import peaks as peaks_mod
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1 and not torch.distributed.is_initialized():
+        torch.distributed.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    libbuild.build()
+    stream = torch.cuda.Stream()
+
+    def reduce_max(x):
+        return rank_reduce(x, "max", world, "cuda")
+
+    def reduce_sum(x):
+        return rank_reduce(x, "sum", world, "cuda")
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    pk = peaks_mod.measure(stream)
+    hbm_peak, hbm_src = _measured_hbm()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sw = measure_sweep(args, stream, flush, "mixed", reduce_max, reduce_sum)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        return None
+    from paper_2104_11404_gb300 import workloads as W
+    cfgs = W.batch_instances()
+    extra = not args.quick
+    sw64 = measure_sweep(args, stream, flush, "fp64", lambda x: x, lambda x: x, steps=1, warmup=1,
+                         autotune=True, e2e=False) if extra else None
+    rates = measure_single_sizes(stream) if extra else None
+    hr = measure_hyper_reduced(stream) if extra else None
+    full = measure_full_runs(stream) if (extra and not args.no_configs) else None
+
+    value = sw["value"]
+    fl = batch_fp64_flops(cfgs)
+    att_ms = sw["attempt_ms"]
+    achieved = fl / (att_ms * 1e-3) / 1e12
+    abytes = batch_attempt_bytes(cfgs, sw["cg_iters_per_solve"])
+    kernels_per_graph = 2
+    launches = sw["graph_launches"] * kernels_per_graph + 2 * args.steps  # + estimate, begin
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "DOF-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": sw["dev_ms"] / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": SWEEP_WORKLOAD, "instances": sw["instances"],
+                   "dofs_total": sw["dofs_total"], "precision": "mixed FP32/FP64",
+                   "step": "one whole sweep (every instance from t = 0 to t = 0.8)",
+                   "steps_per_instance_mean": sw["steps_per_instance_mean"],
+                   "l2": "flushed between timed steps (256 MB write); the packed state and "
+                         "per-CTA scratch exceed L2",
+                   "tuning": sw["tuning"], "autotune_s": sw["autotune_s"],
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "alu", "kernel": "batch_stage_kernel (both stage kernels of an attempt)",
+                     "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s (FP64)",
+                     "frac": achieved / pk["fp64_tflops"], "traffic": STAGE_KERNEL_DRAM_BYTES,
+                     "algorithmic_fp64_flops_per_attempt": fl, "attempt_us": att_ms * 1e3,
+                     "peak_source": "FP64 FMA probe measured in this run (lh_peak_probe, of measured)",
+                     "hbm_view": {"algorithmic_bytes_per_attempt": abytes,
+                                  "achieved": abytes / (att_ms * 1e-3) / 1e9, "peak": hbm_peak,
+                                  "unit": "GB/s", "frac": abytes / (att_ms * 1e-3) / 1e9 / hbm_peak,
+                                  "peak_source": hbm_src,
+                                  "cg_iters_per_solve": sw["cg_iters_per_solve"]}},
+        "e2e": sw["e2e"],
+        "gpu_launches": int(launches),
+        "clocks": sw["clocks"],
+        "measured_peaks": {"fp64_tflops": pk["fp64_tflops"], "fp32_tflops": pk["fp32_tflops"],
+                           "hbm_gbs": hbm_peak},
+        "sweep": {"accepted_steps": sw["steps"], "rejects": sw["rejects"],
+                  "attempt_graphs": sw["graph_launches"], "energy_min": sw["energy_min"]},
+    }
+    if sw64 is not None:
+        v64 = sw64["value_rank"]
+        line["batched_fp64"] = {"value": v64, "ms_per_sweep": sw64["dev_ms"] / sw64["sweeps"],
+                                "tuning": sw64["tuning"],
+                                "speedup_mixed_over_fp64_batched": sw["value_rank"] / v64}
+        # accuracy of the mixed sweep at the final time against the FP64 sweep:
+        # relative L2 difference per instance (eq:relerrors), the worst instance
+        import numpy as np
+        mv, me, ov, oe = sw["final_state"]
+        fv, fe, _, _ = sw64["final_state"]
+        worst = {"v": 0.0, "e": 0.0}
+        for i in range(len(cfgs)):
+            for key, a, b_, off in (("v", fv, mv, ov), ("e", fe, me, oe)):
+                ref = a[off[i]:off[i + 1]]
+                d = np.linalg.norm(b_[off[i]:off[i + 1]] - ref) / max(np.linalg.norm(ref), 1e-300)
+                worst[key] = max(worst[key], float(d))
+        line["batched_fp64"]["mixed_vs_fp64_rel_l2_at_t_final_worst_instance"] = worst
+    if rates is not None:
+        import numpy as np
+        dofs = np.array([2 * 2 * (2 * c["n"][0] + 1) * (2 * c["n"][1] + 1) + 4 * c["n"][0] * c["n"][1]
+                         for c in cfgs], dtype=np.float64)
+        share = dofs / dofs.sum()
+
+        def mix_rate(prec):  # the same DOF-updates through one context per problem
+            return 1.0 / sum(share[i] / rates[(prec, c["n"][0])] for i, c in enumerate(cfgs))
+        line["single_problem"] = {
+            "fp64": {"value": mix_rate("fp64"),
+                     "rates_by_size": {str(n): rates[("fp64", n)] for n in W.BATCH_SIZES}},
+            "mixed": {"value": mix_rate("mixed"),
+                      "rates_by_size": {str(n): rates[("mixed", n)] for n in W.BATCH_SIZES}},
+            "speedup_batched_mixed_over_fp64_single_problem": sw["value_rank"] / mix_rate("fp64"),
+            "speedup_batched_mixed_over_mixed_single_problem": sw["value_rank"] / mix_rate("mixed")}
+    if hr is not None:
+        line["hyper_reduced_force"] = hr
+    if full is not None:
+        line["full_runs"] = full
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sweep()
+    return line
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle timed on the host cores, each bench step a
-    bounded sample (CHUNK_REF accepted time steps) of the same workload."""
+    """Reference arm: the CPU oracle, as it stands, on the host cores, on the
+    headline workload: each bench step advances the same seeded subset of
+    sweep instances (2 per core, one spawned process per core) by 2 accepted
+    RK2-average steps each."""
     world, rank, local = _dist()
     if rank != 0:
         return None
     import oracle as O
-    from paper_2104_11404_gb300 import workloads as W
     O.lib()
-    cfg = W.CONFIGS[WORKLOAD]
-    o = O.Oracle(dim=cfg["dim"], nx=cfg["n"][0], ny=cfg["n"][1], nz=cfg["n"][2],
-                 lo=list(cfg["lo"]), hi=list(cfg["hi"]), order=cfg["order"], problem=cfg["problem"],
-                 gamma=cfg["gamma"], visc=cfg["visc"], source=cfg.get("source", 1),
-                 cfl=cfg.get("cfl", 0.5))
-    v, e, x = o.init_state()
-    N = 2 * o.nv + o.ne
-    chunk = 5
-    dt = 0.0
-    for _ in range(args.warmup):
-        stats, _, _ = o.run(cfg["t_final"], v, e, x, dt=dt, max_steps=chunk)
-        dt = stats["dt"]
-    t0 = time.time()
-    total = 0
-    for _ in range(args.steps):
-        stats, _, _ = o.run(cfg["t_final"], v, e, x, dt=dt, max_steps=chunk)
-        dt = stats["dt"]
-        total += stats["steps"]
-    el = time.time() - t0
-    value = N * total / el
-    return {"metric": "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error",
-            "value": value, "unit": "DOF-updates/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
-            "config": {"workload": "2D Taylor-Green vortex 64x64 Q2/Q1, AV on, CFL 0.1",
-                       "dofs_per_instance": N, "time_steps_per_bench_step": chunk},
-            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d bench steps of %d accepted time steps" % (args.steps, chunk)},
+    nproc = os.cpu_count() or 1
+    sub = _cpu_subset(nproc)
+    pool = OraclePool(sub, nproc, SWEEP_T_FINAL)
+    chunk = 2
+    try:
+        for _ in range(args.warmup):
+            pool.advance(chunk)
+        upd, el = 0, 0.0
+        for _ in range(args.steps):
+            u, dt = pool.advance(chunk)
+            upd += u
+            el += dt
+    finally:
+        pool.close()
+    value = upd / el
+    sample = ("%d instances of the seeded sweep (the first 2 per core), %d accepted RK2-average "
+              "steps each per bench step, %d spawned oracle processes" % (len(sub), chunk, pool.cores))
+    return {"metric": METRIC, "value": value, "unit": "DOF-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": SWEEP_WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "DOF-updates/s", "cores": pool.cores,
+                             "kind": "oracle", "sample": sample, "nproc": nproc},
             "e2e": {"value": value, "unit": "DOF-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -619,17 +691,16 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched sweep")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the other workloads (2D blast 8x8, 3D blast 32^3, Gresho 256^2 Q3)")
-    ap.add_argument("--direct-launch", action="store_true",
-                    help="launch the step's kernels one by one instead of one CUDA graph per "
-                         "attempt (kernel profilers cannot see kernels inside graphs with "
-                         "conditional nodes)")
+                    help="skip the full single-problem runs (2D blast 8x8, Taylor-Green 64x64, "
+                         "3D blast 32^3, Gresho 256^2 Q3)")
+    ap.add_argument("--quick", action="store_true",
+                    help="the headline sweep only (no FP64 sweep, single-problem rates, "
+                         "restricted force or full runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

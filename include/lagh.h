@@ -227,7 +227,12 @@ LH_API lh_status lh_layout(const lh_ctx* ctx, lh_layout_info* info);
  * step size for estimation by the next step. */
 LH_API lh_status lh_init_state(lh_ctx* ctx);
 /* Copies the state in (host or device pointers, N_V / N_E / N_V doubles).
- * dt <= 0 asks the next step for a fresh estimate. */
+ * dt <= 0 asks the next step for a fresh estimate.  With (v, e, x, t, dt)
+ * from lh_get_state, the run continues exactly as it would have without the
+ * round trip (bit for bit in FP64).  The mixed path also recomputes here its
+ * reference pressure, (gamma - 1) times the smallest e of the state given (0
+ * if negative), so a resumed mixed run with a positive background pressure
+ * rounds its FP32 stress differently and agrees to FP32 rounding. */
 LH_API lh_status lh_set_state(lh_ctx* ctx, const double* v, const double* e,
                        const double* x, double t, double dt);
 /* Copies the state out (host or device pointers; any may be NULL) and
@@ -336,6 +341,19 @@ LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* d
  * void*).  Errors: LH_EINVAL, LH_ECUDA. */
 LH_API lh_status lh_check_conversions(const double* in, int64_t n, float* f_out, double* d_out,
                                       double* split_out, void* stream);
+
+/* Peak arithmetic-rate probe (a measurement service of the library, not a
+ * step of the paper): launches one kernel on stream (cudaStream_t as void*)
+ * in which every thread runs eight independent chains of iters fused
+ * multiply-adds, FP64 if fp64 != 0, else FP32, over 8 blocks of 256 threads
+ * per SM.  sink: device memory of at least (8 x SM count) doubles that the
+ * kernel may write (it never does in practice).  *flops (host, may be NULL)
+ * = the floating-point operations of the launch (2 per FMA).  The caller
+ * times the launch (for example with CUDA events on stream); flops / time is
+ * the FP64 or FP32 rate that the library's ALU-bound kernels are quoted
+ * against.  Errors: LH_EINVAL (iters < 1 or > 2^40, sink NULL), LH_ECUDA. */
+LH_API lh_status lh_peak_probe(int32_t fp64, int64_t iters, void* sink, void* stream,
+                               double* flops);
 
 /* ---------------------------------------------------------------------------
  * Batched form: n independent instances of the time step, each on its own

@@ -28,7 +28,7 @@ API_NAMES = [
     "lh_batch_layout", "lh_batch_init_state", "lh_batch_set_state", "lh_batch_get_state",
     "lh_batch_query", "lh_batch_run_to", "lh_batch_step_fixed", "lh_batch_total_energy",
     "lh_batch_force_sampled", "lh_batch_autotune", "lh_batch_tuning_get",
-    "lh_check_conversions",
+    "lh_check_conversions", "lh_peak_probe",
 ]
 
 
@@ -146,6 +146,8 @@ def load():
     L.lh_batch_autotune.argtypes = [_vp, ctypes.c_int32, P(lh_batch_tuning)]
     L.lh_batch_tuning_get.argtypes = [_vp, P(lh_batch_tuning)]
     L.lh_check_conversions.argtypes = [_dp, ctypes.c_int64, _vp, _dp, _dp, _vp]
+    L.lh_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp,
+                                ctypes.POINTER(ctypes.c_double)]
     for name in API_NAMES:
         if name not in ("lh_default_phys", "lh_status_string", "lh_last_error",
                         "lh_batch_last_error"):
@@ -402,3 +404,13 @@ def lh_check_conversions(inp, f_out, d_out, split_out=None, stream=None):
                                      _ptr(split_out), stream)
     if st != LH_OK:
         raise LaghError(st, "lh_check_conversions failed")
+
+
+def lh_peak_probe(fp64, iters, sink, stream=None):
+    """Launches the FMA-rate probe kernel on stream; returns the flops of the
+    launch (the caller times it)."""
+    fl = ctypes.c_double()
+    st = load().lh_peak_probe(1 if fp64 else 0, int(iters), _ptr(sink), stream, ctypes.byref(fl))
+    if st != LH_OK:
+        raise LaghError(st, "lh_peak_probe failed")
+    return fl.value
