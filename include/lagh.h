@@ -80,8 +80,23 @@ typedef enum lh_problem_id {
   LH_TAYLOR_GREEN = 2,  /* Taylor-Green vortex, Section 6.1.3 (2D: with its
                            manufactured energy source) */
   LH_GRESHO = 3,        /* Gresho vortex, Section 6.1.1 */
-  LH_UNIFORM = 4        /* uniform gas at rest (tests) */
+  LH_UNIFORM = 4,       /* uniform gas at rest (tests) */
+  LH_TRIPLE_POINT = 5   /* triple point, Section 6.1.4: two materials in three
+                           states, rho0, p and gamma constant per element and
+                           decided by the element's initial centre (x <= 1:
+                           1, 1, 1.5; x > 1, y <= 1.5: 1, 0.1, 1.4; x > 1,
+                           y > 1.5: 1/8, 0.1, 1.5), on the box [0,7] x [0,3]
+                           (x [0,1.5]); gamma of lh_phys_desc is not used */
 } lh_problem_id;
+
+/* Time integrators of Section 2.2. */
+enum {
+  LH_RK2AVG = 0,  /* RK2-average, eq:RK2-avg (exact discrete energy balance) */
+  LH_RK4 = 1      /* classical RK4 (eq:RK4, eq:RK4coeff) on the combined system
+                     f(S) = (-M_V^{-1} F(S).1, M_E^{-1} (F(S)^T v + source), v),
+                     every stage at its own state; the estimate is the minimum
+                     over the four stages */
+};
 
 /* Cartesian box [lo, hi] split into nx x ny (x nz) equal elements. */
 typedef struct lh_mesh_desc {
@@ -132,6 +147,8 @@ typedef struct lh_phys_desc {
                             M p are bitwise those of the line passes and the element /
                             gather pair, only the CG dot products add their partial sums
                             over another tiling; -1: one kernel per pass and phase */
+  int32_t integrator;    /* LH_RK2AVG (default) or LH_RK4; the batched form runs
+                            RK2-average only */
 } lh_phys_desc;
 
 /* Velocity CG preconditioners.  With rho0 |J0| the same in every element (every

@@ -376,7 +376,11 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
     }
     const lh_phys_desc& p = phys[i];
     if (!(p.gamma > 1.0)) return fail(LH_EINVAL, "gamma must exceed 1");
-    if (p.problem < LH_SEDOV || p.problem > LH_UNIFORM) return fail(LH_EINVAL, "unknown problem");
+    if (p.problem < LH_SEDOV || p.problem > LH_TRIPLE_POINT) return fail(LH_EINVAL, "unknown problem");
+    if (p.problem == LH_TRIPLE_POINT)
+      return fail(LH_EUNSUPPORTED, "the batched form runs single-material problems (rho0 = 1)");
+    if (p.integrator != LH_RK2AVG)
+      return fail(LH_EUNSUPPORTED, "the batched form runs the RK2-average integrator");
     if (!(p.cg_rtol > 0.0) || p.cg_maxit < 1) return fail(LH_EINVAL, "bad CG settings");
     BInst& I = b->inst[i];
     memset(&I, 0, sizeof(I));

@@ -32,6 +32,7 @@ static cudaError_t launch_force_t(const lh_ctx* c, const ForceArgs& fa, cudaStre
   prm.ph = c->ph;
   prm.b = c->basis;
   prm.a = fa;
+  prm.a.gammaE = c->a.gammaE;
   prm.rho0K = c->a.rho0K;
   int64_t blocks = (fa.nslots + F::EPB - 1) / F::EPB;
   return launch_k(c->use_pdl != 0, kern, dim3((unsigned)blocks), dim3(F::NT), F::BYTES, s, prm);

@@ -350,8 +350,10 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
       const T rho0K = from_double<T>(prm.rho0K[el]);
       if (A.mode == kForceFull) {
         const T pref = (MIXED && A.p_ref != nullptr) ? from_double<T>(*A.p_ref) : T(0);
-        flags |= qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, prm.ph, J0i, tab<T>(g.ell0, g.ell0f),
-                                        T(1) / T(K), pref, sigma, tau);
+        const T gam = A.gammaE != nullptr ? from_double<T>(A.gammaE[el])
+                                          : pconst<T>(prm.ph.gamma, prm.ph.gammaf);
+        flags |= qpoint_physics<T, DIM>(J, Gv, e_q, rho0K, gam, prm.ph, J0i,
+                                        tab<T>(g.ell0, g.ell0f), T(1) / T(K), pref, sigma, tau);
         const double tq_d = to_double(tau);
         tau_q = tq_d < tau_q ? tq_d : tau_q;
       } else {
@@ -843,7 +845,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
                                             int64_t el0) {
   using F = EL<DIM, K, MIXED, NTT>;
   constexpr int P = F::P, NQ = F::NQ, ND1 = F::ND1, ND2 = F::ND2, NQD = F::NQD;
-  const double coef = A.frac * (A.ctl != nullptr ? A.ctl->dt_use : A.dt);
+  const double coef = A.rate ? A.frac : A.frac * (A.ctl != nullptr ? A.ctl->dt_use : A.dt);
   // mixed path: F^T w of the reference pressure -p_ref I, in FP64
   const double pref = (MIXED && A.p_ref != nullptr && A.x != nullptr) ? *A.p_ref : 0.0;
   unsigned char* sp = smem;
@@ -972,7 +974,7 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
         if (A.srcE) rhs += A.srcE[el * ND2 + l];
         s = fma(Mi[j * ND2 + l], rhs, s);
       }
-      A.e_out[el * ND2 + j] = fma(crs[0], s, A.e_base[el * ND2 + j]);
+      A.e_out[el * ND2 + j] = A.rate ? crs[0] * s : fma(crs[0], s, A.e_base[el * ND2 + j]);
     }
   team_sync<NQD>();  // the team reuses its element area in the next tile
 }

@@ -127,6 +127,8 @@ struct Arrays {
   double *D;                    // FP64 path: stress weights [nelem][dim*dim][nqe]
   float *FK;                    // mixed path: element force matrices [nelem][dim*nd1][nd2]
   double *srcE;                 // energy source [N_E]
+  double *gammaE;               // adiabatic index per element (NULL: the constant one)
+  double *Kv, *Kx, *Ke, *erate; // RK4: weighted stage sums of dv/dt, dx/dt, de/dt; de/dt
   double *rho0K;                // rho0 |J0| per element
   double *rho0Kinv;             // its reciprocal
   double *dinv;                 // 1 / diag(M_s) per node
@@ -198,6 +200,9 @@ lh_status make_geom(const lh_mesh_desc* mesh, const lh_disc_desc* disc, Geom* g,
 // Initial condition of the problem at the nodes (host arrays, resized).
 void initial_state(const Geom& g, const lh_phys_desc& ph, std::vector<double>& v,
                    std::vector<double>& e, std::vector<double>& x);
+// Triple point (Section 6.1.4): density, pressure and adiabatic index of
+// element el, by its initial centre.
+void triple_point_state(const Geom& g, int64_t el, double* rho, double* p, double* gam);
 // Banded Cholesky factor of the assembled 1D reference mass matrix of nel
 // elements (var = 1: without its two end nodes): L[i][m] = L_{i,i-m}, m <= k.
 void banded_cholesky_1d(const Basis1D& b, int k, int nel, int var, std::vector<double>& L);
@@ -220,6 +225,7 @@ struct ForceArgs {
   int* status;
   const Ctl* ctl;     // if non-NULL and ctl->done, the kernel returns at once
   const double* p_ref;  // device scalar: mixed stress is sigma + p_ref I
+  const double* gammaE; // adiabatic index per element (NULL: Phys::gamma); set by the launcher
   int mode;           // 0: full physics; 1: only the reference pressure -p_ref I (FP64)
   int accumulate;     // add to F1E / FTvE instead of overwriting
 };
@@ -246,6 +252,7 @@ struct EnergyArgs {
   double* e_out;
   double frac;
   double dt;
+  int rate;              // 1: e_out = frac M_E^{-1} (F^T w + src) (no dt, e_base unused)
   const Ctl* ctl;
   const double* rho0Kinv;  // 1 / (rho0 |J0|) per element (NULL: divide)
 };

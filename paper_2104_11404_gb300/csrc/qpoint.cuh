@@ -167,14 +167,14 @@ __device__ __forceinline__ float pconst<float>(double, float f) { return f; }
 // Stress and time-step estimate at one point.  J, Gv: reference gradients
 // (row = component, column = reference direction).  p_ref: a constant
 // reference pressure taken out of the returned stress (sigma + p_ref I is
-// returned; the caller accounts for -p_ref I separately).  Returns the flags
-// kDevTangled / kDevNonFinite (then sigma = 0 and tau = 0).
+// returned; the caller accounts for -p_ref I separately).  gam: the adiabatic
+// index of the element (eq:EOS).  Returns the flags kDevTangled /
+// kDevNonFinite (then sigma = 0 and tau = 0).
 template <typename T, int DIM>
 __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&Gv)[DIM][DIM],
-                                              T e_q, T rho0K, const Phys& ph,
+                                              T e_q, T rho0K, T gam, const Phys& ph,
                                               const T (&J0inv)[DIM], T ell0, T kinv, T p_ref,
                                               T (&sigma)[DIM][DIM], T& tau) {
-  const T gam = pconst<T>(ph.gamma, ph.gammaf);
   T detJ = det_of<T, DIM>(J);
   for (int c = 0; c < DIM; ++c)
     for (int n = 0; n < DIM; ++n) sigma[c][n] = T(0);

@@ -309,7 +309,7 @@ static void free_all(lh_ctx* c) {
   double** dptrs[] = {&c->a.v, &c->a.e, &c->a.x, &c->a.vh, &c->a.eh, &c->a.xh, &c->a.vn,
                       &c->a.en, &c->a.xn, &c->a.vbar, &c->a.F1E, &c->a.rhs, &c->a.acc,
                       &c->a.r, &c->a.r2, &c->a.z, &c->a.p, &c->a.Ap, &c->a.ApE, &c->a.D,
-                      &c->a.srcE,
+                      &c->a.srcE, &c->a.gammaE, &c->a.Kv, &c->a.Kx, &c->a.Ke, &c->a.erate,
                       &c->a.rho0K, &c->a.rho0Kinv, &c->a.dinv, &c->a.partials, &c->a.tmpE, &c->a.tmpV,
                       &c->a.aux};
   for (double** p : dptrs)
@@ -375,8 +375,10 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     if (gs != LH_OK) return fail(gs, why);
   }
   if (!(phys->gamma > 1.0)) return fail(LH_EINVAL, "gamma must exceed 1");
-  if (phys->problem < LH_SEDOV || phys->problem > LH_UNIFORM)
+  if (phys->problem < LH_SEDOV || phys->problem > LH_TRIPLE_POINT)
     return fail(LH_EINVAL, "unknown problem");
+  if (phys->integrator != LH_RK2AVG && phys->integrator != LH_RK4)
+    return fail(LH_EINVAL, "unknown integrator");
   if (!(phys->cg_rtol > 0.0) || phys->cg_maxit < 1) return fail(LH_EINVAL, "bad CG settings");
   Geom& g = c->g;
   const int d = g.dim, k = g.k;
@@ -416,6 +418,15 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   double** vecs_e[] = {&A.e, &A.eh, &A.en, &A.srcE, &A.tmpE};
   for (double** p : vecs_e)
     if (e == cudaSuccess) e = dalloc(p, ne);
+  if (phys->integrator == LH_RK4) {
+    double** rk_v[] = {&A.Kv, &A.Kx};
+    for (double** p : rk_v)
+      if (e == cudaSuccess) e = dalloc(p, nv);
+    double** rk_e[] = {&A.Ke, &A.erate};
+    for (double** p : rk_e)
+      if (e == cudaSuccess) e = dalloc(p, ne);
+  }
+  if (e == cudaSuccess && phys->problem == LH_TRIPLE_POINT) e = dalloc(&A.gammaE, nelem);
   if (e == cudaSuccess) e = dalloc(&A.F1E, nelem * d * nd1);
   if (e == cudaSuccess) e = dalloc(&A.ApE, nelem * d * nd1);
   if (precision == LH_FP64) {
@@ -445,8 +456,18 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   }
   if ((st = cuda_check(c, e, "allocation")) != LH_OK) return fail(st, c->err);
 
-  // quadrature data: rho0 |J0| per element (rho0 = 1 in every problem here)
+  // quadrature data: rho0 |J0| per element (rho0 = 1 in every problem but the
+  // triple point, whose rho0 and gamma are constant per element)
   std::vector<double> rho0K(nelem, 1.0 * vol);
+  std::vector<double> gamE;
+  if (phys->problem == LH_TRIPLE_POINT) {
+    gamE.resize(nelem);
+    for (int64_t el = 0; el < g.nelem; ++el) {
+      double rho, p;
+      triple_point_state(g, el, &rho, &p, &gamE[el]);
+      rho0K[el] = rho * vol;
+    }
+  }
   // diagonal of the scalar kinematic mass matrix, assembled
   std::vector<double> diag(g.nnodes, 0.0);
   {
@@ -566,6 +587,8 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
     e = cudaMemcpy(A.dinv, diag.data(), g.nnodes * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(A.ctl, &ctl0, sizeof(Ctl), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(A.srcE, 0, ne * sizeof(double));
+  if (e == cudaSuccess && A.gammaE)
+    e = cudaMemcpy(A.gammaE, gamE.data(), nelem * sizeof(double), cudaMemcpyHostToDevice);
   if ((st = cuda_check(c, e, "upload")) != LH_OK) return fail(st, c->err);
   *out = c;
   return LH_OK;
@@ -638,10 +661,28 @@ __global__ void pref_kernel(const double* e, int64_t ne, double gm1, Ctl* ctl) {
 
 static lh_status set_pref(lh_ctx* c) {
   if (c->precision != LH_MIXED) return LH_OK;
+  if (c->phys_desc.problem == LH_TRIPLE_POINT) {
+    // gamma varies per element and there is no large background pressure:
+    // the FP32 stress is the whole stress (p_ref = 0)
+    double z = 0.0;
+    cudaError_t err = cudaMemcpyAsync(&c->a.ctl->p_ref, &z, sizeof(double), cudaMemcpyHostToDevice,
+                                      c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    return cuda_check(c, err, "reference pressure");
+  }
   pref_kernel<<<1, 256, 0, c->stream>>>(c->a.e, c->g.ne, c->phys_desc.gamma - 1.0, c->a.ctl);
   cudaError_t err = cudaGetLastError();
   if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
   return cuda_check(c, err, "reference pressure");
+}
+
+void lagh::triple_point_state(const Geom& g, int64_t el, double* rho, double* p, double* gam) {
+  const int64_t E0 = el % g.n[0], E1 = (el / g.n[0]) % g.n[1];
+  const double xc = g.lo[0] + (E0 + 0.5) * g.h[0], yc = g.lo[1] + (E1 + 0.5) * g.h[1];
+  const bool left = xc <= 1.0, low = yc <= 1.5;
+  *rho = (left || low) ? 1.0 : 0.125;
+  *p = left ? 1.0 : 0.1;
+  *gam = (left || !low) ? 1.5 : 1.4;
 }
 
 void lagh::initial_state(const Geom& g, const lh_phys_desc& ph, std::vector<double>& v,
@@ -694,6 +735,12 @@ void lagh::initial_state(const Geom& g, const lh_phys_desc& ph, std::vector<doub
       double ev = 0.0;
       const double rho0 = 1.0;
       switch (ph.problem) {
+        case LH_TRIPLE_POINT: {
+          double rho, p, gam;
+          triple_point_state(g, el, &rho, &p, &gam);
+          ev = p / ((gam - 1.0) * rho);
+          break;
+        }
         case LH_SEDOV:
           ev = (el == 0) ? ph.blast_energy / (rho0 * g.detJ0) : 0.0;
           break;

@@ -1,5 +1,5 @@
-// RK2-average time step (eq:RK2-avg) and the automatic step control of
-// Section 2.2.3, orchestrated on the device.
+// RK2-average time step (eq:RK2-avg), the RK4 step (eq:RK4) and the automatic
+// step control of Section 2.2.3, orchestrated on the device.
 //
 // One attempt is the fixed kernel sequence
 //   force(S^n) -> gather -> CG -> v, x half update -> energy half update
@@ -45,6 +45,50 @@ __global__ void stage2_update_kernel(int64_t nv, const double* __restrict__ v,
     vn[i] = v1;
     vbar[i] = vb;
     xn[i] = x[i] + dt * vb;
+  }
+}
+
+// RK4 stage combination (eq:RK4, eq:RK4coeff).  Stage s (0..3) has produced
+// its rates: dv/dt = a (the CG solution), de/dt = erate and dx/dt = vs (the
+// stage velocity).  They are added to the weighted sums K with weights 1, 2,
+// 2, 1; stages 0..2 then form the next stage state S^n + c dt k_s (c = 1/2,
+// 1/2, 1), stage 3 the candidate S^n + dt/6 K.  The next stage state may be
+// the arrays the current stage's velocity was read from (element-wise, each
+// entry is read before it is written), so no pointer here is restrict.
+__global__ void rk4_combine_kernel(int64_t nv, int64_t ne, int s, const double* v, const double* x,
+                                   const double* e, const double* a, const double* vs,
+                                   const double* erate, double* Kv, double* Kx, double* Ke,
+                                   double* vnext, double* xnext, double* enext, const Ctl* ctl) {
+  pdl_enter();
+  if (ctl->done) return;
+  const double dt = ctl->dt_use;
+  const double w = (s == 1 || s == 2) ? 2.0 : 1.0;
+  const double cdt = (s == 2) ? dt : 0.5 * dt;  // c_{s+1} dt of the next stage
+  const double h6 = dt / 6.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const double ai = a[i], vi = vs[i];
+    const double kv = s == 0 ? ai : Kv[i] + w * ai;
+    const double kx = s == 0 ? vi : Kx[i] + w * vi;
+    if (s < 3) {
+      Kv[i] = kv;
+      Kx[i] = kx;
+      vnext[i] = v[i] + cdt * ai;
+      xnext[i] = x[i] + cdt * vi;
+    } else {
+      vnext[i] = v[i] + h6 * kv;
+      xnext[i] = x[i] + h6 * kx;
+    }
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ne; i += stride) {
+    const double ri = erate[i];
+    const double ke = s == 0 ? ri : Ke[i] + w * ri;
+    if (s < 3) {
+      Ke[i] = ke;
+      enext[i] = e[i] + cdt * ri;
+    } else {
+      enext[i] = e[i] + h6 * ke;
+    }
   }
 }
 
@@ -98,8 +142,73 @@ static cudaError_t stage_cg(lh_ctx* c, cudaStream_t s, bool capturing) {
   return cg_solve_eager(c, c->a.rhs, c->a.acc, s, &done);
 }
 
+static cudaError_t enqueue_control_commit(lh_ctx* c, cudaStream_t s) {
+  Arrays& A = c->a;
+  const Geom& g = c->g;
+  const bool pdl = c->use_pdl != 0;
+  CtlConsts k;
+  k.beta1 = c->phys_desc.beta1;
+  k.beta2 = c->phys_desc.beta2;
+  k.gamma_dt = c->phys_desc.gamma_dt;
+  cudaError_t e = launch_k(pdl, control_kernel, dim3(1), dim3(32), 0, s, A.ctl, k);
+  if (e != cudaSuccess) return e;
+  return launch_k(pdl, commit_kernel, dim3(node_blocks(c, g.nv)), dim3(256), 0, s, g.nv, g.ne, A.v,
+                  A.x, A.e, (const double*)A.vn, (const double*)A.xn, (const double*)A.en,
+                  (const Ctl*)A.ctl);
+}
+
+// Enqueue one attempt of the RK4 step (eq:RK4) on stream s: four stages of
+// force -> gather -> CG -> energy rate -> combination, then control and commit.
+static cudaError_t enqueue_attempt_rk4(lh_ctx* c, cudaStream_t s, bool capturing) {
+  Arrays& A = c->a;
+  const Geom& g = c->g;
+  const bool mixed = c->precision == LH_MIXED;
+  const bool pdl = c->use_pdl != 0;
+  cudaError_t e;
+  for (int st = 0; st < 4; ++st) {
+    const double* vs = st == 0 ? A.v : A.vh;
+    const double* es = st == 0 ? A.e : A.eh;
+    const double* xs = st == 0 ? A.x : A.xh;
+    ForceArgs f = {};
+    f.v = vs; f.e = es; f.x = xs; f.vtest = nullptr;
+    f.list = nullptr; f.nslots = g.nelem;
+    f.F1E = A.F1E;
+    f.D = mixed ? nullptr : A.D;
+    f.FK = mixed ? A.FK : nullptr;
+    f.FTvE = nullptr;
+    f.srcE = c->ph.source ? A.srcE : nullptr;
+    f.tau_bits = &A.ctl->tau_bits[st == 0 ? 0 : 1];  // the minimum over all stages
+    f.status = &A.ctl->status;
+    f.ctl = A.ctl;
+    f.p_ref = &A.ctl->p_ref;
+    f.mode = kForceFull;
+    if ((e = launch_force(c, f, s)) != cudaSuccess) return e;
+    if ((e = launch_gather(c, A.F1E, A.rhs, -1.0, 1, A.ctl, s)) != cudaSuccess) return e;
+    if ((e = stage_cg(c, s, capturing)) != cudaSuccess) return e;
+    EnergyArgs ea = {};
+    ea.w = vs; ea.D = A.D; ea.FK = A.FK;
+    ea.srcE = c->ph.source ? A.srcE : nullptr;
+    ea.x = mixed ? xs : nullptr;
+    ea.p_ref = mixed ? &A.ctl->p_ref : nullptr;
+    ea.e_base = nullptr; ea.e_out = A.erate; ea.frac = 1.0; ea.dt = 0.0; ea.rate = 1;
+    ea.ctl = A.ctl;
+    ea.rho0Kinv = A.rho0Kinv;
+    if ((e = launch_energy_update(c, ea, s)) != cudaSuccess) return e;
+    double* vnext = st < 3 ? A.vh : A.vn;
+    double* xnext = st < 3 ? A.xh : A.xn;
+    double* enext = st < 3 ? A.eh : A.en;
+    e = launch_k(pdl, rk4_combine_kernel, dim3(node_blocks(c, g.nv)), dim3(256), 0, s, g.nv, g.ne,
+                 st, (const double*)A.v, (const double*)A.x, (const double*)A.e,
+                 (const double*)A.acc, vs, (const double*)A.erate, A.Kv, A.Kx, A.Ke, vnext, xnext,
+                 enext, (const Ctl*)A.ctl);
+    if (e != cudaSuccess) return e;
+  }
+  return enqueue_control_commit(c, s);
+}
+
 // Enqueue one attempt of the RK2-average step on stream s.
 static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
+  if (c->phys_desc.integrator == LH_RK4) return enqueue_attempt_rk4(c, s, capturing);
   Arrays& A = c->a;
   const Geom& g = c->g;
   const bool mixed = c->precision == LH_MIXED;
@@ -147,15 +256,7 @@ static cudaError_t enqueue_attempt(lh_ctx* c, cudaStream_t s, bool capturing) {
   e2.w = A.vbar; e2.e_out = A.en; e2.frac = 1.0;
   e2.x = mixed ? A.xh : nullptr;
   if ((e = launch_energy_update(c, e2, s)) != cudaSuccess) return e;
-  CtlConsts k;
-  k.beta1 = c->phys_desc.beta1;
-  k.beta2 = c->phys_desc.beta2;
-  k.gamma_dt = c->phys_desc.gamma_dt;
-  e = launch_k(pdl, control_kernel, dim3(1), dim3(32), 0, s, A.ctl, k);
-  if (e != cudaSuccess) return e;
-  return launch_k(pdl, commit_kernel, dim3(node_blocks(c, g.nv)), dim3(256), 0, s, g.nv, g.ne, A.v,
-                  A.x, A.e, (const double*)A.vn, (const double*)A.xn, (const double*)A.en,
-                  (const Ctl*)A.ctl);
+  return enqueue_control_commit(c, s);
 }
 
 static cudaError_t capture_attempt(lh_ctx* c, const char** where) {

@@ -36,6 +36,7 @@ def descriptors(cfg, cg_rtol=None, cg_maxit=None, phys_overrides=None):
     phys.blast_energy = float(cfg.get("blast_energy", 0.25))
     phys.e_uniform = float(cfg.get("e_uniform", 1.0))
     phys.cfl = float(cfg.get("cfl", 0.5))
+    phys.integrator = int(cfg.get("integrator", 0))
     if cg_rtol is not None:
         phys.cg_rtol = cg_rtol
     if cg_maxit is not None:

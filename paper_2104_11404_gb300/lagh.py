@@ -15,7 +15,8 @@ LIB_PATH = os.path.join(PKG, "_lib", "liblagh.so")
 LH_OK, LH_EINVAL, LH_ENOMEM, LH_ECUDA, LH_ETANGLED, LH_ENONFINITE, LH_EDTMIN, LH_ECG, \
     LH_ETIMEOUT, LH_EUNSUPPORTED, LH_ETOOLARGE = range(11)
 LH_FP64, LH_MIXED = 0, 1
-LH_SEDOV, LH_TAYLOR_GREEN, LH_GRESHO, LH_UNIFORM = 1, 2, 3, 4
+LH_SEDOV, LH_TAYLOR_GREEN, LH_GRESHO, LH_UNIFORM, LH_TRIPLE_POINT = 1, 2, 3, 4, 5
+LH_RK2AVG, LH_RK4 = 0, 1
 LH_PRECOND_JACOBI, LH_PRECOND_TENSOR, LH_PRECOND_EXACT, LH_PRECOND_TENSOR64 = 0, 1, 2, 3
 
 # every entry point declared in include/lagh.h
@@ -50,7 +51,8 @@ class lh_phys_desc(ctypes.Structure):
                 ("gamma_dt", ctypes.c_double), ("q1", ctypes.c_double), ("q2", ctypes.c_double),
                 ("cg_rtol", ctypes.c_double), ("dt_min_frac", ctypes.c_double),
                 ("cg_precond", ctypes.c_int32), ("direct_launch", ctypes.c_int32),
-                ("cg_cluster", ctypes.c_int32), ("cg_tiles", ctypes.c_int32)]
+                ("cg_cluster", ctypes.c_int32), ("cg_tiles", ctypes.c_int32),
+                ("integrator", ctypes.c_int32)]
 
 
 class lh_layout_info(ctypes.Structure):

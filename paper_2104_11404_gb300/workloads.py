@@ -12,7 +12,8 @@ import math
 
 import numpy as np
 
-SEDOV, TAYLOR_GREEN, GRESHO, UNIFORM = 1, 2, 3, 4
+SEDOV, TAYLOR_GREEN, GRESHO, UNIFORM, TRIPLE_POINT = 1, 2, 3, 4, 5
+RK2AVG, RK4 = 0, 1
 
 CONFIGS = {
     # 2D point blast, [0,1]^2, 8x8 Q2/Q1, E0 = 0.25 in the origin element, t_f = 0.8
@@ -31,6 +32,11 @@ CONFIGS = {
     # 2D Gresho vortex, [-0.5,0.5]^2, 256x256 Q3/Q2, no viscosity, t_f = 0.62
     "gresho2d_256": dict(dim=2, n=(256, 256, 1), order=3, problem=GRESHO, gamma=5.0 / 3.0,
                          lo=(-0.5, -0.5, 0.0), hi=(0.5, 0.5, 1.0), visc=0, t_final=0.62),
+    # 3D triple point, [0,7] x [0,3] x [0,1.5], 28 x 12 x 4 Q2/Q1 (the mesh of Table
+    # tab:fom, N_V = 38475, N_E = 10752), per-element rho0 / p / gamma, t_f = 0.8
+    # (gamma here only satisfies the descriptor check; the problem sets its own)
+    "triple3d_28": dict(dim=3, n=(28, 12, 4), order=2, problem=TRIPLE_POINT, gamma=1.5,
+                        lo=(0.0, 0.0, 0.0), hi=(7.0, 3.0, 1.5), visc=1, t_final=0.8),
 }
 
 BATCH_SEED = 2104114040

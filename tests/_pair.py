@@ -11,7 +11,8 @@ def oracle_for(cfg, **over):
               lo=list(cfg["lo"]), hi=list(cfg["hi"]), order=cfg["order"],
               problem=cfg["problem"], gamma=cfg["gamma"], visc=cfg.get("visc", 1),
               blast_energy=cfg.get("blast_energy", 0.25), source=cfg.get("source", 1),
-              e_uniform=cfg.get("e_uniform", 1.0), cfl=cfg.get("cfl", 0.5))
+              e_uniform=cfg.get("e_uniform", 1.0), cfl=cfg.get("cfl", 0.5),
+              integrator=cfg.get("integrator", 0))
     kw.update(over)
     return O.Oracle(**kw)
 

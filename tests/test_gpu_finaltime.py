@@ -1,0 +1,113 @@
+"""Final-time parity of whole runs against the oracle (eq:relerrors).
+
+The oracle's final states come from tests/golden/make_final_states.py, which
+calls only the CPU oracle: the 2D Taylor-Green vortex on 64x64 Q2/Q1 to
+t = 0.5, the 3D blast on 8^3 Q2/Q1 to t = 0.6 and the Gresho vortex on 32^2
+Q3/Q2 to t = 0.62 (the sizes of Table tab:fom for the last two), each from its
+initial condition under the step control of Section 2.2.3.
+
+FP64: the GPU replays the oracle's accepted step sizes (lh_step_fixed) and
+must land within 1e-8 relative L2 of the oracle's final v, e and x; run under
+its own step control it must take the same number of steps and redo the same
+attempts.  Mixed: its own step control, within 1e-4 relative L2 in v and e.
+Total energy (problems without a source): drift <= 1e-12 (FP64), <= 1e-10
+(mixed) relative.  Taylor-Green: the velocity error against the exact steady
+field at t = 0.5 equals the oracle's to within the parity tolerance."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2104_11404_gb300 import workloads as W
+from tests._pair import gpu_for, rel_l2
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+CASES = {
+    "tg2d_64": W.scaled("tg2d_64", n=(64, 64)),
+    "sedov3d_8": W.scaled("sedov3d_32", n=(8, 8, 8)),
+    "gresho2d_32": W.scaled("gresho2d_256", n=(32, 32)),
+}
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, "final_%s.npz" % name)
+    if not os.path.exists(path):
+        pytest.fail("missing %s: run tests/golden/make_final_states.py" % path)
+    return np.load(path)
+
+
+def _host(t):
+    return t.detach().cpu().numpy()
+
+
+def _tg_error(v, x):
+    nn = v.size // 2
+    X, Y = x[:nn], x[nn:]
+    ve = np.concatenate([np.sin(np.pi * X) * np.cos(np.pi * Y), -np.cos(np.pi * X) * np.sin(np.pi * Y)])
+    return np.linalg.norm(v - ve) / np.linalg.norm(ve)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_replay_matches_oracle_at_final_time(name):
+    cfg, ref = CASES[name], _golden(name)
+    g = gpu_for(cfg, "fp64")
+    g.init_state()
+    E0 = g.total_energy()
+    log = ref["dt_log"]
+    assert len(log) == int(ref["steps"])
+    for dt in log:
+        g.step_fixed(float(dt))
+    v, e, x, t, _ = g.get_state()
+    v, e, x = _host(v), _host(e), _host(x)
+    assert abs(t - float(ref["t_final"])) <= 1e-12
+    for a, b in ((ref["v"], v), (ref["e"], e), (ref["x"], x)):
+        assert rel_l2(a, b) <= 1e-8
+    if cfg["problem"] != W.TAYLOR_GREEN:
+        assert abs(g.total_energy() - E0) <= 1e-12 * abs(E0)
+    else:
+        assert abs(_tg_error(v, x) - _tg_error(ref["v"], ref["x"])) <= 1e-8
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_free_running_takes_the_oracles_steps(name):
+    cfg, ref = CASES[name], _golden(name)
+    g = gpu_for(cfg, "fp64")
+    g.init_state()
+    log = torch.zeros(int(ref["steps"]) + 16, dtype=torch.float64, device="cuda")
+    st = g.run_to(cfg["t_final"], dt_log=log)
+    assert st["steps"] == int(ref["steps"]) and st["rejects"] == int(ref["rejects"])
+    got = _host(log)[:st["steps"]]
+    assert np.max(np.abs(got - ref["dt_log"]) / ref["dt_log"]) <= 1e-9
+    v, e, x, t, _ = g.get_state()
+    assert t == cfg["t_final"]
+    for a, b in ((ref["v"], _host(v)), (ref["e"], _host(e)), (ref["x"], _host(x))):
+        assert rel_l2(a, b) <= 1e-8
+    g.close()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_mixed_run_within_contract_at_final_time(name):
+    cfg, ref = CASES[name], _golden(name)
+    g = gpu_for(cfg, "mixed")
+    g.init_state()
+    E0 = g.total_energy()
+    st = g.run_to(cfg["t_final"])
+    v, e, x, t, _ = g.get_state()
+    v, e, x = _host(v), _host(e), _host(x)
+    assert t == cfg["t_final"]
+    assert rel_l2(ref["v"], v) <= 1e-4
+    assert rel_l2(ref["e"], e) <= 1e-4
+    assert rel_l2(ref["x"], x) <= 1e-4
+    if cfg["problem"] != W.TAYLOR_GREEN:
+        assert abs(g.total_energy() - E0) <= 1e-10 * abs(E0)
+    else:
+        # the mixed run's error against the exact solution is the FP64 one
+        # plus at most its own deviation from the oracle
+        assert abs(_tg_error(v, x) - _tg_error(ref["v"], ref["x"])) <= 1e-4
+    # the step control ran over the whole interval without giving up
+    assert st["steps"] >= 0.9 * int(ref["steps"])
+    g.close()

@@ -31,7 +31,7 @@ CASES = [
     ("sedov2d_12", _sedov(2, (12, 12)), 0.3, 40),
     ("sedov3d_5", _sedov(3, (5, 5, 5)), 0.15, 15),
     ("tg2d_16", dict(W.scaled("tg2d_64", n=(16, 16))), 0.06, 25),
-    ("gresho2d_8_q3", dict(W.scaled("gresho2d_256", n=(8, 8))), 0.05, 12),
+    ("gresho2d_8_q3", dict(W.scaled("gresho2d_256", n=(8, 8))), 0.12, 12),
 ]
 
 
