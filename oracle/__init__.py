@@ -69,6 +69,13 @@ def lib():
                                ctypes.POINTER(ctypes.c_long)]
         L.lho_step_rk4.argtypes = [ctypes.c_void_p, ctypes.c_double, _dp, _dp, _dp, _dp,
                                    ctypes.POINTER(ctypes.c_long)]
+        L.lho_run_snapshots.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.POINTER(_Stats),
+                                        _dp, _dp, _dp, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
+        L.lho_svd_jacobi.argtypes = [ctypes.c_long, ctypes.c_long, _dp, _dp, ctypes.c_double,
+                                     ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.lho_pod.argtypes = [ctypes.c_long, ctypes.c_long, _dp, _dp, ctypes.c_double, _dp, _dp,
+                              ctypes.POINTER(ctypes.c_long)]
         L.lho_run.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_long,
                               _dp, _dp, _dp, _dp, ctypes.POINTER(_Stats), _dp, ctypes.c_long]
         L.lho_total_energy.restype = ctypes.c_double
@@ -217,6 +224,24 @@ class Oracle:
         d = {k: getattr(stats, k) for k, _ in _Stats._fields_}
         return d, log[:min(stats.steps, log_cap)].copy(), st
 
+    def run_snapshots(self, t_final, v, e, x, cap, t0=0.0, dt=0.0, max_steps=10 ** 9):
+        """lho_run collecting the RK2-average stage snapshots (S^{n+1/2} and
+        S^{n+1} of every accepted step); returns (stats, Sv, Se, Sx, status)
+        with the snapshot matrices as [column, row] arrays."""
+        dtc = ctypes.c_double(dt)
+        stats = _Stats()
+        Sv = np.zeros((cap, self.nv))
+        Se = np.zeros((cap, self.ne))
+        Sx = np.zeros((cap, self.nv))
+        cnt = ctypes.c_long()
+        st = lib().lho_run_snapshots(self._h, float(t0), float(t_final), int(max_steps), _p(v),
+                                     _p(e), _p(x), ctypes.byref(dtc), ctypes.byref(stats), _p(Sv),
+                                     _p(Se), _p(Sx), cap, ctypes.byref(cnt))
+        d = {k: getattr(stats, k) for k, _ in _Stats._fields_}
+        n = min(cnt.value, cap)
+        d["snapshots"] = cnt.value
+        return d, Sv[:n], Se[:n], Sx[:n], st
+
     def total_energy(self, v, e):
         return lib().lho_total_energy(self._h, _p(v), _p(e))
 
@@ -272,3 +297,27 @@ def sym_min_eig(A):
     s = np.zeros(d)
     lib().lho_sym_min_eig(d, _p(A.reshape(-1)), ctypes.byref(lam), _p(s))
     return lam.value, s
+
+
+def svd_jacobi(A, tol=1e-15, max_sweeps=60):
+    """One-sided Jacobi thin SVD of A (rows x cols); returns (U Sigma columns as
+    an array [col, row], sigma, sweeps, status)."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.float64).T)   # column-major storage
+    n, m = A.shape
+    sg = np.zeros(n)
+    sw = ctypes.c_int()
+    st = lib().lho_svd_jacobi(m, n, _p(A), _p(sg), tol, max_sweeps, ctypes.byref(sw))
+    return A, sg, sw.value, st
+
+
+def pod(S_cols, offset=None, eps=0.9999):
+    """POD of snapshots given as an array [column, row]: returns (U as
+    [column, row] in descending singular-value order, sigma, k, status)."""
+    S = np.ascontiguousarray(S_cols, dtype=np.float64)
+    n, m = S.shape
+    U = np.zeros((n, m))
+    sg = np.zeros(n)
+    k = ctypes.c_long()
+    off = None if offset is None else np.ascontiguousarray(offset, dtype=np.float64)
+    st = lib().lho_pod(m, n, _p(S), _p(off), eps, _p(U), _p(sg), ctypes.byref(k))
+    return U, sg, k.value, st

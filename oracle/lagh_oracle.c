@@ -1066,8 +1066,10 @@ static int all_finite(long n, const double* a) {
   return 1;
 }
 
-int lho_step(const lho_problem* P, double dt, double* v, double* e, double* x,
-             double* tau_out, long* cg_iters) {
+/* One RK2-average step; if vh != NULL the half-step state S^{n+1/2} is copied
+ * to (vh, eh, xh). */
+static int step_rk2avg(const lho_problem* P, double dt, double* v, double* e, double* x,
+                       double* tau_out, long* cg_iters, double* vh, double* eh, double* xh) {
   long nv = P->nv, ne = P->ne;
   size_t blk = (size_t)P->dim * P->nd1 * P->nd2;
   double* FK = (double*)malloc(sizeof(double) * blk * P->nelem);
@@ -1100,6 +1102,11 @@ int lho_step(const lho_problem* P, double dt, double* v, double* e, double* x,
   lho_mass_solve_e(P, g, de);
   for (long i = 0; i < ne; ++i) e[i] = e0[i] + 0.5 * dt * de[i];     /* e^{n+1/2} */
   for (long i = 0; i < nv; ++i) x[i] = x0[i] + 0.5 * dt * v[i];      /* x^{n+1/2} */
+  if (vh) {
+    memcpy(vh, v, sizeof(double) * nv);
+    memcpy(eh, e, sizeof(double) * ne);
+    memcpy(xh, x, sizeof(double) * nv);
+  }
 
   /* stage 2: forces of S^{n+1/2} */
   int s2 = all_element_forces(P, v, e, x, FK, &tau2);
@@ -1129,6 +1136,11 @@ int lho_step(const lho_problem* P, double dt, double* v, double* e, double* x,
   free(FK); free(v0); free(x0); free(e0); free(F1); free(a); free(vbar);
   free(g); free(src); free(de);
   return st;
+}
+
+int lho_step(const lho_problem* P, double dt, double* v, double* e, double* x,
+             double* tau_out, long* cg_iters) {
+  return step_rk2avg(P, dt, v, e, x, tau_out, cg_iters, NULL, NULL, NULL);
 }
 
 /* ----------------------------------------------------------------- RK4 -- */
@@ -1202,13 +1214,35 @@ int lho_step_rk4(const lho_problem* P, double dt, double* v, double* e, double* 
   return st;
 }
 
-int lho_run(const lho_problem* P, double t0, double t_final, long max_steps,
-            double* v, double* e, double* x, double* dt_io, lho_stats* stats,
-            double* dt_log, long dt_log_cap) {
+/* Snapshot buffers of a run (Section 4): column-major matrices with cap
+ * columns of N_V (v, x) or N_E (e) entries. */
+typedef struct {
+  double *Sv, *Se, *Sx;
+  long cap, count;
+} snapshots;
+
+static void snap_put(const lho_problem* P, snapshots* S, const double* v, const double* e,
+                     const double* x) {
+  if (S->count >= S->cap) { S->count++; return; }
+  long c = S->count++;
+  memcpy(S->Sv + c * P->nv, v, sizeof(double) * P->nv);
+  memcpy(S->Se + c * P->ne, e, sizeof(double) * P->ne);
+  memcpy(S->Sx + c * P->nv, x, sizeof(double) * P->nv);
+}
+
+static int run_impl(const lho_problem* P, double t0, double t_final, long max_steps,
+                    double* v, double* e, double* x, double* dt_io, lho_stats* stats,
+                    double* dt_log, long dt_log_cap, snapshots* snap) {
   long nv = P->nv, ne = P->ne;
   double* vs = (double*)malloc(sizeof(double) * nv);
   double* xs = (double*)malloc(sizeof(double) * nv);
   double* es = (double*)malloc(sizeof(double) * ne);
+  double *vh = NULL, *eh = NULL, *xh = NULL;
+  if (snap) {
+    vh = (double*)malloc(sizeof(double) * nv);
+    xh = (double*)malloc(sizeof(double) * nv);
+    eh = (double*)malloc(sizeof(double) * ne);
+  }
   lho_stats S;
   memset(&S, 0, sizeof(S));
   S.energy0 = lho_total_energy(P, v, e);
@@ -1229,8 +1263,9 @@ int lho_run(const lho_problem* P, double t0, double t_final, long max_steps,
     memcpy(es, e, sizeof(double) * ne);
     double tau;
     long its = 0;
-    int st = P->cfg.integrator == LHO_RK4 ? lho_step_rk4(P, dt_use, vs, es, xs, &tau, &its)
-                                          : lho_step(P, dt_use, vs, es, xs, &tau, &its);
+    int st = P->cfg.integrator == LHO_RK4
+                 ? lho_step_rk4(P, dt_use, vs, es, xs, &tau, &its)
+                 : step_rk2avg(P, dt_use, vs, es, xs, &tau, &its, vh, eh, xh);
     S.cg_iters += its;
     if (st == LHO_ETANGLED) tau = 0.0;  /* a tangled stage forces a redo */
     else if (st != LHO_OK) { status = st; break; }
@@ -1244,6 +1279,10 @@ int lho_run(const lho_problem* P, double t0, double t_final, long max_steps,
     memcpy(v, vs, sizeof(double) * nv);
     memcpy(x, xs, sizeof(double) * nv);
     memcpy(e, es, sizeof(double) * ne);
+    if (snap) {  /* the accepted step's stage states: S^{n+1/2}, then S^{n+1} */
+      snap_put(P, snap, vh, eh, xh);
+      snap_put(P, snap, v, e, x);
+    }
     if (dt_log && S.steps < dt_log_cap) dt_log[S.steps] = dt_use;
     S.steps++;
     t = last ? t_final : t + dt_use;
@@ -1256,5 +1295,104 @@ done:
   *dt_io = dt;
   if (stats) *stats = S;
   free(vs); free(xs); free(es);
+  free(vh); free(xh); free(eh);
   return status;
+}
+
+int lho_run(const lho_problem* P, double t0, double t_final, long max_steps,
+            double* v, double* e, double* x, double* dt_io, lho_stats* stats,
+            double* dt_log, long dt_log_cap) {
+  return run_impl(P, t0, t_final, max_steps, v, e, x, dt_io, stats, dt_log, dt_log_cap, NULL);
+}
+
+int lho_run_snapshots(const lho_problem* P, double t0, double t_final, long max_steps,
+                      double* v, double* e, double* x, double* dt_io, lho_stats* stats,
+                      double* Sv, double* Se, double* Sx, long cap, long* count) {
+  if (P->cfg.integrator != LHO_RK2AVG) return LHO_EINVAL;
+  snapshots S = {Sv, Se, Sx, cap, 0};
+  int st = run_impl(P, t0, t_final, max_steps, v, e, x, dt_io, stats, NULL, 0, &S);
+  *count = S.count;
+  return st;
+}
+
+/* ------------------------------------------------------------------ POD -- */
+
+/* Thin SVD A = U Sigma W^T of a column-major m x n matrix by one-sided
+ * (Hestenes) Jacobi: plane rotations of column pairs, in cyclic order, until
+ * every pair is orthogonal to |a_p . a_q| <= tol |a_p| |a_q| (pairs with a
+ * column below 1e-16 of the Frobenius norm count as orthogonal).  On return the
+ * columns of A are U Sigma (unsorted) and sigma[j] their norms. */
+int lho_svd_jacobi(long m, long n, double* A, double* sigma, double tol, int max_sweeps,
+                   int* sweeps_out) {
+  /* columns whose norm is at the rounding level of the whole matrix are the
+   * null space of a rank-deficient A: they are left alone */
+  double fro2 = 0.0;
+  for (long j = 0; j < n; ++j) fro2 += dot(m, A + j * m, A + j * m);
+  const double floor2 = 1e-32 * fro2;
+  int sweep;
+  for (sweep = 1; sweep <= max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (long p = 0; p < n - 1; ++p)
+      for (long q = p + 1; q < n; ++q) {
+        double* ap = A + p * m;
+        double* aq = A + q * m;
+        double alpha = dot(m, ap, ap), beta = dot(m, aq, aq), gamma = dot(m, ap, aq);
+        if (alpha <= floor2 || beta <= floor2) continue;
+        if (fabs(gamma) <= tol * sqrt(alpha * beta) || gamma == 0.0) continue;
+        rotated = 1;
+        /* the rotation that zeroes the (p, q) entry of A^T A */
+        double zeta = (beta - alpha) / (2.0 * gamma);
+        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        for (long i = 0; i < m; ++i) {
+          double u = ap[i], w = aq[i];
+          ap[i] = c * u - s * w;
+          aq[i] = s * u + c * w;
+        }
+      }
+    if (!rotated) break;
+  }
+  if (sweeps_out) *sweeps_out = sweep > max_sweeps ? max_sweeps : sweep;
+  for (long j = 0; j < n; ++j) sigma[j] = sqrt(dot(m, A + j * m, A + j * m));
+  return sweep > max_sweeps ? LHO_ECG : LHO_OK;
+}
+
+/* POD basis of a snapshot matrix (eq:SVD, eq:energy_criteria): the columns
+ * of S (m x n, column-major) minus the offset vector (may be NULL), thin SVD,
+ * singular values in descending order, and the smallest k with
+ * sum_{i<=k} sigma_i >= eps sum_i sigma_i.  U (m x n) receives the left
+ * singular vectors in that order (the first k are the basis), sigma (n) the
+ * singular values. */
+int lho_pod(long m, long n, const double* S, const double* offset, double eps, double* U,
+            double* sigma, long* k_out) {
+  double* A = (double*)malloc(sizeof(double) * m * n);
+  double* sg = (double*)malloc(sizeof(double) * n);
+  long* order = (long*)malloc(sizeof(long) * n);
+  for (long j = 0; j < n; ++j)
+    for (long i = 0; i < m; ++i) A[j * m + i] = S[j * m + i] - (offset ? offset[i] : 0.0);
+  int sweeps;
+  int st = lho_svd_jacobi(m, n, A, sg, 1e-15, 60, &sweeps);
+  /* descending order (stable: equal values keep their column order) */
+  for (long j = 0; j < n; ++j) order[j] = j;
+  for (long a = 1; a < n; ++a) {
+    long key = order[a], b = a - 1;
+    while (b >= 0 && sg[order[b]] < sg[key]) { order[b + 1] = order[b]; --b; }
+    order[b + 1] = key;
+  }
+  double total = 0.0;
+  for (long j = 0; j < n; ++j) total += sg[j];
+  long k = n;
+  double acc = 0.0;
+  for (long r = 0; r < n; ++r) {
+    acc += sg[order[r]];
+    if (acc >= eps * total) { k = r + 1; break; }
+  }
+  for (long r = 0; r < n; ++r) {
+    long j = order[r];
+    sigma[r] = sg[j];
+    for (long i = 0; i < m; ++i) U[r * m + i] = sg[j] > 0.0 ? A[j * m + i] / sg[j] : 0.0;
+  }
+  *k_out = total > 0.0 ? k : 0;
+  free(A); free(sg); free(order);
+  return st;
 }

@@ -154,6 +154,27 @@ int lho_run(const lho_problem* P, double t0, double t_final, long max_steps,
             double* v, double* e, double* x, double* dt, lho_stats* stats,
             double* dt_log, long dt_log_cap);
 
+/* lho_run (RK2-average only) that also collects the snapshots of Section 4:
+ * for every accepted step the half-step state S^{n+1/2} and then S^{n+1}, as
+ * columns of the column-major matrices Sv (N_V x cap), Se (N_E x cap) and Sx
+ * (N_V x cap).  *count = the number of snapshots taken (columns beyond cap
+ * are counted but not stored). */
+int lho_run_snapshots(const lho_problem* P, double t0, double t_final, long max_steps,
+                      double* v, double* e, double* x, double* dt, lho_stats* stats,
+                      double* Sv, double* Se, double* Sx, long cap, long* count);
+
+/* Thin SVD of a column-major m x n matrix by one-sided Jacobi, in place (the
+ * columns become U Sigma, unsorted; sigma = their norms). */
+int lho_svd_jacobi(long m, long n, double* A, double* sigma, double tol, int max_sweeps,
+                   int* sweeps);
+
+/* POD basis (eq:SVD, eq:energy_criteria): U (m x n) = left singular vectors
+ * of S - offset 1^T in descending singular-value order, sigma (n) the
+ * singular values, *k = the smallest basis size whose singular-value sum
+ * reaches eps times the total. */
+int lho_pod(long m, long n, const double* S, const double* offset, double eps, double* U,
+            double* sigma, long* k);
+
 /* Total energy 1/2 v.M_V.v + 1.M_E.e. */
 double lho_total_energy(const lho_problem* P, const double* v, const double* e);
 
