@@ -359,6 +359,24 @@ LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* d
 LH_API lh_status lh_check_conversions(const double* in, int64_t n, float* f_out, double* d_out,
                                       double* split_out, void* stream);
 
+/* POD basis of a snapshot matrix (Section 4, eq:SVD, eq:energy_criteria).
+ * S (device, column-major m x n: n snapshots of m entries), offset (device,
+ * m entries, may be NULL): the thin SVD of S - offset 1^T is computed by
+ * one-sided Jacobi (parallel round-robin sweeps of column-pair rotations until
+ * every pair is orthogonal to 1e-15 relative; columns at 1e-16 of the
+ * Frobenius norm count as null space).  Outputs: U (device, m x n,
+ * column-major) the left singular vectors in descending singular-value order
+ * (zero columns for zero singular values), sigma (device, n) the singular
+ * values in that order, *k (host) the smallest basis size whose singular-value
+ * sum reaches eps times the total (0 for S = offset), *sweeps (host, may be
+ * NULL) the Jacobi sweeps taken.  work: device scratch of at least m n + 2 n +
+ * 16 doubles.  n <= 65535.  Work runs on stream (cudaStream_t as void*) and
+ * the call synchronizes it once per sweep.  Errors: LH_EINVAL, LH_ECUDA,
+ * LH_ECG (60 sweeps without convergence; outputs are still written). */
+LH_API lh_status lh_pod(const double* S, int64_t m, int64_t n, const double* offset, double eps,
+                        double* U, double* sigma, double* work, int64_t* k, int32_t* sweeps,
+                        void* stream);
+
 /* Peak arithmetic-rate probe (a measurement service of the library, not a
  * step of the paper): launches one kernel on stream (cudaStream_t as void*)
  * in which every thread runs eight independent chains of iters fused
@@ -454,6 +472,25 @@ LH_API lh_status lh_batch_force_sampled(lh_batch* b, const int64_t* list_off,
                                         const double* e, const double* x,
                                         const double* vtest, double* F1_local,
                                         double* FTv_local, double* dt_est);
+/* Snapshot capture for the offline stage (Section 4): the solution data of
+ * every accepted step of the selected instances, including the intermediate
+ * RK stage, are written by the stage kernel into caller-owned device
+ * matrices during later lh_batch_run_to / lh_batch_step_fixed calls: for an
+ * accepted step, first S^{n+1/2} = (v, e, x) after stage one, then S^{n+1}.
+ * ids (host, nsel ascending instance indices; nsel = 0 turns capture off).
+ * Layout: column-major matrices of cap columns per selected instance, packed
+ * in selection order: the s-th selected instance i owns Sv[ov_s + c N_V(i) +
+ * row] and Sx likewise (ov_s = cap x sum of N_V of the earlier selected
+ * instances) and Se[oe_s + c N_E(i) + row] (oe_s with N_E), c = 0 .. cap - 1.
+ * Raw states are stored (no offset subtracted).  Columns beyond cap are
+ * counted but not written.  This call resets every count to zero.  Errors:
+ * LH_EINVAL (ids not ascending or out of range, NULL matrices, cap < 1). */
+LH_API lh_status lh_batch_snapshots(lh_batch* b, int32_t nsel, const int32_t* ids, int64_t cap,
+                                    double* Sv, double* Se, double* Sx);
+/* Snapshots taken per instance since the last lh_batch_snapshots (host array
+ * of n; 0 for instances not selected); synchronizes. */
+LH_API lh_status lh_batch_snapshot_count(lh_batch* b, int64_t* counts);
+
 /* Autotuner (not a step of the paper): times the stage kernel on the current
  * states for every launch shape that fits the device (threads per CTA, CTAs
  * per SM, node-line staging, quadrature points per thread), reps launches

@@ -116,6 +116,37 @@ class Batch:
         lagh.lh_batch_force_sampled(self.b, d_off, d_ids, F1, v, e, x, vtest, FTv, dt)
         return F1, FTv, off, dt
 
+    def snapshots(self, ids, cap):
+        """Arms snapshot capture (lh_batch_snapshots) for the instances `ids`
+        with room for `cap` columns each; returns the packed device matrices
+        (Sv, Se, Sx) and per selected instance its (row count v, row count
+        e, column offset v, column offset e)."""
+        ids = sorted(int(i) for i in ids)
+        nv = [self.info[i].nv for i in ids]
+        ne = [self.info[i].ne for i in ids]
+        Sv = torch.zeros(cap * sum(nv), dtype=torch.float64, device=self.dev)
+        Sx = torch.zeros(cap * sum(nv), dtype=torch.float64, device=self.dev)
+        Se = torch.zeros(cap * sum(ne), dtype=torch.float64, device=self.dev)
+        lagh.lh_batch_snapshots(self.b, ids, cap, Sv, Se, Sx)
+        self._snap = (ids, cap, nv, ne)
+        return Sv, Se, Sx
+
+    def snapshot_views(self, Sv, Se, Sx):
+        """Per selected instance: (id, count, V [cols, N_V], E [cols, N_E], X
+        [cols, N_V]) views of the captured columns."""
+        ids, cap, nv, ne = self._snap
+        cnt = lagh.lh_batch_snapshot_count(self.b, self.n)
+        out, ov, oe = [], 0, 0
+        for s, i in enumerate(ids):
+            c = min(cnt[i], cap)
+            V = Sv[ov:ov + cap * nv[s]].view(cap, nv[s])[:c]
+            X = Sx[ov:ov + cap * nv[s]].view(cap, nv[s])[:c]
+            E = Se[oe:oe + cap * ne[s]].view(cap, ne[s])[:c]
+            out.append((i, cnt[i], V, E, X))
+            ov += cap * nv[s]
+            oe += cap * ne[s]
+        return out
+
     def autotune(self, reps=2):
         t = lagh.lh_batch_autotune(self.b, reps)
         return dict(threads=t.threads, ctas_per_sm=t.ctas_per_sm, smem_lines=t.smem_lines,

@@ -60,6 +60,11 @@ struct lh_batch {
   double* aux = nullptr;  // n doubles: estimates, energies, fixed step sizes
   unsigned int* qctr = nullptr;
   int* ndone = nullptr;
+  // snapshot capture (caller-owned matrices; offsets and counts are ours)
+  double *Sv = nullptr, *Se = nullptr, *Sx = nullptr;
+  int64_t snap_cap = 0;
+  int64_t* d_snap_ov = nullptr;  // n + n offsets (v/x then e) followed by n counts
+  int snap_on = 0;
   int64_t s_f1e = 0, s_fkd = 0, s_src = 0, s_vec = 0;
   int slots = 0;
   // host mirrors
@@ -115,6 +120,15 @@ static BatchArgs bargs(const lh_batch* b) {
   a.rtol = b->rtol;
   a.maxit = b->maxit;
   a.smem_lines = b->tune.smem_lines;
+  if (b->snap_on) {
+    a.Sv = b->Sv;
+    a.Se = b->Se;
+    a.Sx = b->Sx;
+    a.snap_ov = b->d_snap_ov;
+    a.snap_oe = b->d_snap_ov + b->n;
+    a.snap_count = b->d_snap_ov + 2 * b->n;
+    a.snap_cap = b->snap_cap;
+  }
   return a;
 }
 
@@ -318,7 +332,7 @@ static lh_status run_loop(lh_batch* b, int64_t max_attempts, int64_t first_batch
 static void free_batch(lh_batch* b) {
   void* ptrs[] = {b->d_inst, b->d_order, b->d_ctl, b->v, b->e, b->x, b->vh, b->eh, b->xh,
                   b->vn, b->en, b->xn, b->vbar, b->rho0K, b->rho0Kinv, b->fac, b->F1E, b->FK, b->D,
-                  b->srcE, b->vec, b->aux, b->qctr, b->ndone};
+                  b->srcE, b->vec, b->aux, b->qctr, b->ndone, b->d_snap_ov};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (b->ctl_host) cudaFreeHost(b->ctl_host);
@@ -491,6 +505,8 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
   if (e == cudaSuccess) e = balloc(&b->aux, 2 * (size_t)n);
   if (e == cudaSuccess) e = balloc(&b->qctr, 8);
   if (e == cudaSuccess) e = balloc(&b->ndone, 1);
+  if (e == cudaSuccess) e = balloc(&b->d_snap_ov, 3 * (size_t)n);
+  if (e == cudaSuccess) e = cudaMemset(b->d_snap_ov, 0, sizeof(int64_t) * 3 * (size_t)n);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->ctl_host, sizeof(Ctl) * n);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&b->ndone_host, sizeof(int));
   if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
@@ -715,6 +731,50 @@ static lh_status batch_run(lh_batch* b, double t_final, int64_t max_steps, int f
     stats->wall_ms = ms;
   }
   return instance_status(b);
+}
+
+extern "C" lh_status lh_batch_snapshots(lh_batch* b, int32_t nsel, const int32_t* ids,
+                                        int64_t cap, double* Sv, double* Se, double* Sx) {
+  if (!b || nsel < 0 || nsel > b->n || cap < 0) return LH_EINVAL;
+  if (nsel > 0 && (!ids || !Sv || !Se || !Sx || cap < 1)) return LH_EINVAL;
+  lh_status st;
+  if ((st = bcheck(b, join(b, true), "stream join")) != LH_OK) return st;
+  std::vector<int64_t> h(3 * (size_t)b->n, 0);
+  for (int i = 0; i < b->n; ++i) h[i] = h[b->n + i] = -1;
+  int64_t ov = 0, oe = 0;
+  for (int s = 0; s < nsel; ++s) {
+    const int i = ids[s];
+    if (i < 0 || i >= b->n || (s > 0 && i <= ids[s - 1]))
+      return bset_error(b, LH_EINVAL, "snapshot ids must be ascending instance indices");
+    h[i] = ov;
+    h[b->n + i] = oe;
+    ov += cap * b->inst[i].g.nv;
+    oe += cap * b->inst[i].g.ne;
+  }
+  cudaError_t e = cudaMemcpyAsync(b->d_snap_ov, h.data(), sizeof(int64_t) * 3 * b->n, cudaMemcpyHostToDevice,
+                      b->work);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->work);
+  if ((st = bcheck(b, e, "snapshot tables")) != LH_OK) return st;
+  b->Sv = Sv;
+  b->Se = Se;
+  b->Sx = Sx;
+  b->snap_cap = cap;
+  b->snap_on = nsel > 0;
+  if (b->graph) {  // the attempt graph holds the kernel arguments: rebuild it
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return bcheck(b, join(b, false), "stream join");
+}
+
+extern "C" lh_status lh_batch_snapshot_count(lh_batch* b, int64_t* counts) {
+  if (!b || !counts) return LH_EINVAL;
+  lh_status st;
+  if ((st = bcheck(b, join(b, true), "stream join")) != LH_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(counts, b->d_snap_ov + 2 * b->n, sizeof(int64_t) * b->n,
+                                  cudaMemcpyDeviceToHost, b->work);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->work);
+  return bcheck(b, e, "snapshot counts");
 }
 
 extern "C" lh_status lh_batch_run_to(lh_batch* b, double t_final, int64_t max_steps,

@@ -64,6 +64,14 @@ struct BatchArgs {
   const double* vtest;
   double* out;           // element rows (sampled force), energies or estimates
   double* out2;          // sampled F^T w rows
+  // snapshot capture (Section 4): caller-owned column-major matrices; per
+  // instance the offset (doubles) of its first column in Sv / Sx and in Se
+  // (-1: not captured) and the count of snapshots taken
+  double *Sv, *Se, *Sx;
+  const int64_t* snap_ov;
+  const int64_t* snap_oe;
+  int64_t* snap_count;
+  int64_t snap_cap;
 };
 
 enum { kQStage0 = 0, kQStage1 = 1, kQAux = 2 };
@@ -353,6 +361,7 @@ __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, con
   __shared__ BInst sI;
   __shared__ unsigned long long s_tau;
   __shared__ int s_status, s_skip, s_acc;
+  __shared__ long long s_snap;
   __shared__ double s_dt;
   const int tid = threadIdx.x;
   const int64_t slot = blockIdx.x;
@@ -483,6 +492,29 @@ __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, con
         x[k] = xn[k];
       }
       for (int64_t k = tid; k < g.ne; k += NTT) e[k] = en[k];
+      // snapshots of the accepted step: S^{n+1/2}, then S^{n+1}
+      if (a.snap_count != nullptr && a.snap_ov[i] >= 0) {
+        if (tid == 0) {
+          s_snap = a.snap_count[i];
+          a.snap_count[i] = s_snap + 2;
+        }
+        __syncthreads();
+        const int64_t c0 = s_snap;
+        const double* vh = a.vh + sI.ov;
+        const double* xh = a.xh + sI.ov;
+        const double* eh = a.eh + sI.oe;
+        for (int h = 0; h < 2; ++h) {
+          if (c0 + h >= a.snap_cap) break;
+          double* sv = a.Sv + a.snap_ov[i] + (c0 + h) * g.nv;
+          double* sx = a.Sx + a.snap_ov[i] + (c0 + h) * g.nv;
+          double* se = a.Se + a.snap_oe[i] + (c0 + h) * g.ne;
+          for (int64_t k = tid; k < g.nv; k += NTT) {
+            sv[k] = h == 0 ? vh[k] : vn[k];
+            sx[k] = h == 0 ? xh[k] : xn[k];
+          }
+          for (int64_t k = tid; k < g.ne; k += NTT) se[k] = h == 0 ? eh[k] : en[k];
+        }
+      }
     }
     (void)ND1;
   }

@@ -29,7 +29,8 @@ API_NAMES = [
     "lh_batch_layout", "lh_batch_init_state", "lh_batch_set_state", "lh_batch_get_state",
     "lh_batch_query", "lh_batch_run_to", "lh_batch_step_fixed", "lh_batch_total_energy",
     "lh_batch_force_sampled", "lh_batch_autotune", "lh_batch_tuning_get",
-    "lh_check_conversions", "lh_peak_probe",
+    "lh_check_conversions", "lh_peak_probe", "lh_pod", "lh_batch_snapshots",
+    "lh_batch_snapshot_count",
 ]
 
 
@@ -148,6 +149,10 @@ def load():
     L.lh_batch_autotune.argtypes = [_vp, ctypes.c_int32, P(lh_batch_tuning)]
     L.lh_batch_tuning_get.argtypes = [_vp, P(lh_batch_tuning)]
     L.lh_check_conversions.argtypes = [_dp, ctypes.c_int64, _vp, _dp, _dp, _vp]
+    L.lh_pod.argtypes = [_dp, ctypes.c_int64, ctypes.c_int64, _dp, ctypes.c_double, _dp, _dp, _dp,
+                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), _vp]
+    L.lh_batch_snapshots.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int64, _dp, _dp, _dp]
+    L.lh_batch_snapshot_count.argtypes = [_vp, _vp]
     L.lh_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp,
                                 ctypes.POINTER(ctypes.c_double)]
     for name in API_NAMES:
@@ -416,3 +421,28 @@ def lh_peak_probe(fp64, iters, sink, stream=None):
     if st != LH_OK:
         raise LaghError(st, "lh_peak_probe failed")
     return fl.value
+
+
+def lh_pod(S, m, n, offset, eps, U, sigma, work, stream=None):
+    """POD of the column-major m x n snapshot matrix S (device); returns
+    (k, sweeps).  Raises LaghError on a non-zero status."""
+    k = ctypes.c_int64()
+    sw = ctypes.c_int32()
+    st = load().lh_pod(_ptr(S), int(m), int(n), _ptr(offset), float(eps), _ptr(U), _ptr(sigma),
+                       _ptr(work), ctypes.byref(k), ctypes.byref(sw), stream)
+    if st != LH_OK:
+        raise LaghError(st, "lh_pod failed")
+    return k.value, sw.value
+
+
+def lh_batch_snapshots(b, ids, cap, Sv, Se, Sx):
+    n = len(ids)
+    arr = (ctypes.c_int32 * max(n, 1))(*[int(i) for i in ids])
+    _bcheck(b, load().lh_batch_snapshots(b, n, arr if n else None, int(cap), _ptr(Sv), _ptr(Se),
+                                         _ptr(Sx)))
+
+
+def lh_batch_snapshot_count(b, n):
+    out = (ctypes.c_int64 * n)()
+    _bcheck(b, load().lh_batch_snapshot_count(b, out))
+    return list(out)
