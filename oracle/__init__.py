@@ -76,6 +76,8 @@ def lib():
                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.lho_pod.argtypes = [ctypes.c_long, ctypes.c_long, _dp, _dp, ctypes.c_double, _dp, _dp,
                               ctypes.POINTER(ctypes.c_long)]
+        L.lho_estimate_elements.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_long, _dp,
+                                            _dp, _dp, ctypes.POINTER(ctypes.c_double)]
         L.lho_run.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_long,
                               _dp, _dp, _dp, _dp, ctypes.POINTER(_Stats), _dp, ctypes.c_long]
         L.lho_total_energy.restype = ctypes.c_double
@@ -159,6 +161,14 @@ class Oracle:
         if st not in (OK,):
             raise RuntimeError("element force status %d" % st)
         return FK
+
+    def estimate_elements(self, elems, v, e, x):
+        """Estimate of eq:adaptive-timestep over the listed elements only."""
+        ids = np.ascontiguousarray(elems, dtype=np.int64)
+        tau = ctypes.c_double()
+        st = lib().lho_estimate_elements(self._h, ids.ctypes.data, len(ids), _p(v), _p(e), _p(x),
+                                         ctypes.byref(tau))
+        return tau.value, st
 
     def energy_source(self, x):
         s = np.zeros(self.ne)

@@ -783,6 +783,24 @@ int lho_element_force_matrix(const lho_problem* P, long elem, const double* v,
   return element_force(P, elem, v, e, x, FK, &tau);
 }
 
+int lho_estimate_elements(const lho_problem* P, const long* elems, long n, const double* v,
+                          const double* e, const double* x, double* tau) {
+  size_t blk = (size_t)P->dim * P->nd1 * P->nd2;
+  double* FK = (double*)malloc(sizeof(double) * blk);
+  int status = LHO_OK;
+  double tmin = INFINITY;
+  for (long s = 0; s < n; ++s) {
+    if (elems[s] < 0 || elems[s] >= P->nelem) { status = LHO_EINVAL; break; }
+    double t;
+    int st = element_force(P, elems[s], v, e, x, FK, &t);
+    if (st != LHO_OK) status = st;
+    if (t < tmin) tmin = t;
+  }
+  free(FK);
+  *tau = tmin;
+  return status;
+}
+
 /* All element matrices of a state; returns the minimum estimate. */
 static int all_element_forces(const lho_problem* P, const double* v, const double* e,
                               const double* x, double* FKall, double* tau) {

@@ -120,6 +120,11 @@ int lho_force(const lho_problem* P, const double* v, const double* e,
 int lho_element_force_matrix(const lho_problem* P, long elem, const double* v,
                              const double* e, const double* x, double* FK);
 
+/* Minimum of the estimate of eq:adaptive-timestep over the quadrature points
+ * of the n listed elements (the hyper-reduced step sees only those). */
+int lho_estimate_elements(const lho_problem* P, const long* elems, long n, const double* v,
+                          const double* e, const double* x, double* tau);
+
 /* Manufactured energy source int rho e_src phi_j (length N_E); zeros if the
  * problem has none. */
 int lho_energy_source(const lho_problem* P, const double* x, double* src);
