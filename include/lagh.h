@@ -359,6 +359,67 @@ LH_API lh_status lh_force_static(const lh_mesh_desc* mesh, const lh_disc_desc* d
 LH_API lh_status lh_check_conversions(const double* in, int64_t n, float* f_out, double* d_out,
                                       double* split_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Hyper-reduced online step of the reduced order model (Section 3): the
+ * RK2-average scheme in reduced coordinates (eq:RK2-avg-rom-hr) with the SNS
+ * nonlinear-term bases of Section 4.2 (eq:rom-hr-sns: Phi_F = M_V Phi_v with
+ * its essential rows zero, as those of F.1, and Phi_G = M_E Phi_e) and DEIM
+ * sampling (Section 4.3), under the step control of Section 2.2.3 with the
+ * estimate taken over the sampled elements (the lifted state exists only
+ * there).  Built on an FP64 context of a problem without an energy source;
+ * the context's force kernel evaluates the sampled elements.
+ * ------------------------------------------------------------------------ */
+typedef struct lh_rom lh_rom;
+typedef struct lh_rom_info_t {
+  int32_t nb_v, nb_e, nb_x;  /* basis sizes */
+  int32_t ns_f, ns_g;        /* sampled entries of F.1 and of F^T v */
+  int64_t n_elems;           /* sampled elements (every element touching a
+                                sampled F.1 node, the element of every sampled
+                                F^T v entry) */
+  int64_t n_rows_v, n_rows_e;  /* lifted rows (kinematic, thermodynamic) */
+} lh_rom_info_t;
+
+/* Creates the reduced model of ctx (FP64, no source term): Phi_v (N_V x
+ * nb_v), Phi_e (N_E x nb_e), Phi_x (N_V x nb_x) column-major bases and the
+ * offsets v_os, e_os, x_os (eq:solrepresentation), all host or device
+ * pointers, copied.  ns_f >= nb_v and ns_g >= nb_e sampled entries; samples_f
+ * / samples_g (host, distinct row indices of F.1 / F^T v) or NULL to select
+ * them by greedy DEIM with over-sampling (basis vector j receives its share of
+ * the samples, each at the largest entry of the residual of its least-squares
+ * reconstruction by the basis vectors before it; ties to the lowest row).
+ * Forms the SNS bases, the least-squares matrices (Z^T Phi)^+ of
+ * eq:sol-ls-hyper, the sampled elements and their basis rows, and allocates
+ * the reduced state (zero).  Errors: LH_EINVAL (sizes, samples, a
+ * rank-deficient sampled basis), LH_EUNSUPPORTED (mixed context, source
+ * term), LH_ENOMEM, LH_ECUDA.  Basis sizes <= 1024, samples <= 6144. */
+LH_API lh_status lh_rom_create(lh_ctx* ctx, const double* Phi_v, int32_t nb_v,
+                               const double* Phi_e, int32_t nb_e, const double* Phi_x,
+                               int32_t nb_x, const double* v_os, const double* e_os,
+                               const double* x_os, int32_t ns_f, int32_t ns_g,
+                               const int64_t* samples_f, const int64_t* samples_g, lh_rom** out);
+LH_API lh_status lh_rom_destroy(lh_rom* rom);
+LH_API const char* lh_rom_last_error(const lh_rom* rom);
+/* Sizes (info, may be NULL) and the sample rows and sampled elements (host
+ * arrays of ns_f, ns_g and n_elems entries, each may be NULL). */
+LH_API lh_status lh_rom_info(const lh_rom* rom, lh_rom_info_t* info, int64_t* samples_f,
+                             int64_t* samples_g, int32_t* elems);
+/* Reduced coordinates in / out (host or device, nb_v / nb_e / nb_x doubles),
+ * time and proposed step (dt <= 0: estimate at the next step). */
+LH_API lh_status lh_rom_set_state(lh_rom* rom, const double* vhat, const double* ehat,
+                                  const double* xhat, double t, double dt);
+LH_API lh_status lh_rom_get_state(lh_rom* rom, double* vhat, double* ehat, double* xhat,
+                                  double* t, double* dt);
+/* The lifted full-order state v_os + Phi_v vhat, ... (device, N_V / N_E / N_V,
+ * any may be NULL); synchronizes. */
+LH_API lh_status lh_rom_lift(lh_rom* rom, double* v, double* e, double* x);
+/* One hyper-reduced RK2-average step of size dt, accepted without control;
+ * tau (host, may be NULL) = the estimate over both stages. */
+LH_API lh_status lh_rom_step_fixed(lh_rom* rom, double dt, double* tau);
+/* The step control loop to t_final (or max_steps accepted steps), one CUDA
+ * graph per attempt; stats (host, may be NULL; cg_iters and energies 0). */
+LH_API lh_status lh_rom_run_to(lh_rom* rom, double t_final, int64_t max_steps,
+                               lh_run_stats* stats);
+
 /* POD basis of a snapshot matrix (Section 4, eq:SVD, eq:energy_criteria).
  * S (device, column-major m x n: n snapshots of m entries), offset (device,
  * m entries, may be NULL): the thin SVD of S - offset 1^T is computed by

@@ -30,7 +30,9 @@ API_NAMES = [
     "lh_batch_query", "lh_batch_run_to", "lh_batch_step_fixed", "lh_batch_total_energy",
     "lh_batch_force_sampled", "lh_batch_autotune", "lh_batch_tuning_get",
     "lh_check_conversions", "lh_peak_probe", "lh_pod", "lh_batch_snapshots",
-    "lh_batch_snapshot_count",
+    "lh_batch_snapshot_count", "lh_rom_create", "lh_rom_destroy", "lh_rom_last_error",
+    "lh_rom_info", "lh_rom_set_state", "lh_rom_get_state", "lh_rom_lift", "lh_rom_step_fixed",
+    "lh_rom_run_to",
 ]
 
 
@@ -77,6 +79,12 @@ class lh_batch_stats(ctypes.Structure):
                 ("cg_iters", ctypes.c_int64), ("attempts", ctypes.c_int64),
                 ("instances_done", ctypes.c_int64), ("dof_updates", ctypes.c_int64),
                 ("graph_launches", ctypes.c_int64), ("wall_ms", ctypes.c_double)]
+
+
+class lh_rom_info_t(ctypes.Structure):
+    _fields_ = [("nb_v", ctypes.c_int32), ("nb_e", ctypes.c_int32), ("nb_x", ctypes.c_int32),
+                ("ns_f", ctypes.c_int32), ("ns_g", ctypes.c_int32), ("n_elems", ctypes.c_int64),
+                ("n_rows_v", ctypes.c_int64), ("n_rows_e", ctypes.c_int64)]
 
 
 class lh_batch_tuning(ctypes.Structure):
@@ -153,11 +161,22 @@ def load():
                          ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32), _vp]
     L.lh_batch_snapshots.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int64, _dp, _dp, _dp]
     L.lh_batch_snapshot_count.argtypes = [_vp, _vp]
+    L.lh_rom_create.argtypes = [_vp, _dp, ctypes.c_int32, _dp, ctypes.c_int32, _dp, ctypes.c_int32,
+                                _dp, _dp, _dp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, P(_vp)]
+    L.lh_rom_destroy.argtypes = [_vp]
+    L.lh_rom_last_error.argtypes = [_vp]
+    L.lh_rom_last_error.restype = ctypes.c_char_p
+    L.lh_rom_info.argtypes = [_vp, P(lh_rom_info_t), _vp, _vp, _vp]
+    L.lh_rom_set_state.argtypes = [_vp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double]
+    L.lh_rom_get_state.argtypes = [_vp, _dp, _dp, _dp, P(ctypes.c_double), P(ctypes.c_double)]
+    L.lh_rom_lift.argtypes = [_vp, _dp, _dp, _dp]
+    L.lh_rom_step_fixed.argtypes = [_vp, ctypes.c_double, P(ctypes.c_double)]
+    L.lh_rom_run_to.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, P(lh_run_stats)]
     L.lh_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp,
                                 ctypes.POINTER(ctypes.c_double)]
     for name in API_NAMES:
         if name not in ("lh_default_phys", "lh_status_string", "lh_last_error",
-                        "lh_batch_last_error"):
+                        "lh_batch_last_error", "lh_rom_last_error"):
             getattr(L, name).restype = S
     _lib = L
     return L
@@ -446,3 +465,67 @@ def lh_batch_snapshot_count(b, n):
     out = (ctypes.c_int64 * n)()
     _bcheck(b, load().lh_batch_snapshot_count(b, out))
     return list(out)
+
+
+# ---- hyper-reduced online step ----------------------------------------------
+
+def _rcheck(r, st):
+    if st != LH_OK:
+        raise LaghError(st, load().lh_rom_last_error(r).decode())
+
+
+def lh_rom_create(ctx, Phi_v, nbv, Phi_e, nbe, Phi_x, nbx, v_os, e_os, x_os, ns_f, ns_g,
+                  samples_f=None, samples_g=None):
+    import numpy as np
+    h = _vp()
+    sf = None if samples_f is None else np.ascontiguousarray(samples_f, dtype=np.int64)
+    sg = None if samples_g is None else np.ascontiguousarray(samples_g, dtype=np.int64)
+    st = load().lh_rom_create(ctx, _ptr(Phi_v), int(nbv), _ptr(Phi_e), int(nbe), _ptr(Phi_x),
+                              int(nbx), _ptr(v_os), _ptr(e_os), _ptr(x_os), int(ns_f), int(ns_g),
+                              _ptr(sf), _ptr(sg), ctypes.byref(h))
+    if st != LH_OK:
+        raise LaghError(st, load().lh_last_error(ctx).decode())
+    return h
+
+
+def lh_rom_destroy(r):
+    load().lh_rom_destroy(r)
+
+
+def lh_rom_info(r):
+    import numpy as np
+    info = lh_rom_info_t()
+    _rcheck(r, load().lh_rom_info(r, ctypes.byref(info), None, None, None))
+    sf = np.zeros(info.ns_f, dtype=np.int64)
+    sg = np.zeros(info.ns_g, dtype=np.int64)
+    els = np.zeros(info.n_elems, dtype=np.int32)
+    _rcheck(r, load().lh_rom_info(r, None, sf.ctypes.data, sg.ctypes.data, els.ctypes.data))
+    return info, sf, sg, els
+
+
+def lh_rom_set_state(r, vh, eh, xh, t=0.0, dt=0.0):
+    _rcheck(r, load().lh_rom_set_state(r, _ptr(vh), _ptr(eh), _ptr(xh), float(t), float(dt)))
+
+
+def lh_rom_get_state(r, vh, eh, xh):
+    t = ctypes.c_double()
+    dt = ctypes.c_double()
+    _rcheck(r, load().lh_rom_get_state(r, _ptr(vh), _ptr(eh), _ptr(xh), ctypes.byref(t),
+                                       ctypes.byref(dt)))
+    return t.value, dt.value
+
+
+def lh_rom_lift(r, v, e, x):
+    _rcheck(r, load().lh_rom_lift(r, _ptr(v), _ptr(e), _ptr(x)))
+
+
+def lh_rom_step_fixed(r, dt):
+    tau = ctypes.c_double()
+    _rcheck(r, load().lh_rom_step_fixed(r, float(dt), ctypes.byref(tau)))
+    return tau.value
+
+
+def lh_rom_run_to(r, t_final, max_steps=2 ** 62):
+    st = lh_run_stats()
+    _rcheck(r, load().lh_rom_run_to(r, float(t_final), int(max_steps), ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in lh_run_stats._fields_}
