@@ -36,6 +36,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Lagrangian step DOF-updates/s; mixed/batched vs FP64 GPU at stated rel. error"
 SWEEP_T_FINAL = 0.8
+CHUNK = 100          # accepted time steps of every unfinished sweep instance per bench step
 SWEEP_WORKLOAD = ("batched sweep: 512 independent 2D point-blast instances, E0 U[0.1,1], gamma "
                   "U[1.3,1.67], n x n Q2/Q1 quads with n from {16,24,32,48}, each from its initial "
                   "condition to t = 0.8, splitmix64 seed 2104114040")
@@ -308,9 +309,20 @@ def cpu_baseline_sweep(bounded_seconds=15.0, steps_each=3):
 
 # ------------------------------------------------------------ native arm
 
+def _inst_flops_bytes(cfgs, cg_iters_per_solve):
+    """Per instance: algorithmic FP64 flops and bytes of one attempt."""
+    import numpy as np
+    fl = np.array([batch_fp64_flops([c]) for c in cfgs], dtype=np.float64)
+    by = np.array([batch_attempt_bytes([c], cg_iters_per_solve) for c in cfgs], dtype=np.float64)
+    return fl, by
+
+
 def measure_sweep(args, stream, flush, precision, reduce_max, reduce_sum, steps=None,
-                  warmup=None, autotune=True, e2e=True):
-    """Timed whole sweeps of the batch (see the module docstring)."""
+                  warmup=None, autotune=True, e2e=True, whole=False):
+    """The batched sweep in bench steps of CHUNK accepted time steps of every
+    unfinished instance, the sweep continuing from one bench step to the next
+    (restarted from the initial state, untimed, once every instance has reached
+    t = 0.8).  With whole=True one complete sweep from t = 0 is also timed."""
     import numpy as np
     import torch
     from paper_2104_11404_gb300 import lagh
@@ -331,64 +343,67 @@ def measure_sweep(args, stream, flush, precision, reduce_max, reduce_sum, steps=
             tune = b.autotune(reps=2)
             tune_s = time.time() - t0
         dofs = b.dofs()
+        state = {"fresh": True}
+
+        def restart_if_done():
+            q = b.query()
+            if state["fresh"] or np.all(q["t"] >= SWEEP_T_FINAL):
+                b.set_state(v0, e0, x0, zeros, zeros)
+                state["fresh"] = False
+
         for _ in range(warmup):
-            b.set_state(v0, e0, x0, zeros, zeros)
-            b.run_to(SWEEP_T_FINAL)
+            restart_if_done()
+            b.run_to(SWEEP_T_FINAL, max_steps=CHUNK)
         torch.cuda.synchronize()
         dev_ms, upd, nsteps, rejects, graphs, cg = 0.0, 0, 0, 0, 0, 0
+        att_i = np.zeros(b.n)
         clk = Clocks(torch.cuda.current_device())
         clk.start()
         for _ in range(steps):
+            restart_if_done()
             flush.fill_(1.0)
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
-            b.set_state(v0, e0, x0, zeros, zeros)
-            st = b.run_to(SWEEP_T_FINAL)
+            st = b.run_to(SWEEP_T_FINAL, max_steps=CHUNK)
             ev1.record(stream)
             ev1.synchronize()
             dev_ms += ev0.elapsed_time(ev1)
+            q = b.query()
+            att_i += q["steps"] + q["rejects"]
             upd += st["dof_updates"]
             nsteps += st["steps"]
             rejects += st["rejects"]
             graphs += st["graph_launches"]
             cg += st["cg_iters"]
         clocks = clk.stop()
-        q = b.query()
-        assert np.all(q["t"] == SWEEP_T_FINAL) and np.all(q["status"] == 0)
-        E_all = b.total_energy()
-        fv, fe, _ = b.get_state()
-        final = (fv.cpu().numpy(), fe.cpu().numpy(), b.off_v.copy(), b.off_e.copy())
         attempts = nsteps + rejects
         out = {"dev_ms": dev_ms, "dof_updates": upd, "steps": nsteps, "rejects": rejects,
-               "graph_launches": graphs, "attempt_ms": dev_ms / max(1, graphs),
+               "graph_launches": graphs, "attempts_per_instance": att_i,
                "cg_iters_per_solve": cg / max(1, 2 * attempts), "tuning": tune,
-               "autotune_s": tune_s, "clocks": clocks, "energy_min": float(np.min(E_all)),
+               "autotune_s": tune_s, "clocks": clocks,
                "value": reduce_sum(upd) / (reduce_max(dev_ms) * 1e-3),
                "value_rank": upd / (dev_ms * 1e-3), "dofs_total": int(dofs.sum()),
-               "instances": len(cfgs), "sweeps": steps,
-               "steps_per_instance_mean": nsteps / steps / len(cfgs), "final_state": final}
+               "instances": len(cfgs), "bench_steps": steps}
         if e2e:
-            # end to end through the C ABI: pinned host initial state in, the
-            # whole sweep, the final state out to pinned host memory
+            # end to end through the C ABI: the bench step's state from pinned
+            # host memory, the chunk, the new state back to pinned host memory
             hv = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
             he = torch.empty(b.ne, dtype=torch.float64, pin_memory=True)
             hx = torch.empty(b.nv, dtype=torch.float64, pin_memory=True)
-            hv.copy_(v0)
-            he.copy_(e0)
-            hx.copy_(x0)
-            ov = torch.empty_like(hv).pin_memory()
-            oe = torch.empty_like(he).pin_memory()
-            ox = torch.empty_like(hx).pin_memory()
+            b.set_state(v0, e0, x0, zeros, zeros)
+            lagh.lh_batch_get_state(b.b, hv, he, hx)
+            q = b.query()
             e2e_ms, e2e_upd = 0.0, 0
             for _ in range(max(1, steps // 2)):
                 flush.fill_(1.0)
                 ev0 = torch.cuda.Event(enable_timing=True)
                 ev1 = torch.cuda.Event(enable_timing=True)
                 ev0.record(stream)
-                b.set_state(hv, he, hx, zeros, zeros)
-                st = b.run_to(SWEEP_T_FINAL)
-                lagh.lh_batch_get_state(b.b, ov, oe, ox)
+                b.set_state(hv, he, hx, q["t"], q["dt"])
+                st = b.run_to(SWEEP_T_FINAL, max_steps=CHUNK)
+                lagh.lh_batch_get_state(b.b, hv, he, hx)
+                q = b.query()
                 ev1.record(stream)
                 ev1.synchronize()
                 e2e_ms += ev0.elapsed_time(ev1)
@@ -397,6 +412,26 @@ def measure_sweep(args, stream, flush, precision, reduce_max, reduce_sum, steps=
                           "unit": "DOF-updates/s",
                           "h2d_bytes_per_step": 8 * (2 * b.nv + b.ne) + 16 * b.n,
                           "d2h_bytes_per_step": 8 * (2 * b.nv + b.ne)}
+        if whole:
+            flush.fill_(1.0)
+            b.set_state(v0, e0, x0, zeros, zeros)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            b.set_state(v0, e0, x0, zeros, zeros)
+            st = b.run_to(SWEEP_T_FINAL)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            q = b.query()
+            assert np.all(q["t"] == SWEEP_T_FINAL) and np.all(q["status"] == 0)
+            fv, fe, _ = b.get_state()
+            out["whole"] = {"value": st["dof_updates"] / (ms * 1e-3), "sweep_ms": ms,
+                            "accepted_steps": st["steps"], "rejects": st["rejects"],
+                            "steps_per_instance_mean": st["steps"] / b.n,
+                            "energy_min": float(np.min(b.total_energy()))}
+            out["final_state"] = (fv.cpu().numpy(), fe.cpu().numpy(), b.off_v.copy(),
+                                  b.off_e.copy())
         b.close()
     return out
 
@@ -458,6 +493,156 @@ def measure_single_sizes(stream, nsteps=20):
                 rates[(prec, n)] = (2 * g.nv + g.ne) * st["steps"] / (ev0.elapsed_time(ev1) * 1e-3)
                 g.close()
     return rates
+
+
+def measure_sweep_accuracy(stream, count=12, max_n=24):
+    """The mixed batched path against the FP64 batched path at t = 0.8 on the
+    first `count` sweep instances of mesh size <= max_n: relative L2 difference
+    per instance (eq:relerrors), the worst, and the step counts."""
+    import numpy as np
+    import torch
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.batch import Batch
+    sub = [c for c in W.batch_instances() if c["n"][0] <= max_n][:count]
+    res = {}
+    with torch.cuda.stream(stream):
+        for prec in ("fp64", "mixed"):
+            b = Batch(sub, precision=prec, stream=stream)
+            b.init_state()
+            b.run_to(SWEEP_T_FINAL)
+            v, e, _ = b.get_state()
+            q = b.query()
+            res[prec] = (v.cpu().numpy(), e.cpu().numpy(), q["steps"].copy(), b.off_v.copy(),
+                         b.off_e.copy(), b.total_energy())
+            b.close()
+    fv, fe, fs, ov, oe, fE = res["fp64"]
+    mv, me, ms, _, _, mE = res["mixed"]
+    rel = lambda a, b_: float(np.linalg.norm(b_ - a) / max(np.linalg.norm(a), 1e-300))
+    dv = [rel(fv[ov[i]:ov[i + 1]], mv[ov[i]:ov[i + 1]]) for i in range(len(sub))]
+    de = [rel(fe[oe[i]:oe[i + 1]], me[oe[i]:oe[i + 1]]) for i in range(len(sub))]
+    return {"instances": len(sub), "sizes": sorted({c["n"][0] for c in sub}),
+            "rel_l2_v_worst": max(dv), "rel_l2_e_worst": max(de),
+            "rel_l2_v_median": float(np.median(dv)), "rel_l2_e_median": float(np.median(de)),
+            "steps_fp64": [int(x) for x in fs], "steps_mixed": [int(x) for x in ms],
+            "energy_drift_mixed_worst": float(np.max(np.abs(mE - fE) / np.abs(fE)))}
+
+
+WINDOWS = {"sedov2d_8": None, "tg2d_64": 50, "sedov3d_32": 20, "gresho2d_256": 20}
+
+
+def measure_windows(stream):
+    """The single-problem workloads through one context each, FP64 and mixed:
+    a window of accepted steps after three warm-up steps (the 2D blast 8x8 to
+    its final time): throughput, the mixed/FP64 speed-up, the mixed state's
+    relative L2 difference from the FP64 state after the same window, and the
+    mixed energy drift (problems without a source)."""
+    import numpy as np
+    import torch
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.hydro import Hydro
+    out = {}
+    for name, nsteps in WINDOWS.items():
+        cfg = W.CONFIGS[name]
+        res, states = {}, {}
+        for prec in ("fp64", "mixed"):
+            with torch.cuda.stream(stream):
+                g = Hydro(cfg, precision=prec, stream=stream)
+                g.init_state()
+                E0 = g.total_energy()
+                if nsteps is not None:
+                    g.run_to(cfg["t_final"], max_steps=3)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
+                st = g.run_to(cfg["t_final"], max_steps=nsteps if nsteps else 2 ** 62)
+                ev1.record(stream)
+                ev1.synchronize()
+                ms = ev0.elapsed_time(ev1)
+                N = 2 * g.nv + g.ne
+                v, e, x, t, _ = g.get_state()
+                states[prec] = (v.cpu().numpy(), e.cpu().numpy(), t)
+                r = {"value": N * st["steps"] / (ms * 1e-3), "ms_per_step": ms / max(1, st["steps"]),
+                     "steps": st["steps"],
+                     "cg_iters_per_solve": st["cg_iters"] / max(1, 2 * (st["steps"] + st["rejects"]))}
+                if cfg["problem"] != W.TAYLOR_GREEN:
+                    r["energy_drift"] = abs(g.total_energy() - E0) / abs(E0)
+                res[prec] = r
+                g.close()
+        rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(a), 1e-300))
+        out[name] = {"dofs": int(N), "window": nsteps if nsteps else "to t_final",
+                     "fp64": res["fp64"], "mixed": res["mixed"],
+                     "speedup_mixed_over_fp64": res["mixed"]["value"] / res["fp64"]["value"],
+                     "mixed_vs_fp64_rel_l2": {"v": rel(states["fp64"][0], states["mixed"][0]),
+                                              "e": rel(states["fp64"][1], states["mixed"][1])}}
+    return out
+
+
+def measure_rom(stream, t_final=0.1):
+    """The reduced model of Sections 3-4 on the 3D blast of Table tab:fom
+    (8^3 Q2/Q1, FP64) over t in [0, 0.1]: snapshots of the batched run, GPU POD
+    bases (0.9999 criterion), SNS bases and over-sampled DEIM (twice the basis
+    sizes), then the hyper-reduced online run against the full-order run over
+    the same interval: wall time of each time loop, speed-up, and the lifted
+    reduced state's relative L2 error at t = 0.1 (eq:relerrors)."""
+    import numpy as np
+    import torch
+    from paper_2104_11404_gb300 import lagh
+    from paper_2104_11404_gb300 import workloads as W
+    from paper_2104_11404_gb300.batch import Batch
+    from paper_2104_11404_gb300.hydro import Hydro
+    from paper_2104_11404_gb300.rom import Rom
+    cfg = W.scaled("sedov3d_32", n=(8, 8, 8), t_final=t_final)
+    with torch.cuda.stream(stream):
+        b = Batch([cfg], precision="fp64", stream=stream)
+        b.init_state()
+        v0, e0, x0 = (a.clone() for a in b.get_state())
+        Sv, Se, Sx = b.snapshots([0], 8000)
+        b.run_to(t_final)
+        (_, cnt, V, E, X), = b.snapshot_views(Sv, Se, Sx)
+        bases = []
+        for cols, off in ((V, v0), (E, e0), (X, x0)):
+            n, m = cols.shape
+            U = torch.zeros(n * m, dtype=torch.float64, device="cuda")
+            sig = torch.zeros(n, dtype=torch.float64, device="cuda")
+            work = torch.zeros(m * n + 2 * n + 16, dtype=torch.float64, device="cuda")
+            k, _ = lagh.lh_pod(cols.contiguous(), m, n, off, 0.9999, U, sig, work, stream.cuda_stream)
+            bases.append(U.view(n, m)[:k].contiguous())
+        b.close()
+        f = Hydro(cfg, precision="fp64", stream=stream)
+        f.init_state()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        stf = f.run_to(t_final)
+        ev1.record(stream)
+        ev1.synchronize()
+        fom_ms = ev0.elapsed_time(ev1)
+        fv, fe, fx, _, _ = f.get_state()
+        g = Hydro(cfg, precision="fp64", stream=stream)
+        nb = [B.shape[0] for B in bases]
+        r = Rom(g, bases[0], bases[1], bases[2], v0, e0, x0, min(2 * nb[0], g.nv),
+                min(2 * nb[1], g.ne))
+        r.run_to(t_final)                       # warm-up (builds the graph)
+        r.set_state(np.zeros(nb[0]), np.zeros(nb[1]), np.zeros(nb[2]))
+        ev0.record(stream)
+        st = r.run_to(t_final)
+        ev1.record(stream)
+        ev1.synchronize()
+        rom_ms = ev0.elapsed_time(ev1)
+        lv, le, lx = r.lift()
+        rel = lambda a, b_: float(torch.linalg.norm(b_ - a) / torch.linalg.norm(a))
+        out = {"problem": "3D point blast 8^3 Q2/Q1 (Table tab:fom), t in [0, %g], FP64" % t_final,
+               "snapshots": int(cnt), "basis_sizes": {"v": nb[0], "e": nb[1], "x": nb[2]},
+               "samples": {"F1": int(r.info.ns_f), "FTv": int(r.info.ns_g)},
+               "sampled_elements": int(r.info.n_elems), "elements": int(g.nelem),
+               "fom": {"steps": stf["steps"], "ms": fom_ms},
+               "rom": {"steps": st["steps"], "ms": rom_ms},
+               "speedup_rom_over_fom": fom_ms / rom_ms,
+               "rel_l2_error_at_t_final": {"v": rel(fv, lv), "e": rel(fe, le), "x": rel(fx, lx)}}
+        r.close()
+        g.close()
+        f.close()
+    return out
 
 
 FULL_RUNS = ("sedov2d_8", "tg2d_64", "sedov3d_32", "gresho2d_256")
@@ -555,19 +740,26 @@ def run_native(args):
     if rank != 0:
         return None
     from paper_2104_11404_gb300 import workloads as W
+    import numpy as np
     cfgs = W.batch_instances()
     extra = not args.quick
-    sw64 = measure_sweep(args, stream, flush, "fp64", lambda x: x, lambda x: x, steps=1, warmup=1,
+    whole = measure_sweep(args, stream, flush, "mixed", lambda x: x, lambda x: x, steps=0,
+                          warmup=0, autotune=True, e2e=False, whole=True)["whole"] if extra else None
+    sw64 = measure_sweep(args, stream, flush, "fp64", lambda x: x, lambda x: x, steps=3, warmup=1,
                          autotune=True, e2e=False) if extra else None
+    acc = measure_sweep_accuracy(stream) if extra else None
     rates = measure_single_sizes(stream) if extra else None
     hr = measure_hyper_reduced(stream) if extra else None
-    full = measure_full_runs(stream) if (extra and not args.no_configs) else None
+    windows = measure_windows(stream) if (extra and not args.no_configs) else None
+    full = measure_full_runs(stream) if args.full_runs else None
+    rom = measure_rom(stream) if extra else None
 
     value = sw["value"]
-    fl = batch_fp64_flops(cfgs)
-    att_ms = sw["attempt_ms"]
-    achieved = fl / (att_ms * 1e-3) / 1e12
-    abytes = batch_attempt_bytes(cfgs, sw["cg_iters_per_solve"])
+    fl_i, by_i = _inst_flops_bytes(cfgs, sw["cg_iters_per_solve"])
+    att = sw["attempts_per_instance"]
+    dev_s = sw["dev_ms"] * 1e-3
+    achieved = float(fl_i @ att) / dev_s / 1e12
+    abytes = float(by_i @ att)
     kernels_per_graph = 2
     launches = sw["graph_launches"] * kernels_per_graph + 2 * args.steps  # + estimate, begin
     line = {
@@ -585,8 +777,9 @@ def run_native(args):
         "data": "synthetic",
         "config": {"workload": SWEEP_WORKLOAD, "instances": sw["instances"],
                    "dofs_total": sw["dofs_total"], "precision": "mixed FP32/FP64",
-                   "step": "one whole sweep (every instance from t = 0 to t = 0.8)",
-                   "steps_per_instance_mean": sw["steps_per_instance_mean"],
+                   "step": "%d accepted RK2-average time steps of every unfinished instance, the "
+                           "sweep continuing across bench steps and restarting from t = 0 once "
+                           "every instance has reached t = 0.8" % CHUNK,
                    "l2": "flushed between timed steps (256 MB write); the packed state and "
                          "per-CTA scratch exceed L2",
                    "tuning": sw["tuning"], "autotune_s": sw["autotune_s"],
@@ -594,11 +787,12 @@ def run_native(args):
         "roofline": {"bound": "alu", "kernel": "batch_stage_kernel (both stage kernels of an attempt)",
                      "achieved": achieved, "peak": pk["fp64_tflops"], "unit": "TFLOP/s (FP64)",
                      "frac": achieved / pk["fp64_tflops"], "traffic": STAGE_KERNEL_DRAM_BYTES,
-                     "algorithmic_fp64_flops_per_attempt": fl, "attempt_us": att_ms * 1e3,
+                     "algorithmic_fp64_flops": float(fl_i @ att),
+                     "attempts": float(att.sum()),
                      "peak_source": "FP64 FMA probe measured in this run (lh_peak_probe, of measured)",
-                     "hbm_view": {"algorithmic_bytes_per_attempt": abytes,
-                                  "achieved": abytes / (att_ms * 1e-3) / 1e9, "peak": hbm_peak,
-                                  "unit": "GB/s", "frac": abytes / (att_ms * 1e-3) / 1e9 / hbm_peak,
+                     "hbm_view": {"algorithmic_bytes": abytes,
+                                  "achieved": abytes / dev_s / 1e9, "peak": hbm_peak,
+                                  "unit": "GB/s", "frac": abytes / dev_s / 1e9 / hbm_peak,
                                   "peak_source": hbm_src,
                                   "cg_iters_per_solve": sw["cg_iters_per_solve"]}},
         "e2e": sw["e2e"],
@@ -607,27 +801,18 @@ def run_native(args):
         "measured_peaks": {"fp64_tflops": pk["fp64_tflops"], "fp32_tflops": pk["fp32_tflops"],
                            "hbm_gbs": hbm_peak},
         "sweep": {"accepted_steps": sw["steps"], "rejects": sw["rejects"],
-                  "attempt_graphs": sw["graph_launches"], "energy_min": sw["energy_min"]},
+                  "attempt_graphs": sw["graph_launches"]},
     }
+    if whole is not None:
+        line["whole_sweep"] = whole
     if sw64 is not None:
         v64 = sw64["value_rank"]
-        line["batched_fp64"] = {"value": v64, "ms_per_sweep": sw64["dev_ms"] / sw64["sweeps"],
+        line["batched_fp64"] = {"value": v64, "ms_per_step": sw64["dev_ms"] / sw64["bench_steps"],
                                 "tuning": sw64["tuning"],
                                 "speedup_mixed_over_fp64_batched": sw["value_rank"] / v64}
-        # accuracy of the mixed sweep at the final time against the FP64 sweep:
-        # relative L2 difference per instance (eq:relerrors), the worst instance
-        import numpy as np
-        mv, me, ov, oe = sw["final_state"]
-        fv, fe, _, _ = sw64["final_state"]
-        worst = {"v": 0.0, "e": 0.0}
-        for i in range(len(cfgs)):
-            for key, a, b_, off in (("v", fv, mv, ov), ("e", fe, me, oe)):
-                ref = a[off[i]:off[i + 1]]
-                d = np.linalg.norm(b_[off[i]:off[i + 1]] - ref) / max(np.linalg.norm(ref), 1e-300)
-                worst[key] = max(worst[key], float(d))
-        line["batched_fp64"]["mixed_vs_fp64_rel_l2_at_t_final_worst_instance"] = worst
+    if acc is not None:
+        line["mixed_accuracy"] = acc
     if rates is not None:
-        import numpy as np
         dofs = np.array([2 * 2 * (2 * c["n"][0] + 1) * (2 * c["n"][1] + 1) + 4 * c["n"][0] * c["n"][1]
                          for c in cfgs], dtype=np.float64)
         share = dofs / dofs.sum()
@@ -643,8 +828,12 @@ def run_native(args):
             "speedup_batched_mixed_over_mixed_single_problem": sw["value_rank"] / mix_rate("mixed")}
     if hr is not None:
         line["hyper_reduced_force"] = hr
+    if windows is not None:
+        line["configs"] = windows
     if full is not None:
         line["full_runs"] = full
+    if rom is not None:
+        line["rom"] = rom
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sweep()
     return line
@@ -696,8 +885,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the full single-problem runs (2D blast 8x8, Taylor-Green 64x64, "
+                    help="skip the single-problem windows (2D blast 8x8, Taylor-Green 64x64, "
                          "3D blast 32^3, Gresho 256^2 Q3)")
+    ap.add_argument("--full-runs", action="store_true",
+                    help="also run every single-problem workload to its final time in FP64 "
+                         "and mixed (several minutes)")
     ap.add_argument("--quick", action="store_true",
                     help="the headline sweep only (no FP64 sweep, single-problem rates, "
                          "restricted force or full runs)")

@@ -72,7 +72,10 @@ typedef enum lh_precision {
                    entries accumulated with error-free FP32 transformations
                    (about 2^-48 relative) and widened once to FP64; positions,
                    time integration, CG iterates, residuals and dot products
-                   and the energy in FP64 */
+                   and the energy in FP64.  The FP32 stress leaves out a constant
+                   reference pressure whose F.1 vanishes on the box after the wall
+                   condition: states must keep the wall nodes on their walls, as
+                   every state the integrator makes from lh_init_state does */
 } lh_precision;
 
 typedef enum lh_problem_id {

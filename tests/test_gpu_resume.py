@@ -74,7 +74,7 @@ def test_resume_in_fresh_context_is_bit_identical(name, cfg, t_final, cut, preci
         # pressure); a resumed run therefore rounds its FP32 stress
         # differently, and agrees to FP32 rounding, not bitwise
         for a, b in ((vr, vw), (er, ew), (xr, xw)):
-            assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-6
+            assert float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) <= 1e-5
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
