@@ -17,9 +17,13 @@
  *     (nq = 2k by default).
  *  R3 Artificial viscosity (sigma_a of eq:euler).  eps = sym(grad v);
  *     (lambda_min, s) = smallest eigenpair of eps (2D closed form, 3D cyclic
- *     Jacobi, ties -> lowest index).  If lambda_min < 0:
- *     l_s = l_0 |J J0^{-1} s|, mu = rho (q2 l_s^2 |lambda_min| + q1 l_s c_s),
- *     sigma_a = mu eps; otherwise mu = 0.  l_0 = |K_0|^{1/d} / k.
+ *     Jacobi, ties -> lowest index).  The point is in compression when
+ *     lambda_min < -1e-5 (|eps|_F + c_s / h_min): a compression rate below that
+ *     floor is rounding noise of a vanishing strain rate (a z-invariant flow
+ *     in 3D, a gas at rest), where the sign alone would switch on the linear
+ *     term.  In compression: l_s = l_0 |J J0^{-1} s|,
+ *     mu = rho (q2 l_s^2 |lambda_min| + q1 l_s c_s), sigma_a = mu eps;
+ *     otherwise mu = 0.  l_0 = |K_0|^{1/d} / k.
  *  R4 h_min of eq:adaptive-timestep is sigma_min(J) / k.
  *  R5 dt_0 is the estimate of the initial state; the last step is clamped to
  *     land on t_final; dt < dt_min_frac * t_final is an error.
@@ -57,6 +61,7 @@
 #define MAXK 4
 #define LHO_PI 3.14159265358979323846
 #define MAXQ 8
+#define LHO_COMPRESSION_FLOOR 1e-5  /* reading R3 */
 
 struct lho_problem {
   lho_config cfg;
@@ -684,7 +689,10 @@ static int qpoint_gamma(const lho_problem* P, double gam, const double* J,
         eps[c * d + n] = 0.5 * (gradv[c * d + n] + gradv[n * d + c]);
     double lam, s[3];
     lho_sym_min_eig(d, eps, &lam, s);
-    if (lam < 0.0) {
+    double frob = 0.0;
+    for (int i = 0; i < d * d; ++i) frob += eps[i] * eps[i];
+    frob = sqrt(frob);
+    if (lam < -LHO_COMPRESSION_FLOOR * (frob + cs / hmin)) {
       /* l_s = l_0 |J J0^{-1} s| */
       double JJ0[9], ds[3];
       for (int c = 0; c < d; ++c)

@@ -201,7 +201,15 @@ __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&
       for (int n = 0; n < DIM; ++n) eps[c][n] = T(0.5) * (gv[c][n] + gv[n][c]);
     T lam, s[DIM];
     min_eigenpair<T, DIM>(eps, lam, s);
-    if (lam < T(0)) {
+    // compression only above a floor of 1e-5 (|eps|_F + c_s / h_min): below it
+    // the sign of the smallest strain rate is rounding noise (a vanishing
+    // strain rate: z-invariant flow in 3D, gas at rest) and would switch on
+    // the linear term
+    T frob = T(0);
+    for (int c = 0; c < DIM; ++c)
+      for (int n = 0; n < DIM; ++n) frob += eps[c][n] * eps[c][n];
+    frob = t_sqrt(frob);
+    if (lam < -T(1e-5) * (frob + cs / hmin)) {
       T n2 = T(0);
       for (int c = 0; c < DIM; ++c) {
         T dc = T(0);

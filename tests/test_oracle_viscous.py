@@ -88,7 +88,8 @@ def _sigma_numpy(o, J, Gv, e_q, vol):
     lam, vecs = np.linalg.eigh(eps)
     sig = -p * np.eye(d)
     mu = 0.0
-    if lam[0] < 0.0:
+    hmin = np.linalg.svd(J, compute_uv=False).min() / k
+    if lam[0] < -1e-5 * (np.linalg.norm(eps) + cs / hmin):
         s = vecs[:, 0]
         ell = (np.prod(h0) ** (1.0 / d) / k) * np.linalg.norm(J @ (s / h0))
         mu = rho * (q2 * ell * ell * abs(lam[0]) + q1 * ell * cs)
