@@ -382,8 +382,9 @@ def measure_sweep(args, stream, flush, precision, reduce_max, reduce_sum, steps=
                "graph_launches": graphs, "attempts_per_instance": att_i,
                "cg_iters_per_solve": cg / max(1, 2 * attempts), "tuning": tune,
                "autotune_s": tune_s, "clocks": clocks,
-               "value": reduce_sum(upd) / (reduce_max(dev_ms) * 1e-3),
-               "value_rank": upd / (dev_ms * 1e-3), "dofs_total": int(dofs.sum()),
+               "value": reduce_sum(upd) / (reduce_max(dev_ms) * 1e-3) if steps else None,
+               "value_rank": upd / (dev_ms * 1e-3) if steps else None,
+               "dofs_total": int(dofs.sum()),
                "instances": len(cfgs), "bench_steps": steps}
         if e2e:
             # end to end through the C ABI: the bench step's state from pinned
