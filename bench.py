@@ -158,19 +158,24 @@ def flops_per_element_force(dim, k, mixed):
 
 
 def batch_fp64_flops(cfgs):
-    """Algorithmic FP64 flops of one attempt (two stages) of the batched
-    mixed step, summed over instances, with n_e elements and N_V velocity
-    unknowns each (2D Q2/Q1): per element F.1 row sums 72, node gather 18,
-    mass apply (two 3x3 contractions per component, scale) 234 and its gather
-    18, energy update (F^T w 144, M_E^-1 32, update 4) 180; per velocity
-    unknown the line solves 21 (forward and backward substitution along both
-    directions, k = 2, and the scale), CG dots and updates 12, stage update 4."""
+    """FP64 flops of one attempt (two stages) of the batched mixed step, summed
+    over instances: the work the mixed design keeps in FP64 (2D Q2/Q1, n_e
+    elements, N_V velocity unknowns per instance), counted per stage from the
+    kernels' loops.  Per element: the FP64 element-origin shift of the staged
+    positions 18, the widening of the error-free F.1 row sums 18, the node
+    gather of -F.1 18, the CG mass apply (two 3x3 contractions per component,
+    54 multiply-adds each, the rho0|J0| scaling 18) 234 and its node sums 18,
+    the energy update (widening of the error-free F^T w sums 4, M_E^-1 16
+    multiply-adds, the update 4 multiply-adds) 44: 350.  Per velocity unknown:
+    the line solves 21 (forward and backward substitution along both
+    directions, k = 2, and the scale), the CG dots and updates 12, the stage
+    update 4: 37."""
     tot = 0
     for c in cfgs:
         n = c["n"][0] * c["n"][1]
         nn = (2 * c["n"][0] + 1) * (2 * c["n"][1] + 1)
         nv = 2 * nn
-        tot += 522 * n + 37 * nv
+        tot += 350 * n + 37 * nv
     return 2 * tot
 
 
@@ -521,11 +526,49 @@ def measure_sweep_accuracy(stream, count=12, max_n=24):
     rel = lambda a, b_: float(np.linalg.norm(b_ - a) / max(np.linalg.norm(a), 1e-300))
     dv = [rel(fv[ov[i]:ov[i + 1]], mv[ov[i]:ov[i + 1]]) for i in range(len(sub))]
     de = [rel(fe[oe[i]:oe[i + 1]], me[oe[i]:oe[i + 1]]) for i in range(len(sub))]
-    return {"instances": len(sub), "sizes": sorted({c["n"][0] for c in sub}),
+    free = {"what": "each path under its own step control to t = 0.8 (a borderline "
+                    "step-control decision can part the step sequences, after which the runs "
+                    "differ by their time discretisation)",
             "rel_l2_v_worst": max(dv), "rel_l2_e_worst": max(de),
             "rel_l2_v_median": float(np.median(dv)), "rel_l2_e_median": float(np.median(de)),
             "steps_fp64": [int(x) for x in fs], "steps_mixed": [int(x) for x in ms],
             "energy_drift_mixed_worst": float(np.max(np.abs(mE - fE) / np.abs(fE)))}
+    # precision alone: the mixed batch replays the FP64 step sizes of each
+    # instance (one context per instance records them) for the common number
+    # of accepted steps, against the FP64 state after those steps
+    from paper_2104_11404_gb300.hydro import Hydro
+    sub2 = sub[:4]
+    logs, refs = [], []
+    with torch.cuda.stream(stream):
+        for c in sub2:
+            g = Hydro(c, precision="fp64", stream=stream)
+            g.init_state()
+            lg = torch.zeros(20000, dtype=torch.float64, device="cuda")
+            st = g.run_to(SWEEP_T_FINAL, dt_log=lg)
+            logs.append(lg.cpu().numpy()[:st["steps"]])
+            g.close()
+        nrep = min(len(l) for l in logs)
+        for c in sub2:
+            g = Hydro(c, precision="fp64", stream=stream)
+            g.init_state()
+            g.run_to(SWEEP_T_FINAL, max_steps=nrep)
+            v, e, _, _, _ = g.get_state()
+            refs.append((v.cpu().numpy(), e.cpu().numpy()))
+            g.close()
+        b = Batch(sub2, precision="mixed", stream=stream)
+        b.init_state()
+        for k in range(nrep):
+            b.step_fixed(np.array([l[k] for l in logs]))
+        v, e, _ = b.get_state()
+        v, e = v.cpu().numpy(), e.cpu().numpy()
+        rv = [rel(refs[i][0], v[b.off_v[i]:b.off_v[i + 1]]) for i in range(len(sub2))]
+        re_ = [rel(refs[i][1], e[b.off_e[i]:b.off_e[i + 1]]) for i in range(len(sub2))]
+        b.close()
+    replay = {"what": "the mixed batch replaying each instance's FP64 step sizes (%d accepted "
+                      "steps): the precision alone" % nrep,
+              "instances": len(sub2), "rel_l2_v_worst": max(rv), "rel_l2_e_worst": max(re_)}
+    return {"instances": len(sub), "sizes": sorted({c["n"][0] for c in sub}),
+            "replay": replay, "free_running": free}
 
 
 WINDOWS = {"sedov2d_8": None, "tg2d_64": 50, "sedov3d_32": 20, "gresho2d_256": 20}
@@ -837,7 +880,45 @@ def run_native(args):
         line["rom"] = rom
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_sweep()
+    if world == 1 and args.cpu_configs:
+        line["cpu_configs"] = cpu_configs()
     return line
+
+
+def cpu_configs(seconds=6.0):
+    """The oracle on the single-problem workloads, as it stands: one core
+    (accepted steps from the initial state for about `seconds`) and all host
+    cores (one independent copy of the problem per core, spawned processes,
+    the same accepted steps each); DOF-updates/s with the core count."""
+    import oracle as O
+    from paper_2104_11404_gb300 import workloads as W
+    from tests._pair import oracle_for
+    nproc = os.cpu_count() or 1
+    out = {}
+    for name in WINDOWS:
+        cfg = W.CONFIGS[name]
+        o = oracle_for(cfg)
+        v, e, x = o.init_state()
+        N = 2 * o.nv + o.ne
+        t0 = time.time()
+        total, dt, t = 0, 0.0, 0.0
+        while time.time() - t0 < seconds and t < cfg["t_final"]:
+            st, _, s_ = o.run(cfg["t_final"], v, e, x, t0=t, dt=dt, max_steps=1)
+            if s_ != O.OK:
+                break
+            total += st["steps"]
+            dt, t = st["dt"], st["t"]
+        one = N * total / (time.time() - t0)
+        del o
+        pool = OraclePool([dict(cfg) for _ in range(nproc)], nproc, cfg["t_final"])
+        try:
+            steps_each = max(1, min(total, 20))
+            upd, el = pool.advance(steps_each)
+        finally:
+            pool.close()
+        out[name] = {"one_core": one, "all_cores": upd / el, "cores": pool.cores,
+                     "steps_one_core": total, "steps_each_all_cores": steps_each}
+    return out
 
 
 def run_reference(args):
@@ -891,6 +972,9 @@ def main():
     ap.add_argument("--full-runs", action="store_true",
                     help="also run every single-problem workload to its final time in FP64 "
                          "and mixed (several minutes)")
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="also time the oracle on each single-problem workload, one core and "
+                         "all host cores")
     ap.add_argument("--quick", action="store_true",
                     help="the headline sweep only (no FP64 sweep, single-problem rates, "
                          "restricted force or full runs)")

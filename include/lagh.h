@@ -133,8 +133,8 @@ typedef struct lh_phys_desc {
   double q1, q2;         /* linear and quadratic viscosity coefficients */
   double cg_rtol;        /* stop when ||r||_2 <= cg_rtol ||b||_2 */
   double dt_min_frac;    /* dt < dt_min_frac * t_final -> LH_EDTMIN */
-  int32_t cg_precond;    /* LH_PRECOND_TENSOR (default), LH_PRECOND_TENSOR64, LH_PRECOND_EXACT
-                            or LH_PRECOND_JACOBI */
+  int32_t cg_precond;    /* LH_PRECOND_AUTO (default), LH_PRECOND_TENSOR,
+                            LH_PRECOND_TENSOR64, LH_PRECOND_EXACT or LH_PRECOND_JACOBI */
   int32_t direct_launch; /* 0 (default): each step attempt is one CUDA graph launch
                             (the CG iterations a WHILE node inside it); 1: the same
                             kernels launched one by one, with a host poll of the CG
@@ -164,7 +164,9 @@ typedef struct lh_phys_desc {
  * inverse diagonal.  Meshes where rho0 |J0| varies use
  * JACOBI whatever is asked. */
 enum { LH_PRECOND_JACOBI = 0, LH_PRECOND_TENSOR = 1, LH_PRECOND_EXACT = 2,
-       LH_PRECOND_TENSOR64 = 3 };
+       LH_PRECOND_TENSOR64 = 3,
+       LH_PRECOND_AUTO = 4  /* EXACT in 3D, TENSOR in 2D (the faster measured on the
+                               3D blast 32^3 and the 2D workloads) */ };
 
 typedef struct lh_layout_info {
   int64_t nv;            /* N_V = dim * nnodes */

@@ -25,7 +25,7 @@ namespace lagh {
 template <int DIM, int K, bool MIXED>
 static cudaError_t launch_force_t(const lh_ctx* c, const ForceArgs& fa, cudaStream_t s) {
   using F = FL<DIM, K, MIXED>;
-  auto kern = force_kernel<DIM, K, MIXED>;
+  using F1 = FL<DIM, K, MIXED, F::TEAM>;  // one element per block
   if (fa.nslots == 0) return cudaSuccess;
   ForceKParams prm;
   prm.g = c->g;
@@ -35,7 +35,17 @@ static cudaError_t launch_force_t(const lh_ctx* c, const ForceArgs& fa, cudaStre
   prm.a.gammaE = c->a.gammaE;
   prm.rho0K = c->a.rho0K;
   int64_t blocks = (fa.nslots + F::EPB - 1) / F::EPB;
-  return launch_k(c->use_pdl != 0, kern, dim3((unsigned)blocks), dim3(F::NT), F::BYTES, s, prm);
+  // a short element list (a sampled subset) would leave most SMs idle with
+  // several elements per block: one element per block spreads it out (each
+  // element's arithmetic is the same either way).  Only for teams of whole
+  // warps (3D Q2: 64 threads), so every warp-level primitive sees full warps.
+  if constexpr (F::TEAM % 32 == 0) {
+    if (fa.list != nullptr && F::EPB > 1 && blocks < c->num_sms)
+      return launch_k(c->use_pdl != 0, force_kernel<DIM, K, MIXED, F::TEAM>,
+                      dim3((unsigned)fa.nslots), dim3(F1::NT), F1::BYTES, s, prm);
+  }
+  return launch_k(c->use_pdl != 0, force_kernel<DIM, K, MIXED>, dim3((unsigned)blocks),
+                  dim3(F::NT), F::BYTES, s, prm);
 }
 
 #define LAGH_DISPATCH(DIMV, KV, FN, ...)                                            \
@@ -112,6 +122,13 @@ static cudaError_t prepare_t() {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)FL<DIM, K, MIXED>::BYTES);
   if (e != cudaSuccess) return e;
+  constexpr int TEAM = FL<DIM, K, MIXED>::TEAM;
+  if constexpr (TEAM % 32 == 0) {
+    e = cudaFuncSetAttribute(force_kernel<DIM, K, MIXED, TEAM>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)FL<DIM, K, MIXED, TEAM>::BYTES);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(energy_update_kernel<DIM, K, MIXED>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)EL<DIM, K, MIXED>::BYTES);

@@ -621,11 +621,11 @@ l2_part:
   team_sync<TEAM>();  // the team reuses its element area in the next tile
 }
 
-template <int DIM, int K, bool MIXED>
-__global__ void __launch_bounds__(FL<DIM, K, MIXED>::NT)
+template <int DIM, int K, bool MIXED, int NTT = 256>
+__global__ void __launch_bounds__(FL<DIM, K, MIXED, NTT>::NT)
 force_kernel(const ForceKParams prm) {
   pdl_enter();
-  using F = FL<DIM, K, MIXED>;
+  using F = FL<DIM, K, MIXED, NTT>;
   if (prm.a.ctl != nullptr && prm.a.ctl->done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   force_tables<DIM, K, MIXED, F::NT>(prm.b, smem);

@@ -17,7 +17,8 @@ LH_OK, LH_EINVAL, LH_ENOMEM, LH_ECUDA, LH_ETANGLED, LH_ENONFINITE, LH_EDTMIN, LH
 LH_FP64, LH_MIXED = 0, 1
 LH_SEDOV, LH_TAYLOR_GREEN, LH_GRESHO, LH_UNIFORM, LH_TRIPLE_POINT = 1, 2, 3, 4, 5
 LH_RK2AVG, LH_RK4 = 0, 1
-LH_PRECOND_JACOBI, LH_PRECOND_TENSOR, LH_PRECOND_EXACT, LH_PRECOND_TENSOR64 = 0, 1, 2, 3
+LH_PRECOND_JACOBI, LH_PRECOND_TENSOR, LH_PRECOND_EXACT, LH_PRECOND_TENSOR64, LH_PRECOND_AUTO = \
+    0, 1, 2, 3, 4
 
 # every entry point declared in include/lagh.h
 API_NAMES = [

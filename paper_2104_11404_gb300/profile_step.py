@@ -7,7 +7,7 @@ that contain conditional nodes, which is how the library normally runs).
 
 --batch runs the 512-instance point-blast sweep through the batched form
 instead (its attempt graph holds kernel nodes only, so profilers see them);
---tuning threads,ctas_per_sm,smem_lines fixes the launch shape (no autotuner
+--tuning threads,ctas_per_sm,smem_lines[,qpt] fixes the launch shape (no autotuner
 launches before the profiled ones).  --apply N instead applies the CG
 preconditioner N times to a random vector (the plain band passes, as bench.py
 times them for its roofline line).
@@ -27,7 +27,7 @@ def main():
     ap.add_argument("--graph", action="store_true", help="keep the CUDA graph launches")
     ap.add_argument("--batch", action="store_true", help="the batched point-blast sweep")
     ap.add_argument("--instances", type=int, default=512)
-    ap.add_argument("--tuning", default="", help="threads,ctas_per_sm,smem_lines")
+    ap.add_argument("--tuning", default="", help="threads,ctas_per_sm,smem_lines[,qpt]")
     ap.add_argument("--precond", type=int, default=-1,
                     help="cg_precond (0 Jacobi, 1 tensor bands, 2 exact); default: the library's")
     ap.add_argument("--apply", type=int, default=0,
@@ -78,8 +78,8 @@ def run_batch(args):
     torch.cuda.set_device(0)
     tuning = None
     if args.tuning:
-        t, c, sl = (int(v) for v in args.tuning.split(","))
-        tuning = dict(threads=t, ctas_per_sm=c, smem_lines=sl)
+        f = [int(v) for v in args.tuning.split(",")]
+        tuning = dict(threads=f[0], ctas_per_sm=f[1], smem_lines=f[2], qpt=f[3] if len(f) > 3 else 1)
     b = Batch(W.batch_instances(args.instances), precision=args.precision, tuning=tuning)
     b.init_state()
     if tuning is None:
