@@ -102,13 +102,13 @@ def test_cg_preconditioners_agree(dim, k, n):
 
 @pytest.mark.parametrize("dim,k,n", SMALL)
 def test_precond_apply_approximates_mass_inverse(dim, k, n):
+    from paper_2104_11404_gb300 import lagh
     cfg = _cfg(dim, k, n)
     o = oracle_for(cfg)
-    g = gpu_for(cfg)
+    g = gpu_for(cfg, phys_overrides={"cg_precond": lagh.LH_PRECOND_TENSOR})
     b = np.random.default_rng(11 + dim + k).normal(size=o.nv)
     xo, _, _, _ = o.mass_solve_v(b)
     out = g.zeros_v()
-    from paper_2104_11404_gb300 import lagh
     lagh.lh_precond_apply(g.ctx, dev(b), out)
     z = host(out)
     assert np.all(z[W.essential_mask(cfg)] == 0.0)
