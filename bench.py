@@ -555,18 +555,33 @@ def measure_sweep_accuracy(stream, count=12, max_n=24):
             v, e, _, _, _ = g.get_state()
             refs.append((v.cpu().numpy(), e.cpu().numpy()))
             g.close()
-        b = Batch(sub2, precision="mixed", stream=stream)
-        b.init_state()
-        for k in range(nrep):
-            b.step_fixed(np.array([l[k] for l in logs]))
-        v, e, _ = b.get_state()
-        v, e = v.cpu().numpy(), e.cpu().numpy()
-        rv = [rel(refs[i][0], v[b.off_v[i]:b.off_v[i + 1]]) for i in range(len(sub2))]
-        re_ = [rel(refs[i][1], e[b.off_e[i]:b.off_e[i + 1]]) for i in range(len(sub2))]
-        b.close()
+        out = {}
+        for label, prec, perturb in (("mixed", "mixed", False), ("fp64_perturbed", "fp64", True)):
+            b = Batch(sub2, precision=prec, stream=stream)
+            b.init_state()
+            if perturb:
+                # the conditioning of the problem: the FP64 run from an initial
+                # energy perturbed by a seeded 1e-7 relative amount
+                v0, e0, x0 = b.get_state()
+                gen = torch.Generator(device="cuda").manual_seed(2104)
+                noise = 2.0 * torch.rand(e0.shape, generator=gen, device="cuda",
+                                         dtype=torch.float64) - 1.0
+                b.set_state(v0, e0 * (1.0 + 1e-7 * noise), x0)
+            for k in range(nrep):
+                b.step_fixed(np.array([l[k] for l in logs]))
+            v, e, _ = b.get_state()
+            v, e = v.cpu().numpy(), e.cpu().numpy()
+            out[label] = ([rel(refs[i][0], v[b.off_v[i]:b.off_v[i + 1]]) for i in range(len(sub2))],
+                          [rel(refs[i][1], e[b.off_e[i]:b.off_e[i + 1]]) for i in range(len(sub2))])
+            b.close()
     replay = {"what": "the mixed batch replaying each instance's FP64 step sizes (%d accepted "
                       "steps): the precision alone" % nrep,
-              "instances": len(sub2), "rel_l2_v_worst": max(rv), "rel_l2_e_worst": max(re_)}
+              "instances": len(sub2), "rel_l2_v": out["mixed"][0], "rel_l2_e": out["mixed"][1],
+              "rel_l2_v_worst": max(out["mixed"][0]), "rel_l2_e_worst": max(out["mixed"][1]),
+              "conditioning": {"what": "the FP64 batch from an initial energy perturbed by 1e-7 "
+                                       "(relative, seeded), same step sizes",
+                               "rel_l2_v": out["fp64_perturbed"][0],
+                               "rel_l2_e": out["fp64_perturbed"][1]}}
     return {"instances": len(sub), "sizes": sorted({c["n"][0] for c in sub}),
             "replay": replay, "free_running": free}
 
