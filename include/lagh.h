@@ -429,8 +429,9 @@ LH_API lh_status lh_rom_run_to(lh_rom* rom, double t_final, int64_t max_steps,
  * S (device, column-major m x n: n snapshots of m entries), offset (device,
  * m entries, may be NULL): the thin SVD of S - offset 1^T is computed by
  * one-sided Jacobi (parallel round-robin sweeps of column-pair rotations until
- * every pair is orthogonal to 1e-15 relative; columns at 1e-16 of the
- * Frobenius norm count as null space).  Outputs: U (device, m x n,
+ * every pair is orthogonal to sqrt(m) 2^-52 relative, the rounding level of
+ * an m-term inner product; columns at 1e-16 of the Frobenius norm count as
+ * null space).  Outputs: U (device, m x n,
  * column-major) the left singular vectors in descending singular-value order
  * (zero columns for zero singular values), sigma (device, n) the singular
  * values in that order, *k (host) the smallest basis size whose singular-value

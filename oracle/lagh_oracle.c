@@ -1397,7 +1397,8 @@ int lho_pod(long m, long n, const double* S, const double* offset, double eps, d
   for (long j = 0; j < n; ++j)
     for (long i = 0; i < m; ++i) A[j * m + i] = S[j * m + i] - (offset ? offset[i] : 0.0);
   int sweeps;
-  int st = lho_svd_jacobi(m, n, A, sg, 1e-15, 60, &sweeps);
+  /* orthogonality at the rounding level of an m-term inner product */
+  int st = lho_svd_jacobi(m, n, A, sg, sqrt((double)m) * 2.220446049250313e-16, 60, &sweeps);
   /* descending order (stable: equal values keep their column order) */
   for (long j = 0; j < n; ++j) order[j] = j;
   for (long a = 1; a < n; ++a) {

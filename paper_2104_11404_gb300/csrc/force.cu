@@ -105,6 +105,24 @@ static cudaError_t launch_energy_t(const lh_ctx* c, const EnergyArgs& ea, cudaSt
 }
 
 template <int DIM, int K>
+static cudaError_t launch_ftv_list_dk(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s) {
+  using F = EL<DIM, K, false>;
+  if (ea.nslots == 0) return cudaSuccess;
+  EnergyKParams prm;
+  prm.g = c->g;
+  prm.b = c->basis;
+  prm.a = ea;
+  prm.rho0K = c->a.rho0K;
+  int64_t blocks = (ea.nslots + F::EPB - 1) / F::EPB;
+  return launch_k(c->use_pdl != 0, energy_update_kernel<DIM, K, false>, dim3((unsigned)blocks),
+                  dim3(F::NT), F::BYTES, s, prm);
+}
+
+cudaError_t launch_ftv_list(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s) {
+  LAGH_DISPATCH(c->g.dim, c->g.k, launch_ftv_list_dk, c, ea, s);
+}
+
+template <int DIM, int K>
 static cudaError_t launch_energy_dk(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s) {
   if (c->precision == LH_MIXED) return launch_energy_t<DIM, K, true>(c, ea, s);
   return launch_energy_t<DIM, K, false>(c, ea, s);

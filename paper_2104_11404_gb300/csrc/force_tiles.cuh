@@ -865,10 +865,12 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   float* whs = reinterpret_cast<float*>(ep);  // mixed: w split into two floats
   float* wls = whs + DIM * ND1;
 
-  const int64_t el = el0 + le;
-  const bool active = le < F::EPB && el < g.nelem;
+  // slot el0 + le: the element itself, or (list mode) the listed element
+  const int64_t slot = el0 + le;
+  const bool active = le < F::EPB && slot < (A.list ? A.nslots : g.nelem);
+  const int64_t el = active ? (A.list ? (int64_t)A.list[slot] : slot) : 0;
   int E[3] = {0, 0, 0};
-  elem_ijk(g, active ? el : 0, E);
+  elem_ijk(g, el, E);
   const int nstage = (pref != 0.0) ? 2 * DIM * ND1 : DIM * ND1;
   if (active) {  // loads first, then the shared-memory stores
     constexpr int PS = (2 * DIM * ND1 + NQD - 1) / NQD;
@@ -962,6 +964,12 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
     }
     team_sync<NQD>();
     l2_contract<DIM, K, NQD>(gq, l2s, Ls, tq, active, ftv, false);
+  }
+  if (A.FTvE != nullptr) {  // list mode: the element rows of F^T w only
+    if (active)
+      for (int j = tq; j < ND2; j += NQD) A.FTvE[slot * ND2 + j] = ftv[j];
+    team_sync<NQD>();
+    return;
   }
   if (active && tq == 0) crs[0] = A.rho0Kinv ? coef * A.rho0Kinv[el] : coef / rho0Kp[el];
   team_sync<NQD>();

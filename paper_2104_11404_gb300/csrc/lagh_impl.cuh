@@ -253,10 +253,16 @@ struct EnergyArgs {
   double frac;
   double dt;
   int rate;              // 1: e_out = frac M_E^{-1} (F^T w + src) (no dt, e_base unused)
+  const int32_t* list;   // list mode (with FTvE): the elements whose F^T w rows are wanted
+  int64_t nslots;
+  double* FTvE;          // list mode output: F^T w element rows [slot][j] (from the stored D)
   const Ctl* ctl;
   const double* rho0Kinv;  // 1 / (rho0 |J0|) per element (NULL: divide)
 };
 cudaError_t launch_energy_update(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s);
+// F^T w element rows of the listed elements from the stress weights D that the
+// FP64 force kernel stored for them (ea.list, ea.nslots, ea.FTvE, ea.w, ea.D).
+cudaError_t launch_ftv_list(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s);
 
 // Mass operations.
 cudaError_t launch_mass_apply(const lh_ctx* c, const double* in, double* out, cudaStream_t s);

@@ -9,8 +9,9 @@
 // disjoint and every pair meets once per sweep.  One CTA per pair computes
 // the three inner products (fixed-order block sums), the rotation that makes
 // the pair orthogonal, and rotates both columns in place.  Sweeps repeat until
-// no pair needed a rotation (|a_p . a_q| <= tol |a_p| |a_q|, or a column at
-// the rounding level of the whole matrix).  The left singular vectors are the
+// no pair needed a rotation (|a_p . a_q| <= sqrt(m) 2^-52 |a_p| |a_q|, the
+// rounding level of the inner product, or a column at the rounding level of
+// the whole matrix).  The left singular vectors are the
 // final columns divided by their norms; no right singular vectors are formed.
 #include "lagh_impl.cuh"
 
@@ -164,11 +165,14 @@ extern "C" lh_status lh_pod(const double* S, int64_t m, int64_t n, const double*
   if (cudaGetLastError() != cudaSuccess) return LH_ECUDA;
   const int64_t N = (n + 1) / 2 * 2, M = N - 1;
   const int max_sweeps = 60;
+  // orthogonality at the rounding level of an m-term inner product (a fixed
+  // 1e-15 sits below it for long columns, and the sweeps then chase noise)
+  const double tol = sqrt((double)m) * 2.220446049250313e-16;
   int sweep = 0, hflag = 1;
   for (sweep = 1; sweep <= max_sweeps && n > 1; ++sweep) {
     if (cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) return LH_ECUDA;
     for (int64_t r = 0; r < M; ++r)
-      pod_round_kernel<<<(unsigned)(N / 2), kPodThreads, 0, s>>>(A, m, n, N, r, scal, 1e-15, flag);
+      pod_round_kernel<<<(unsigned)(N / 2), kPodThreads, 0, s>>>(A, m, n, N, r, scal, tol, flag);
     if (cudaGetLastError() != cudaSuccess) return LH_ECUDA;
     if (cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)

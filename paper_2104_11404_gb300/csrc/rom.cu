@@ -13,13 +13,14 @@
 // gather a sampled entry from the element rows of the restricted force; and
 // C = Phi_x^T Phi_v, b = Phi_x^T v_os for the position equation.
 //
-// Online step (one CUDA graph per attempt, every scalar on the device):
+// Online step (one CUDA graph per attempt, every scalar on the device; one
+// restricted force evaluation per stage):
 //   stage s = 0, 1:
 //     lift the stage coordinates at the sampled rows (eq:discretesolrepresentation)
 //     restricted force on the sampled elements -> F.1 at Z_F, estimate
 //     f = A_F Z_F^T F.1 and the velocity update (single CTA)
 //     lift the test velocity (v^{n+1/2}, then the average) at the sampled rows
-//     restricted force with that test vector -> F^T w at Z_G
+//     F^T w of the sampled elements from the stress weights the force kept -> F^T w at Z_G
 //     g = A_G Z_G^T F^T w and the energy and position updates (single CTA)
 //   control (Section 2.2.3) and commit.
 #include <math.h>
@@ -363,6 +364,7 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
     f.v = r->vF; f.e = r->eF; f.x = r->xF; f.vtest = nullptr;
     f.list = r->sel; f.nslots = r->nsel;
     f.F1E = r->F1E;
+    f.D = c->a.D;  // stress weights of the sampled elements, for F^T w below
     f.tau_bits = &r->ctl->tau_bits[st];
     f.status = &r->ctl->status;
     f.ctl = r->ctl;
@@ -384,12 +386,15 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
                       (const double*)r->Pv, (const double*)r->vos, (const int64_t*)r->rows_v, cw,
                       r->wF, (const Ctl*)r->ctl)) != cudaSuccess)
       return e;
-    ForceArgs f2 = f;
-    f2.vtest = r->wF;
-    f2.FTvE = r->FTvE;
-    f2.tau_bits = nullptr;
-    f2.status = nullptr;
-    if ((e = launch_force(c, f2, s)) != cudaSuccess) return e;
+    // F^T w of the same force (the stress weights the force kernel kept)
+    EnergyArgs ea = {};
+    ea.w = r->wF;
+    ea.D = c->a.D;
+    ea.list = r->sel;
+    ea.nslots = r->nsel;
+    ea.FTvE = r->FTvE;
+    ea.ctl = r->ctl;
+    if ((e = launch_ftv_list(c, ea, s)) != cudaSuccess) return e;
     rs.which = 1;
     if ((e = launch_k(pdl, rom_update_kernel, dim3(1), dim3(256), zsm, s, rs, r->nbv, r->nbe, r->nbx,
                       r->nsf, r->nsg, (const double*)r->F1E, (const double*)r->FTvE,
