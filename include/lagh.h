@@ -484,7 +484,8 @@ LH_API lh_status lh_peak_probe(int32_t fp64, int64_t iters, void* sink, void* st
  * stream).  tuning: NULL (or threads == 0) for the default launch shape, to be
  * replaced by lh_batch_autotune; otherwise a fixed shape.  Allocates every
  * array, including per-CTA scratch sized by the largest instance.  Errors:
- * LH_EINVAL, LH_EUNSUPPORTED, LH_ENOMEM, LH_ECUDA.  *out is NULL on failure. */
+ * LH_EINVAL, LH_EUNSUPPORTED (also: an instance with 2^31 or more velocity
+ * unknowns), LH_ENOMEM, LH_ECUDA.  *out is NULL on failure. */
 LH_API lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
                                  const lh_disc_desc* disc, const lh_phys_desc* phys,
                                  int32_t precision, void* stream,

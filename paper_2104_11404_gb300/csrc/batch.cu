@@ -396,6 +396,8 @@ extern "C" lh_status lh_batch_create(int32_t n, const lh_mesh_desc* meshes,
     if (p.integrator != LH_RK2AVG)
       return fail(LH_EUNSUPPORTED, "the batched form runs the RK2-average integrator");
     if (!(p.cg_rtol > 0.0) || p.cg_maxit < 1) return fail(LH_EINVAL, "bad CG settings");
+    if (g.nv >= (int64_t(1) << 31))
+      return fail(LH_EUNSUPPORTED, "an instance of the batched form holds fewer than 2^31 velocity unknowns");
     BInst& I = b->inst[i];
     memset(&I, 0, sizeof(I));
     I.g = g;

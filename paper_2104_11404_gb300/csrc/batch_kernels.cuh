@@ -117,49 +117,73 @@ __device__ __forceinline__ void load_instance(const BatchArgs& a, int i, BInst* 
   __syncthreads();
 }
 
+// Multi-index of a node of an instance (32-bit: an instance of the batched
+// form holds fewer than 2^31 velocity unknowns).
+__device__ __forceinline__ void node_ijk32(const Geom& g, int node, int I[3]) {
+  const int n0 = g.nn[0], n1 = g.nn[1];
+  const int r = node / n0;
+  I[0] = node - r * n0;
+  I[1] = r % n1;
+  I[2] = r / n1;
+}
+
 // z_c = scale (G^-1 (x) ... (x) G^-1) r_c on the free entries of component c
 // (zero on its wall-normal nodes) for every component: the 1D solves along
 // each direction in turn, every node line independent.  mode 2: all
 // components staged in buf (DIM nnodes doubles of shared memory) and solved
 // together; mode 1: one component at a time in buf (nnodes doubles); mode 0:
-// in place on z in device memory.
+// in place on z in device memory.  With Pv and rz given, the copy-out also
+// sets Pv = z and adds this thread's share of r . z to *rz.
 template <int DIM, int K>
 __device__ void tensor_solve(const Geom& g, const double* __restrict__ fac,
                              const int64_t (*fo)[2], double scale, const double* r, double* z,
-                             double* buf, int mode) {
+                             double* buf, int mode, double* Pv = nullptr, double* rz = nullptr) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t nn = g.nnodes;
+  const int nn = (int)g.nnodes;
   const int cpass = mode == 2 ? DIM : 1;  // components per pass
+  double rzl = 0.0;
   for (int c0 = 0; c0 < DIM; c0 += cpass) {
-    double* w = mode == 0 ? z + c0 * nn : buf;  // holds components c0 .. c0 + cpass - 1
-    for (int64_t idx = tid; idx < cpass * nn; idx += nt) {
-      const int c = c0 + (int)(idx / nn);
-      const int64_t node = idx - (int64_t)(c - c0) * nn;
+    double* w = mode == 0 ? z + (int64_t)c0 * nn : buf;  // holds components c0 .. c0 + cpass - 1
+    for (int node = tid; node < nn; node += nt) {
       int I[3];
-      node_ijk(g, node, I);
-      w[idx] = (I[c] == 0 || I[c] == g.nn[c] - 1) ? 0.0 : r[c * nn + node];
+      node_ijk32(g, node, I);
+      for (int cc = 0; cc < cpass; ++cc) {
+        const int c = c0 + cc;
+        w[cc * nn + node] = (I[c] == 0 || I[c] == g.nn[c] - 1) ? 0.0 : r[c * nn + node];
+      }
     }
     __syncthreads();
     for (int d = 0; d < DIM; ++d) {
-      const int64_t nlines = nn / g.nn[d];
+      const int nlines = nn / g.nn[d];
       const int64_t stride = d == 0 ? 1 : (d == 1 ? (int64_t)g.nn[0] : (int64_t)g.nn[0] * g.nn[1]);
-      for (int64_t li = tid; li < cpass * nlines; li += nt) {
-        const int c = c0 + (int)(li / nlines);
-        const int64_t line = li - (int64_t)(c - c0) * nlines;
+      for (int li = tid; li < cpass * nlines; li += nt) {
+        const int cc = li / nlines, c = c0 + cc;
+        const int line = li - cc * nlines;
         const int var = (d == c) ? 1 : 0;
         int I[3] = {0, 0, 0};
-        if (d == 0) { I[1] = (int)(line % g.nn[1]); I[2] = (int)(line / g.nn[1]); }
-        else if (d == 1) { I[0] = (int)(line % g.nn[0]); I[2] = (int)(line / g.nn[0]); }
-        else { I[0] = (int)(line % g.nn[0]); I[1] = (int)(line / g.nn[0]); }
+        if (d == 0) { I[1] = line % g.nn[1]; I[2] = line / g.nn[1]; }
+        else if (d == 1) { I[0] = line % g.nn[0]; I[2] = line / g.nn[0]; }
+        else { I[0] = line % g.nn[0]; I[1] = line / g.nn[0]; }
         if (d != c && (I[c] == 0 || I[c] == g.nn[c] - 1)) continue;  // essential line
-        line_solve<K>(w + (int64_t)(c - c0) * nn + node_index(g, I[0], I[1], I[2]) + var * stride,
+        line_solve<K>(w + (int64_t)cc * nn + node_index(g, I[0], I[1], I[2]) + var * stride,
                       stride, g.nn[d] - 2 * var, fac + fo[d][var]);
       }
       __syncthreads();
     }
-    for (int64_t idx = tid; idx < cpass * nn; idx += nt) z[c0 * nn + idx] = scale * w[idx];
+    const int64_t o = (int64_t)c0 * nn;
+    if (Pv != nullptr) {
+      for (int idx = tid; idx < cpass * nn; idx += nt) {
+        const double zv = scale * w[idx];
+        z[o + idx] = zv;
+        Pv[o + idx] = zv;
+        rzl = fma(r[o + idx], zv, rzl);
+      }
+    } else {
+      for (int idx = tid; idx < cpass * nn; idx += nt) z[o + idx] = scale * w[idx];
+    }
     __syncthreads();
   }
+  if (rz != nullptr) *rz = rzl;
 }
 
 // Shared-memory plan of the stage kernel (bytes of each phase; the phases
@@ -188,19 +212,21 @@ struct BL {
 // (M1 x M1) p_K is formed in registers and added to its nodes.  The elements
 // are taken in four colours (parity of the element indices), so no two
 // elements of one colour share a node and every node receives its (at most
-// four) contributions in colour order: the sums are deterministic.  Writes
-// AP (zero on the wall-normal entries) and returns p . Ap.
+// four) contributions in colour order: the sums are deterministic.  The
+// second factor's table M1r is rho0 |J0| M1 (uniform in an instance) and its
+// products are accumulated onto the node sums directly.  Writes AP (zero on
+// the wall-normal entries) and returns p . Ap.
 template <int K>
-__device__ double cta_mass_colored(const Geom& g, const double* M1s, double rho0K,
+__device__ double cta_mass_colored(const Geom& g, const double* M1s, const double* M1r,
                                    const double* Pv, double* AP, double* buf) {
   constexpr int P = K + 1;
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int64_t nn = g.nnodes;
+  const int nn = (int)g.nnodes, n0 = g.nn[0];
   double* pc = buf;
   double* ac = buf + nn;
   double pap = 0.0;
   for (int c = 0; c < 2; ++c) {
-    for (int64_t node = tid; node < nn; node += nt) {
+    for (int node = tid; node < nn; node += nt) {
       pc[node] = Pv[c * nn + node];
       ac[node] = 0.0;
     }
@@ -209,14 +235,15 @@ __device__ double cta_mass_colored(const Geom& g, const double* M1s, double rho0
       const int bx = color & 1, by = color >> 1;
       const int mx = (g.n[0] - bx + 1) / 2, my = (g.n[1] - by + 1) / 2;
       for (int item = tid; item < mx * my; item += nt) {
-        const int ex = 2 * (item % mx) + bx, ey = 2 * (item / mx) + by;
-        const int64_t base = (int64_t)ex * K + (int64_t)g.nn[0] * ((int64_t)ey * K);
+        const int iy = item / mx;
+        const int ex = 2 * (item - iy * mx) + bx, ey = 2 * iy + by;
+        const int base = ex * K + n0 * (ey * K);
         double t[P][P];
 #pragma unroll
         for (int b = 0; b < P; ++b) {
           double u[P];
 #pragma unroll
-          for (int a = 0; a < P; ++a) u[a] = pc[base + (int64_t)g.nn[0] * b + a];
+          for (int a = 0; a < P; ++a) u[a] = pc[base + n0 * b + a];
 #pragma unroll
           for (int ap = 0; ap < P; ++ap) {
             double acc = 0.0;
@@ -229,20 +256,20 @@ __device__ double cta_mass_colored(const Geom& g, const double* M1s, double rho0
         for (int bp = 0; bp < P; ++bp)
 #pragma unroll
           for (int ap = 0; ap < P; ++ap) {
-            double acc = 0.0;
+            double acc = ac[base + n0 * bp + ap];
 #pragma unroll
-            for (int b = 0; b < P; ++b) acc = fma(M1s[bp * P + b], t[b][ap], acc);
-            ac[base + (int64_t)g.nn[0] * bp + ap] += acc;
+            for (int b = 0; b < P; ++b) acc = fma(M1r[bp * P + b], t[b][ap], acc);
+            ac[base + n0 * bp + ap] = acc;
           }
       }
       __syncthreads();
     }
-    for (int64_t node = tid; node < nn; node += nt) {
-      const int i0 = (int)(node % g.nn[0]), i1 = (int)(node / g.nn[0]);
+    for (int node = tid; node < nn; node += nt) {
+      const int i1 = node / n0, i0 = node - i1 * n0;
       const int ic = c == 0 ? i0 : i1;
-      const double ap = (ic == 0 || ic == g.nn[c] - 1) ? 0.0 : rho0K * ac[node];
+      const double ap = (ic == 0 || ic == g.nn[c] - 1) ? 0.0 : ac[node];
       AP[c * nn + node] = ap;
-      pap += pc[node] * ap;
+      pap = fma(pc[node], ap, pap);
     }
     __syncthreads();
   }
@@ -270,7 +297,12 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* __restrict__ R
   double* t = u + CGT * DIM * ND1;
   double* y = t + CGT * DIM * ND1;
   double* lines = a.smem_lines ? y + CGT * DIM * ND1 : nullptr;
-  for (int i = tid; i < P * P; i += NTT) M1s[i] = M1[(i / P) * (kMaxOrder + 1) + i % P];
+  double* M1r = t;  // 2D shared-memory apply: rho0 |J0| M1 (the tile buffers are unused there)
+  for (int i = tid; i < P * P; i += NTT) {
+    const double m = M1[(i / P) * (kMaxOrder + 1) + i % P];
+    M1s[i] = m;
+    M1r[i] = I.rho0K * m;
+  }
   double bb = 0.0;
 #pragma unroll 4
   for (int64_t k = tid; k < nv; k += NTT) {
@@ -284,14 +316,8 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* __restrict__ R
     *conv = true;
     return 0;
   }
-  tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines, a.smem_lines);
-  double rz = 0.0;
-#pragma unroll 4
-  for (int64_t k = tid; k < nv; k += NTT) {
-    const double zv = Z[k];
-    Pv[k] = zv;
-    rz += R[k] * zv;
-  }
+  double rz;
+  tensor_solve<DIM, K>(g, a.fac, I.fac, I.scale, R, Z, lines, a.smem_lines, Pv, &rz);
   rz = cta_sum(rz);
   int it = 0;
   double rr = bb;
@@ -301,7 +327,7 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* __restrict__ R
     double pap;
     if (DIM == 2 && a.smem_lines == 2) {
       // A p on shared-memory node arrays (rho0 |J0| is uniform in an instance)
-      pap = cta_mass_colored<K>(g, M1s, I.rho0K, Pv, AP, lines);
+      pap = cta_mass_colored<K>(g, M1s, M1r, Pv, AP, lines);
     } else {
       // element phase (tiles of CGT elements), then the node gather
       for (int64_t el0 = 0; el0 < g.nelem; el0 += CGT) {
@@ -309,9 +335,9 @@ __device__ int cta_cg(const BatchArgs& a, const BInst& I, double* __restrict__ R
         mass_elements<DIM, K>(g, M1s, Pv, rho0K, ApE, el0, nel, u, t, y);
       }
       pap = 0.0;
-      for (int64_t node = tid; node < nn; node += NTT) {
+      for (int node = tid; node < (int)nn; node += NTT) {
         int Ix[3];
-        node_ijk(g, node, Ix);
+        node_ijk32(g, node, Ix);
         for (int c = 0; c < DIM; ++c) {
           const int64_t k = c * nn + node;
           const double ap = essential(g, Ix, c) ? 0.0 : gather_node<DIM, K>(g, ApE, Ix, c);
@@ -412,9 +438,9 @@ __global__ void __launch_bounds__(NTT) batch_stage_kernel(const BatchArgs a, con
     double* Z = vec + 2 * g.nv;
     double* Pv = vec + 3 * g.nv;
     double* AP = vec + 4 * g.nv;
-    for (int64_t node = tid; node < g.nnodes; node += NTT) {
+    for (int node = tid; node < (int)g.nnodes; node += NTT) {
       int Ix[3];
-      node_ijk(g, node, Ix);
+      node_ijk32(g, node, Ix);
       for (int c = 0; c < DIM; ++c)
         R[c * g.nnodes + node] = essential(g, Ix, c) ? 0.0 : -gather_node<DIM, K>(g, F1E, Ix, c);
     }

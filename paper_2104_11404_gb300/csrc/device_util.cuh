@@ -75,7 +75,8 @@ __device__ __forceinline__ int node_elems_1d(int I, int nel, int* el, int* loc) 
 }
 
 // Deterministic gather of an element-local kinematic vector E[el][c][i] at one
-// node: the contributions of the <= 2^DIM elements are summed in a fixed order.
+// node: the contributions of the <= 2^DIM elements are summed in a fixed order
+// (the first one starts the sum; every node lies in at least one element).
 template <int DIM, int K>
 __device__ __forceinline__ double gather_node(const Geom& g, const double* __restrict__ E,
                                               const int I[3], int c) {
@@ -86,13 +87,30 @@ __device__ __forceinline__ double gather_node(const Geom& g, const double* __res
   int ny = node_elems_1d<K>(I[1], g.n[1], ey, ly);
   int nz = 1;
   if (DIM == 3) nz = node_elems_1d<K>(I[2], g.n[2], ez, lz);
-  double s = 0.0;
-  for (int kz = 0; kz < nz; ++kz)
-    for (int ky = 0; ky < ny; ++ky)
-      for (int kx = 0; kx < nx; ++kx) {
-        int64_t el = (int64_t)ex[kx] + (int64_t)g.n[0] * ((int64_t)ey[ky] + (int64_t)g.n[1] * ez[kz]);
-        int i = lx[kx] + P * (ly[ky] + P * lz[kz]);
-        s += E[(el * DIM + c) * ND1 + i];
+  double v[DIM == 3 ? 8 : 4];
+#pragma unroll
+  for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz)
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        const int t = (kz * 2 + ky) * 2 + kx;
+        v[t] = 0.0;
+        if (kx < nx && ky < ny && kz < nz) {
+          int64_t el = (int64_t)ex[kx] + (int64_t)g.n[0] * ((int64_t)ey[ky] + (int64_t)g.n[1] * ez[kz]);
+          int i = lx[kx] + P * (ly[ky] + P * lz[kz]);
+          v[t] = E[(el * DIM + c) * ND1 + i];
+        }
+      }
+  double s = v[0];
+#pragma unroll
+  for (int kz = 0; kz < (DIM == 3 ? 2 : 1); ++kz)
+#pragma unroll
+    for (int ky = 0; ky < 2; ++ky)
+#pragma unroll
+      for (int kx = 0; kx < 2; ++kx) {
+        const int t = (kz * 2 + ky) * 2 + kx;
+        if (t > 0 && kx < nx && ky < ny && kz < nz) s += v[t];
       }
   return s;
 }

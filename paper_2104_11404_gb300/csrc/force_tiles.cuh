@@ -654,7 +654,10 @@ __global__ void gather_kernel(Geom g, const double* __restrict__ E, double* __re
 // ------------------------------------------------------- energy update ----
 
 // e_out = e_base + coef * M_E^{-1} (F^T w + src) per element.  One team of
-// NQ^DIM threads per element (same mapping as the force kernel).
+// NQ^DIM threads per element (same mapping as the force kernel) forms F^T w;
+// the FP64 combination and M_E^{-1} then run over the tile's (element, row)
+// pairs with every lane busy (an FP64 instruction costs its warp the same
+// pipe time however few of its lanes are active).
 template <int DIM, int K, bool MIXED, int NTT = 256>
 struct EL {
   static constexpr int P = K + 1, NQ = 2 * K;
@@ -667,9 +670,11 @@ struct EL {
                                            : 2 * NFI * P * P * NQ + 3 * NFI * P * NQ * NQ;
   static constexpr int S_L2 = DIM == 2 ? K * NQ : K * NQ * NQ + K * K * NQ;
   static constexpr size_t al(size_t b) { return (b + 15) & ~size_t(15); }
+  // per element: staged fields, interpolation scratch, point integrands,
+  // L2 scratch, F^T w, the mixed path's chunk sums and reference-pressure part
   static constexpr size_t B_ELEM = al(NFI * ND1 * 8) + al(S_INTERP * 8) + al(NQD * 8) +
-                                   al(S_L2 * 8) + al(ND2 * 8) + al(8) +
-                                   (MIXED ? al(2 * DIM * ND1 * 4) : 0);
+                                   al(S_L2 * 8) + al(ND2 * 8) +
+                                   (MIXED ? al(NQD * 8) + al(ND2 * 8) : 0);
   static constexpr size_t B_TAB = 3 * al(NQ * P * 8) + al(NQ * K * 8) + al(81 * 8);
   static constexpr size_t BYTES = B_TAB + EPB * B_ELEM;
 };
@@ -838,7 +843,8 @@ __device__ __forceinline__ void l2_contract(const double* gq, double* l2s, const
   }
 }
 
-// One tile of EPB elements [el0, el0 + EPB) of the energy update.
+// One tile of EPB elements [el0, el0 + EPB) of the energy update.  Every
+// thread of the block calls it (it synchronises the block).
 template <int DIM, int K, bool MIXED, int NTT>
 __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, const EnergyArgs& A,
                                             const double* rho0Kp, unsigned char* smem,
@@ -854,88 +860,100 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   double* Wd = reinterpret_cast<double*>(sp); sp += F::al(NQ * P * 8);
   double* Ls = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * 8);
   double* Mi = reinterpret_cast<double*>(sp); sp += F::al(81 * 8);
+  unsigned char* const area = sp;  // element areas, B_ELEM bytes each
+  constexpr size_t O_SCR = F::al(F::NFI * ND1 * 8);
+  constexpr size_t O_GQ = O_SCR + F::al(F::S_INTERP * 8);
+  constexpr size_t O_L2 = O_GQ + F::al(NQD * 8);
+  constexpr size_t O_FTV = O_L2 + F::al(F::S_L2 * 8);
+  constexpr size_t O_PART = O_FTV + F::al(ND2 * 8);
+  constexpr size_t O_FTVP = O_PART + F::al(NQD * 8);
   const int tid = threadIdx.x, le = tid / NQD, tq = tid - le * NQD;
-  unsigned char* ep = sp + le * F::B_ELEM;
-  double* ws = reinterpret_cast<double*>(ep); ep += F::al(F::NFI * ND1 * 8);  // w, then x
-  double* scr = reinterpret_cast<double*>(ep); ep += F::al(F::S_INTERP * 8);
-  double* gq = reinterpret_cast<double*>(ep); ep += F::al(NQD * 8);
-  double* l2s = reinterpret_cast<double*>(ep); ep += F::al(F::S_L2 * 8);
-  double* ftv = reinterpret_cast<double*>(ep); ep += F::al(ND2 * 8);
-  double* crs = reinterpret_cast<double*>(ep); ep += F::al(8);  // coef / (rho0 |J0|)
-  float* whs = reinterpret_cast<float*>(ep);  // mixed: w split into two floats
-  float* wls = whs + DIM * ND1;
+  unsigned char* ep = area + le * F::B_ELEM;
+  double* ws = reinterpret_cast<double*>(ep);  // w, then x
+  double* scr = reinterpret_cast<double*>(ep + O_SCR);
+  double* gq = reinterpret_cast<double*>(ep + O_GQ);
+  double* l2s = reinterpret_cast<double*>(ep + O_L2);
+  double* ftv = reinterpret_cast<double*>(ep + O_FTV);
 
   // slot el0 + le: the element itself, or (list mode) the listed element
+  const int64_t nslots = A.list ? A.nslots : g.nelem;
   const int64_t slot = el0 + le;
-  const bool active = le < F::EPB && slot < (A.list ? A.nslots : g.nelem);
+  const bool active = le < F::EPB && slot < nslots;
   const int64_t el = active ? (A.list ? (int64_t)A.list[slot] : slot) : 0;
   int E[3] = {0, 0, 0};
   elem_ijk(g, el, E);
-  const int nstage = (pref != 0.0) ? 2 * DIM * ND1 : DIM * ND1;
-  if (active) {  // loads first, then the shared-memory stores
-    constexpr int PS = (2 * DIM * ND1 + NQD - 1) / NQD;
-    double sv[PS];
-#pragma unroll
-    for (int j = 0; j < PS; ++j) {
-      const int w = tq + j * NQD;
-      sv[j] = 0.0;
-      if (w < nstage) {
-        const int f = w / ND1, i = w - f * ND1;
-        const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
-        const int64_t node = elem_node<K>(g, E, a, b, cc);
-        sv[j] = f < DIM ? A.w[f * g.nnodes + node] : A.x[(f - DIM) * g.nnodes + node];
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < PS; ++j)
-      if (tq + j * NQD < nstage) ws[tq + j * NQD] = sv[j];
-  }
-  team_sync<NQD>();
 
   if constexpr (MIXED) {
     // F^T w from the stored FP32 element matrix, to ~2^-48: w is split into
     // two floats, each product f w_hi is formed exactly (TwoProduct), the
     // terms are added with error-free sums and the errors collected apart,
     // all on the FP32 pipe.  The team's NQD = 2^DIM ND2 threads split the
-    // DIM ND1 terms of each of the ND2 sums into 2^DIM chunks; the chunk sums
-    // are then added in chunk order and widened to FP64.
+    // DIM ND1 terms of each of the ND2 sums into 2^DIM chunks (thread tq:
+    // row j = tq mod ND2, chunk tq / ND2); each thread loads its chunk's
+    // matrix entries and w values itself, every load issued before the
+    // first use.  The chunk sums are added in chunk order below.
     constexpr int NPART = NQD / ND2, NCI = DIM * ND1, CH = (NCI + NPART - 1) / NPART;
-    float2* part = reinterpret_cast<float2*>(gq);  // NQD pairs per element, free here
-    if (active)
-      for (int w = tq; w < NCI; w += NQD) split_df(ws[w], whs[w], wls[w]);
-    team_sync<NQD>();
+    constexpr int UB = CH < 6 ? CH : 6;  // loads in flight per batch
+    float2* part = reinterpret_cast<float2*>(ep + O_PART);
+    const int j = tq % ND2, pc = tq / ND2;
+    const int c0 = pc * CH, c1 = (c0 + CH < NCI) ? c0 + CH : NCI;
+    float S = 0.0f, C = 0.0f;
     if (active) {
-      const int j = tq % ND2, pc = tq / ND2;
       const float* fk = A.FK + el * (DIM * ND1 * ND2);
-      const int c0 = pc * CH, c1 = (c0 + CH < NCI) ? c0 + CH : NCI;
-      float S = 0.0f, C = 0.0f;
-      for (int ci = c0; ci < c1; ++ci) {
-        const float f = fk[ci * ND2 + j];
-        const float p = __fmul_rn(f, whs[ci]);
-        const float pe = __fmaf_rn(f, whs[ci], -p);  // f w_hi - p, exact
-        float s2, e2;
-        two_sum_f(S, p, s2, e2);
-        S = s2;
-        C = __fadd_rn(C, __fadd_rn(e2, __fmaf_rn(f, wls[ci], pe)));
+      for (int u0 = c0; u0 < c1; u0 += UB) {
+        float fv[UB];
+        double wv[UB];
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          const int ci = u0 + u;
+          fv[u] = 0.0f;
+          wv[u] = 0.0;
+          if (ci < c1) {
+            const int c = ci / ND1, i = ci - c * ND1;
+            const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+            fv[u] = fk[ci * ND2 + j];
+            wv[u] = A.w[c * g.nnodes + elem_node<K>(g, E, a, b, cc)];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < UB; ++u) {
+          if (u0 + u >= c1) break;
+          float wh, wl;
+          split_df(wv[u], wh, wl);
+          const float f = fv[u];
+          const float p = __fmul_rn(f, wh);
+          const float pe = __fmaf_rn(f, wh, -p);  // f w_hi - p, exact
+          float s2, e2;
+          two_sum_f(S, p, s2, e2);
+          S = s2;
+          C = __fadd_rn(C, __fadd_rn(e2, __fmaf_rn(f, wl, pe)));
+        }
       }
       part[tq] = make_float2(S, C);
     }
-    team_sync<NQD>();
-    if (active && tq < ND2) {
-      float S = part[tq].x, C = part[tq].y;
-      for (int pc = 1; pc < NPART; ++pc) {
-        const float2 q = part[pc * ND2 + tq];
-        float s2, e2;
-        two_sum_f(S, q.x, s2, e2);
-        S = s2;
-        C = __fadd_rn(C, __fadd_rn(e2, q.y));
-      }
-      ftv[tq] = f2d_exact(S) + f2d_exact(C);
-    }
     if (pref != 0.0) {
-      // -p_ref alpha_q tr(adj(J) grad w) at the points, J from the FP64 positions
+      // -p_ref alpha_q tr(adj(J) grad w) at the points, J from the FP64
+      // positions, contracted into ftvp
+      if (active) {
+        constexpr int PS = (2 * DIM * ND1 + NQD - 1) / NQD;
+        double sv[PS];
+#pragma unroll
+        for (int jj = 0; jj < PS; ++jj) {
+          const int w = tq + jj * NQD;
+          sv[jj] = 0.0;
+          if (w < 2 * DIM * ND1) {
+            const int f = w / ND1, i = w - f * ND1;
+            const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+            const int64_t node = elem_node<K>(g, E, a, b, cc);
+            sv[jj] = f < DIM ? A.w[f * g.nnodes + node] : A.x[(f - DIM) * g.nnodes + node];
+          }
+        }
+#pragma unroll
+        for (int jj = 0; jj < PS; ++jj)
+          if (tq + jj * NQD < 2 * DIM * ND1) ws[tq + jj * NQD] = sv[jj];
+      }
+      team_sync<NQD>();
       double grad[2 * DIM][DIM];
-      team_sync<NQD>();  // gq is reused
       interp_grads<DIM, K, NQD, 2 * DIM>(ws, 2 * DIM, scr, Bs, Gs, tq, active, grad);
       if (active) {
         const int qx = tq % NQ, qy = (tq / NQ) % NQ, qz = DIM == 3 ? tq / (NQ * NQ) : 0;
@@ -950,9 +968,47 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
         gq[tq] = -pref * alpha * tr;
       }
       team_sync<NQD>();
-      l2_contract<DIM, K, NQD>(gq, l2s, Ls, tq, active, ftv, true);
+      l2_contract<DIM, K, NQD>(gq, l2s, Ls, tq, active,
+                               reinterpret_cast<double*>(ep + O_FTVP), false);
+    }
+    __syncthreads();
+    // F^T w rows: the chunk sums of row j in chunk order, widened to FP64
+    for (int idx = tid; idx < F::EPB * ND2; idx += NTT) {
+      const int l = idx / ND2, jr = idx - l * ND2;
+      if (el0 + l >= nslots) continue;
+      const unsigned char* e2p = area + l * F::B_ELEM;
+      const float2* pp = reinterpret_cast<const float2*>(e2p + O_PART);
+      float S2 = pp[jr].x, C2 = pp[jr].y;
+      for (int q = 1; q < NPART; ++q) {
+        const float2 r = pp[q * ND2 + jr];
+        float s2, e2;
+        two_sum_f(S2, r.x, s2, e2);
+        S2 = s2;
+        C2 = __fadd_rn(C2, __fadd_rn(e2, r.y));
+      }
+      double f = f2d_exact(S2) + f2d_exact(C2);
+      if (pref != 0.0) f += reinterpret_cast<const double*>(e2p + O_FTVP)[jr];
+      reinterpret_cast<double*>(area + l * F::B_ELEM + O_FTV)[jr] = f;
     }
   } else {
+    if (active) {  // loads first, then the shared-memory stores
+      constexpr int PS = (DIM * ND1 + NQD - 1) / NQD;
+      double sv[PS];
+#pragma unroll
+      for (int jj = 0; jj < PS; ++jj) {
+        const int w = tq + jj * NQD;
+        sv[jj] = 0.0;
+        if (w < DIM * ND1) {
+          const int f = w / ND1, i = w - f * ND1;
+          const int a = i % P, b = (i / P) % P, cc = DIM == 3 ? i / (P * P) : 0;
+          sv[jj] = A.w[f * g.nnodes + elem_node<K>(g, E, a, b, cc)];
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < PS; ++jj)
+        if (tq + jj * NQD < DIM * ND1) ws[tq + jj * NQD] = sv[jj];
+    }
+    team_sync<NQD>();
     double gw[DIM][DIM];
     interp_grads<DIM, K, NQD, DIM>(ws, DIM, scr, Bs, Gs, tq, active, gw);
     if (active) {
@@ -965,26 +1021,30 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
     team_sync<NQD>();
     l2_contract<DIM, K, NQD>(gq, l2s, Ls, tq, active, ftv, false);
   }
-  if (A.FTvE != nullptr) {  // list mode: the element rows of F^T w only
-    if (active)
-      for (int j = tq; j < ND2; j += NQD) A.FTvE[slot * ND2 + j] = ftv[j];
-    team_sync<NQD>();
-    return;
-  }
-  if (active && tq == 0) crs[0] = A.rho0Kinv ? coef * A.rho0Kinv[el] : coef / rho0Kp[el];
-  team_sync<NQD>();
-  if (active)
-    for (int j = tq; j < ND2; j += NQD) {
-      // M_E,K^{-1} = Mref^{-1} / (rho0 |J0|)_K, applied to F^T w + src
-      double s = 0.0;
-      for (int l = 0; l < ND2; ++l) {
-        double rhs = ftv[l];
-        if (A.srcE) rhs += A.srcE[el * ND2 + l];
-        s = fma(Mi[j * ND2 + l], rhs, s);
-      }
-      A.e_out[el * ND2 + j] = A.rate ? crs[0] * s : fma(crs[0], s, A.e_base[el * ND2 + j]);
+  __syncthreads();
+  // per (element, row) of the tile: the F^T w rows (list mode), or
+  // e_out = e_base + coef M_E,K^{-1} (F^T w + src) with
+  // M_E,K^{-1} = Mref^{-1} / (rho0 |J0|)_K
+  for (int idx = tid; idx < F::EPB * ND2; idx += NTT) {
+    const int l = idx / ND2, jr = idx - l * ND2;
+    const int64_t sl = el0 + l;
+    if (sl >= nslots) continue;
+    const double* fv = reinterpret_cast<const double*>(area + l * F::B_ELEM + O_FTV);
+    if (A.FTvE != nullptr) {
+      A.FTvE[sl * ND2 + jr] = fv[jr];
+      continue;
     }
-  team_sync<NQD>();  // the team reuses its element area in the next tile
+    const int64_t e2 = sl;  // the energy update runs over all elements
+    const double crs = A.rho0Kinv ? coef * A.rho0Kinv[e2] : coef / rho0Kp[e2];
+    double s = 0.0;
+    for (int q = 0; q < ND2; ++q) {
+      double rhs = fv[q];
+      if (A.srcE) rhs += A.srcE[e2 * ND2 + q];
+      s = fma(Mi[jr * ND2 + q], rhs, s);
+    }
+    A.e_out[e2 * ND2 + jr] = A.rate ? crs * s : fma(crs, s, A.e_base[e2 * ND2 + jr]);
+  }
+  __syncthreads();  // the element areas are reused by the next tile
 }
 
 template <int DIM, int K, bool MIXED>
