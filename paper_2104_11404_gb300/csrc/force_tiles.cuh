@@ -882,6 +882,16 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   const int64_t el = active ? (A.list ? (int64_t)A.list[slot] : slot) : 0;
   int E[3] = {0, 0, 0};
   elem_ijk(g, el, E);
+  // the (element, row) pair this thread updates at the end of the tile
+  // (EPB ND2 = NTT / 2^DIM pairs): its loads are issued now
+  static_assert(F::EPB * ND2 <= NTT, "one (element, row) pair per thread");
+  const int lo = tid / ND2, jo = tid - lo * ND2;
+  const bool out = tid < F::EPB * ND2 && el0 + lo < nslots;
+  double eb = 0.0, rk = 1.0;
+  if (out && A.FTvE == nullptr) {
+    if (!A.rate) eb = A.e_base[(el0 + lo) * ND2 + jo];
+    rk = A.rho0Kinv ? A.rho0Kinv[el0 + lo] : rho0Kp[el0 + lo];
+  }
 
   if constexpr (MIXED) {
     // F^T w from the stored FP32 element matrix, to ~2^-48: w is split into
@@ -1025,24 +1035,21 @@ __device__ __forceinline__ void energy_tile(const Geom& g, const Basis1D& bas, c
   // per (element, row) of the tile: the F^T w rows (list mode), or
   // e_out = e_base + coef M_E,K^{-1} (F^T w + src) with
   // M_E,K^{-1} = Mref^{-1} / (rho0 |J0|)_K
-  for (int idx = tid; idx < F::EPB * ND2; idx += NTT) {
-    const int l = idx / ND2, jr = idx - l * ND2;
-    const int64_t sl = el0 + l;
-    if (sl >= nslots) continue;
-    const double* fv = reinterpret_cast<const double*>(area + l * F::B_ELEM + O_FTV);
+  if (out) {
+    const int64_t sl = el0 + lo;
+    const double* fv = reinterpret_cast<const double*>(area + lo * F::B_ELEM + O_FTV);
     if (A.FTvE != nullptr) {
-      A.FTvE[sl * ND2 + jr] = fv[jr];
-      continue;
+      A.FTvE[sl * ND2 + jo] = fv[jo];
+    } else {
+      const double crs = A.rho0Kinv ? coef * rk : coef / rk;
+      double s = 0.0;
+      for (int q = 0; q < ND2; ++q) {
+        double rhs = fv[q];
+        if (A.srcE) rhs += A.srcE[sl * ND2 + q];
+        s = fma(Mi[jo * ND2 + q], rhs, s);
+      }
+      A.e_out[sl * ND2 + jo] = A.rate ? crs * s : fma(crs, s, eb);
     }
-    const int64_t e2 = sl;  // the energy update runs over all elements
-    const double crs = A.rho0Kinv ? coef * A.rho0Kinv[e2] : coef / rho0Kp[e2];
-    double s = 0.0;
-    for (int q = 0; q < ND2; ++q) {
-      double rhs = fv[q];
-      if (A.srcE) rhs += A.srcE[e2 * ND2 + q];
-      s = fma(Mi[jr * ND2 + q], rhs, s);
-    }
-    A.e_out[e2 * ND2 + jr] = A.rate ? crs * s : fma(crs, s, A.e_base[e2 * ND2 + jr]);
   }
   __syncthreads();  // the element areas are reused by the next tile
 }
