@@ -44,9 +44,11 @@ struct FL {
   static constexpr size_t B_SCR = al(SCR * sizeof(T));
   static constexpr size_t B_L2 = al(S_L2 * sizeof(double));
   static constexpr size_t B_ELEM = B_XS + B_VS + B_WS + B_ES + B_DQ + B_GQ + B_FK + B_SCR + B_L2;
+  // basis tables; the mixed path adds the products B L and G L of the
+  // contractions into F_K: [x][a K + j] = B_a(x) L_j(x) (resp. G_a(x) L_j(x))
   static constexpr size_t B_TAB = al(NQ * P * sizeof(T)) * 2 + al(NQ * K * sizeof(T)) +
                                   al(NQ * K * sizeof(double)) + al(NQ * sizeof(double)) +
-                                  al(NQ * sizeof(T));
+                                  al(NQ * sizeof(T)) + (MIXED ? 2 * al(NQ * PK * sizeof(float)) : 0);
   static constexpr size_t BYTES = B_TAB + EPB * B_ELEM + NTT * sizeof(unsigned long long);
 };
 
@@ -134,6 +136,17 @@ __device__ __forceinline__ void force_tables(const Basis1D& bas, unsigned char* 
     Wd[i] = bas.W[i];
     Wt[i] = tab<T>(bas.W[i], bas.Wf[i]);
   }
+  if constexpr (MIXED) {
+    constexpr int PK = F::PK;
+    sp += F::al(NQ * sizeof(T));
+    float* BLt = reinterpret_cast<float*>(sp); sp += F::al(NQ * PK * sizeof(float));
+    float* GLt = reinterpret_cast<float*>(sp);
+    for (int i = tid; i < NQ * PK; i += blockDim.x) {
+      const int x = i / PK, u = i - x * PK, a = u / K, j = u - a * K;
+      BLt[i] = __fmul_rn(bas.Bf[x][a], bas.Lf[x][j]);
+      GLt[i] = __fmul_rn(bas.Gf[x][a], bas.Lf[x][j]);
+    }
+  }
 }
 
 // One tile of EPB element slots [slot0, slot0 + EPB) of the force evaluation,
@@ -159,6 +172,12 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
   double* Ld = reinterpret_cast<double*>(sp); sp += F::al(NQ * K * sizeof(double));
   double* Wd = reinterpret_cast<double*>(sp); sp += F::al(NQ * sizeof(double));
   T* Wt = reinterpret_cast<T*>(sp); sp += F::al(NQ * sizeof(T));
+  const float* BLt = nullptr;
+  const float* GLt = nullptr;
+  if constexpr (MIXED) {
+    BLt = reinterpret_cast<const float*>(sp); sp += F::al(NQ * F::PK * sizeof(float));
+    GLt = reinterpret_cast<const float*>(sp); sp += F::al(NQ * F::PK * sizeof(float));
+  }
   unsigned long long* red = reinterpret_cast<unsigned long long*>(smem + F::B_TAB + F::EPB * F::B_ELEM);
 
   const int tid = threadIdx.x;
@@ -465,72 +484,111 @@ __device__ __forceinline__ void force_tile(const Geom& g, const Phys& ph, const 
     }
     }
   } else {
-    // Mixed: F_K[(c,i), j] = sum_q phi_j(q) sum_m D[c][m](q) d_m w_i(q) in FP32
+    // Mixed: F_K[(c,i), j] = sum_q phi_j(q) sum_m D[c][m](q) d_m w_i(q) in FP32,
+    // one direction at a time (sum factorisation).  The factor of direction
+    // d is B_a L_j, or G_a L_j along the derivative's direction m = d, taken
+    // from the product tables (each product rounded once, as a product
+    // formed on the fly).  A work item holds the NQ points of one line in
+    // registers and produces all PK = P K (a, j) outputs of that line; the
+    // terms of every sum are added in point order (m, then the point, in the
+    // last direction).
     constexpr int PK = F::PK;
     if constexpr (DIM == 2) {
-      T* Y = scr;
+      T* Y = scr;  // [cm][u = (b, jy)][x]
       if (active)
-        for (int w = tq; w < DIM * DIM * PK * NQ; w += TEAM) {
-          int x_ = w % NQ, u = (w / NQ) % PK, cm = w / (NQ * PK), m = cm % DIM;
-          int b = u / K, jy = u - b * K;
-          const T* X = (m == 1) ? Gs : Bs;
-          T s = T(0);
-          for (int y_ = 0; y_ < NQ; ++y_)
-            s += X[y_ * P + b] * Ls[y_ * K + jy] * dq[cm * NQD + y_ * NQ + x_];
-          Y[w] = s;
+        for (int it = tq; it < DIM * DIM * NQ; it += TEAM) {
+          const int x_ = it % NQ, cm = it / NQ, m = cm % DIM;
+          const float* Ty = (m == 1) ? GLt : BLt;
+          float dv[NQ];
+#pragma unroll
+          for (int y_ = 0; y_ < NQ; ++y_) dv[y_] = dq[cm * NQD + y_ * NQ + x_];
+#pragma unroll
+          for (int u = 0; u < PK; ++u) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int y_ = 0; y_ < NQ; ++y_) acc = fmaf(Ty[y_ * PK + u], dv[y_], acc);
+            Y[(cm * PK + u) * NQ + x_] = acc;
+          }
         }
       team_sync<TEAM>();
       if (active)
-        for (int w = tq; w < DIM * ND1 * ND2; w += TEAM) {
-          int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
-          int a = i % P, b = i / P, jx = j % K, jy = j / K;
-          T s = T(0);
-          for (int m = 0; m < DIM; ++m) {
-            const T* X = (m == 0) ? Gs : Bs;
-            for (int x_ = 0; x_ < NQ; ++x_)
-              s += X[x_ * P + a] * Ls[x_ * K + jx] * Y[(((c * DIM + m) * PK + b * K + jy) * NQ) + x_];
+        for (int it = tq; it < DIM * PK; it += TEAM) {
+          const int c = it / PK, u = it - c * PK, b = u / K, jy = u - b * K;
+          float yv[DIM][NQ];
+#pragma unroll
+          for (int m = 0; m < DIM; ++m)
+#pragma unroll
+            for (int x_ = 0; x_ < NQ; ++x_) yv[m][x_] = Y[((c * DIM + m) * PK + u) * NQ + x_];
+#pragma unroll
+          for (int v = 0; v < PK; ++v) {
+            const int a = v / K, jx = v - a * K;
+            float acc = 0.0f;
+#pragma unroll
+            for (int m = 0; m < DIM; ++m) {
+              const float* Tx = (m == 0) ? GLt : BLt;
+#pragma unroll
+              for (int x_ = 0; x_ < NQ; ++x_) acc = fmaf(Tx[x_ * PK + v], yv[m][x_], acc);
+            }
+            fk[(c * ND1 + a + P * b) * ND2 + jx + K * jy] = acc;
           }
-          fk[w] = s;
         }
     } else {
-      T* Y = scr;
-      T* Z = scr + DIM * DIM * PK * NQ * NQ;
+      T* Y = scr;                                 // [cm][uz][y][x]
+      T* Z = scr + DIM * DIM * PK * NQ * NQ;      // [cm][uz][uy][x]
       if (active)
-        for (int w = tq; w < DIM * DIM * PK * NQ * NQ; w += TEAM) {
-          int x_ = w % NQ, y_ = (w / NQ) % NQ, u = (w / (NQ * NQ)) % PK, cm = w / (NQ * NQ * PK);
-          int m = cm % DIM, cz = u / K, jz = u - cz * K;
-          const T* X = (m == 2) ? Gs : Bs;
-          T s = T(0);
-          for (int z_ = 0; z_ < NQ; ++z_)
-            s += X[z_ * P + cz] * Ls[z_ * K + jz] * dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
-          Y[w] = s;
-        }
-      team_sync<TEAM>();
-      if (active)
-        for (int w = tq; w < DIM * DIM * PK * PK * NQ; w += TEAM) {
-          int x_ = w % NQ, uy = (w / NQ) % PK, uz = (w / (NQ * PK)) % PK, cm = w / (NQ * PK * PK);
-          int m = cm % DIM, b = uy / K, jy = uy - b * K;
-          const T* X = (m == 1) ? Gs : Bs;
-          T s = T(0);
-          for (int y_ = 0; y_ < NQ; ++y_)
-            s += X[y_ * P + b] * Ls[y_ * K + jy] * Y[((cm * PK + uz) * NQ + y_) * NQ + x_];
-          Z[w] = s;
-        }
-      team_sync<TEAM>();
-      if (active)
-        for (int w = tq; w < DIM * ND1 * ND2; w += TEAM) {
-          int j = w % ND2, ci = w / ND2, c = ci / ND1, i = ci - c * ND1;
-          int a = i % P, b = (i / P) % P, cz = i / (P * P);
-          int jx = j % K, jy = (j / K) % K, jz = j / (K * K);
-          int uy = b * K + jy, uz = cz * K + jz;
-          T s = T(0);
-          for (int m = 0; m < DIM; ++m) {
-            const T* X = (m == 0) ? Gs : Bs;
-            for (int x_ = 0; x_ < NQ; ++x_)
-              s += X[x_ * P + a] * Ls[x_ * K + jx] *
-                   Z[((((c * DIM + m) * PK + uz) * PK + uy) * NQ) + x_];
+        for (int it = tq; it < DIM * DIM * NQ * NQ; it += TEAM) {
+          const int x_ = it % NQ, y_ = (it / NQ) % NQ, cm = it / (NQ * NQ), m = cm % DIM;
+          const float* Tz = (m == 2) ? GLt : BLt;
+          float dv[NQ];
+#pragma unroll
+          for (int z_ = 0; z_ < NQ; ++z_) dv[z_] = dq[cm * NQD + (z_ * NQ + y_) * NQ + x_];
+#pragma unroll
+          for (int u = 0; u < PK; ++u) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int z_ = 0; z_ < NQ; ++z_) acc = fmaf(Tz[z_ * PK + u], dv[z_], acc);
+            Y[((cm * PK + u) * NQ + y_) * NQ + x_] = acc;
           }
-          fk[w] = s;
+        }
+      team_sync<TEAM>();
+      if (active)
+        for (int it = tq; it < DIM * DIM * PK * NQ; it += TEAM) {
+          const int x_ = it % NQ, uz = (it / NQ) % PK, cm = it / (NQ * PK), m = cm % DIM;
+          const float* Ty = (m == 1) ? GLt : BLt;
+          float yv[NQ];
+#pragma unroll
+          for (int y_ = 0; y_ < NQ; ++y_) yv[y_] = Y[((cm * PK + uz) * NQ + y_) * NQ + x_];
+#pragma unroll
+          for (int uy = 0; uy < PK; ++uy) {
+            float acc = 0.0f;
+#pragma unroll
+            for (int y_ = 0; y_ < NQ; ++y_) acc = fmaf(Ty[y_ * PK + uy], yv[y_], acc);
+            Z[((cm * PK + uz) * PK + uy) * NQ + x_] = acc;
+          }
+        }
+      team_sync<TEAM>();
+      if (active)
+        for (int it = tq; it < DIM * PK * PK; it += TEAM) {
+          const int uy = it % PK, uz = (it / PK) % PK, c = it / (PK * PK);
+          const int b = uy / K, jy = uy - b * K, cz = uz / K, jz = uz - cz * K;
+          float zv[DIM][NQ];
+#pragma unroll
+          for (int m = 0; m < DIM; ++m)
+#pragma unroll
+            for (int x_ = 0; x_ < NQ; ++x_)
+              zv[m][x_] = Z[((((c * DIM + m) * PK + uz) * PK + uy) * NQ) + x_];
+#pragma unroll
+          for (int v = 0; v < PK; ++v) {
+            const int a = v / K, jx = v - a * K;
+            float acc = 0.0f;
+#pragma unroll
+            for (int m = 0; m < DIM; ++m) {
+              const float* Tx = (m == 0) ? GLt : BLt;
+#pragma unroll
+              for (int x_ = 0; x_ < NQ; ++x_) acc = fmaf(Tx[x_ * PK + v], zv[m][x_], acc);
+            }
+            fk[(c * ND1 + a + P * (b + P * cz)) * ND2 + jx + K * (jy + K * jz)] = acc;
+          }
         }
     }
     team_sync<TEAM>();

@@ -19,12 +19,57 @@
 
 namespace lagh {
 
+// Square root, quotient and hypotenuse in the working precision: correctly
+// rounded in FP64.  In FP32 the 2D point physics issues a dozen of them per
+// point, so these take the single hardware approximations (reciprocal and
+// reciprocal square root, about one unit in the last place) with products
+// that are never fused: every template instance then computes the same bits,
+// whatever launch shape it is compiled for.
+__device__ __forceinline__ float rcp_approx(float a) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float a) {
+  float r;
+  asm("rsqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 template <typename T> __device__ __forceinline__ T t_sqrt(T a);
 template <> __device__ __forceinline__ double t_sqrt<double>(double a) { return sqrt(a); }
-template <> __device__ __forceinline__ float t_sqrt<float>(float a) { return sqrtf(a); }
+// a rsqrt(a) for finite a > 0; 0, +inf (and NaN) map to themselves
+template <> __device__ __forceinline__ float t_sqrt<float>(float a) {
+  return (a > 0.0f && a < __int_as_float(0x7f800000)) ? __fmul_rn(a, rsqrt_approx(a)) : a;
+}
+template <typename T> __device__ __forceinline__ T t_div(T a, T b);
+template <> __device__ __forceinline__ double t_div<double>(double a, double b) { return a / b; }
+template <> __device__ __forceinline__ float t_div<float>(float a, float b) {
+  return __fmul_rn(a, rcp_approx(b));
+}
 template <typename T> __device__ __forceinline__ T t_hypot(T a, T b);
 template <> __device__ __forceinline__ double t_hypot<double>(double a, double b) { return hypot(a, b); }
-template <> __device__ __forceinline__ float t_hypot<float>(float a, float b) { return hypotf(a, b); }
+// FP32: |(a, b)| without rescaling (the mixed path's gradients and strain
+// rates are far from the FP32 overflow range; squares below the underflow
+// range stand for a vanishing vector)
+template <> __device__ __forceinline__ float t_hypot<float>(float a, float b) {
+  return t_sqrt<float>(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)));
+}
+
+// The point physics takes the approximate FP32 forms in 2D.  In 3D it keeps
+// correctly rounded quotients and square roots: there the mixed path's
+// velocity after a whole 3D blast run sits close to its 1e-4 bound against
+// the FP64 run, and the approximations (measured) carry it past the bound.
+template <typename T> __device__ __forceinline__ T ieee_sqrt(T a);
+template <> __device__ __forceinline__ double ieee_sqrt<double>(double a) { return sqrt(a); }
+template <> __device__ __forceinline__ float ieee_sqrt<float>(float a) { return sqrtf(a); }
+template <typename T, int DIM> __device__ __forceinline__ T q_sqrt(T a) {
+  if constexpr (DIM == 2) return t_sqrt<T>(a);
+  else return ieee_sqrt<T>(a);
+}
+template <typename T, int DIM> __device__ __forceinline__ T q_div(T a, T b) {
+  if constexpr (DIM == 2) return t_div<T>(a, b);
+  else return a / b;
+}
 template <typename T> __device__ __forceinline__ T t_abs(T a) { return a < T(0) ? -a : a; }
 template <typename T> __device__ __forceinline__ T t_inf();
 template <> __device__ __forceinline__ double t_inf<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
@@ -82,9 +127,11 @@ __device__ __forceinline__ void jacobi_sym3(T (&S)[3][3], T (&V)[3][3]) {
       const int q = r == 0 ? 1 : 2;
       T spq = S[p][q];
       if (spq == T(0)) continue;
+      // a correctly rounded quotient here: spq may be subnormal with an exactly
+      // zero numerator (theta = 0, a 45 degree rotation)
       T theta = (S[q][q] - S[p][p]) / (T(2) * spq);
-      T t = (theta >= T(0) ? T(1) : T(-1)) / (t_abs(theta) + t_sqrt(theta * theta + T(1)));
-      T cs = T(1) / t_sqrt(t * t + T(1));
+      T t = (theta >= T(0) ? T(1) : T(-1)) / (t_abs(theta) + ieee_sqrt(theta * theta + T(1)));
+      T cs = T(1) / ieee_sqrt(t * t + T(1));
       T sn = t * cs;
       for (int j = 0; j < 3; ++j) {  // rows p, q
         T a = S[p][j], b = S[q][j];
@@ -116,8 +163,8 @@ __device__ __forceinline__ void min_eigenpair(const T (&E)[DIM][DIM], T& lam, T 
     // null vectors (b, lam - a) and (lam - d, b) of E - lam I: keep the longer
     T u0 = b, u1 = lam - a, w0 = lam - d, w1 = b;
     T nu = t_hypot(u0, u1), nw = t_hypot(w0, w1);
-    if (nu >= nw) { s[0] = u0 / nu; s[1] = u1 / nu; }
-    else { s[0] = w0 / nw; s[1] = w1 / nw; }
+    if (nu >= nw) { s[0] = t_div(u0, nu); s[1] = t_div(u1, nu); }
+    else { s[0] = t_div(w0, nw); s[1] = t_div(w1, nw); }
   } else {
     T S[3][3], V[3][3];
     for (int i = 0; i < 3; ++i)
@@ -138,7 +185,7 @@ __device__ __forceinline__ T sigma_min_of(const T (&J)[DIM][DIM], T detJ) {
     // sigma_max = (|(a+d, c-b)| + |(a-d, b+c)|) / 2 and sigma_min = |det| / sigma_max
     T s1 = t_hypot(J[0][0] + J[1][1], J[1][0] - J[0][1]);
     T s2 = t_hypot(J[0][0] - J[1][1], J[0][1] + J[1][0]);
-    return T(2) * t_abs(detJ) / (s1 + s2);
+    return t_div(T(2) * t_abs(detJ), s1 + s2);
   } else {
     T S[3][3], V[3][3];
     for (int i = 0; i < 3; ++i)
@@ -151,7 +198,7 @@ __device__ __forceinline__ T sigma_min_of(const T (&J)[DIM][DIM], T detJ) {
     T m = S[0][0];
     if (S[1][1] < m) m = S[1][1];
     if (S[2][2] < m) m = S[2][2];
-    return t_sqrt(m > T(0) ? m : T(0));
+    return ieee_sqrt(m > T(0) ? m : T(0));
   }
 }
 
@@ -180,17 +227,17 @@ __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&
     for (int n = 0; n < DIM; ++n) sigma[c][n] = T(0);
   if (!isfinite(detJ) || !isfinite(e_q)) { tau = T(0); return kDevNonFinite; }
   if (!(detJ > T(0))) { tau = T(0); return kDevTangled; }
-  T rho = rho0K / detJ;
+  T rho = q_div<T, DIM>(rho0K, detJ);
   T p = (gam - T(1)) * rho * e_q;
   T cs2 = gam * (gam - T(1)) * e_q;
-  T cs = t_sqrt(cs2 > T(0) ? cs2 : T(0));
+  T cs = q_sqrt<T, DIM>(cs2 > T(0) ? cs2 : T(0));
   for (int c = 0; c < DIM; ++c) sigma[c][c] = p_ref - p;
   T hmin = sigma_min_of<T, DIM>(J, detJ) * kinv;
   T mu = T(0);
   if (ph.visc) {
     T A[DIM][DIM], eps[DIM][DIM], gv[DIM][DIM];
     adj_of<T, DIM>(J, A);
-    T idet = T(1) / detJ;
+    T idet = q_div<T, DIM>(T(1), detJ);
     for (int c = 0; c < DIM; ++c)
       for (int n = 0; n < DIM; ++n) {
         T acc = T(0);
@@ -208,22 +255,22 @@ __device__ __forceinline__ int qpoint_physics(const T (&J)[DIM][DIM], const T (&
     T frob = T(0);
     for (int c = 0; c < DIM; ++c)
       for (int n = 0; n < DIM; ++n) frob += eps[c][n] * eps[c][n];
-    frob = t_sqrt(frob);
-    if (lam < -T(1e-5) * (frob + cs / hmin)) {
+    frob = q_sqrt<T, DIM>(frob);
+    if (lam < -T(1e-5) * (frob + q_div<T, DIM>(cs, hmin))) {
       T n2 = T(0);
       for (int c = 0; c < DIM; ++c) {
         T dc = T(0);
         for (int m = 0; m < DIM; ++m) dc += J[c][m] * J0inv[m] * s[m];
         n2 += dc * dc;
       }
-      T ell = ell0 * t_sqrt(n2);
+      T ell = ell0 * q_sqrt<T, DIM>(n2);
       mu = rho * (pconst<T>(ph.q2, ph.q2f) * ell * ell * (-lam) + pconst<T>(ph.q1, ph.q1f) * ell * cs);
       for (int c = 0; c < DIM; ++c)
         for (int n = 0; n < DIM; ++n) sigma[c][n] += mu * eps[c][n];
     }
   }
-  T inv = cs / hmin + pconst<T>(ph.cfl_mu, ph.cfl_muf) * mu / (rho * hmin * hmin);
-  tau = inv > T(0) ? pconst<T>(ph.cfl, ph.cflf) / inv : t_inf<T>();
+  T inv = q_div<T, DIM>(cs, hmin) + q_div<T, DIM>(pconst<T>(ph.cfl_mu, ph.cfl_muf) * mu, rho * hmin * hmin);
+  tau = inv > T(0) ? q_div<T, DIM>(pconst<T>(ph.cfl, ph.cflf), inv) : t_inf<T>();
   return 0;
 }
 
