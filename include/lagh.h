@@ -457,6 +457,14 @@ LH_API lh_status lh_pod(const double* S, int64_t m, int64_t n, const double* off
 LH_API lh_status lh_peak_probe(int32_t fp64, int64_t iters, void* sink, void* stream,
                                double* flops);
 
+/* The same probe with the chains on the first `lanes` lanes of every warp
+ * only (1..32; the other lanes idle), to measure how the pipe time of a warp
+ * instruction depends on its active lanes (the paper has no counterpart).
+ * *flops counts the active lanes' operations only.  Errors: LH_EINVAL
+ * (lanes outside 1..32, or as lh_peak_probe), LH_ECUDA. */
+LH_API lh_status lh_peak_probe_lanes(int32_t fp64, int32_t lanes, int64_t iters, void* sink,
+                                     void* stream, double* flops);
+
 /* ---------------------------------------------------------------------------
  * Batched form: n independent instances of the time step, each on its own
  * Cartesian box mesh with its own physics (a parameter sweep such as the

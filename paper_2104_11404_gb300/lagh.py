@@ -30,7 +30,7 @@ API_NAMES = [
     "lh_batch_layout", "lh_batch_init_state", "lh_batch_set_state", "lh_batch_get_state",
     "lh_batch_query", "lh_batch_run_to", "lh_batch_step_fixed", "lh_batch_total_energy",
     "lh_batch_force_sampled", "lh_batch_autotune", "lh_batch_tuning_get",
-    "lh_check_conversions", "lh_peak_probe", "lh_pod", "lh_batch_snapshots",
+    "lh_check_conversions", "lh_peak_probe", "lh_peak_probe_lanes", "lh_pod", "lh_batch_snapshots",
     "lh_batch_snapshot_count", "lh_rom_create", "lh_rom_destroy", "lh_rom_last_error",
     "lh_rom_info", "lh_rom_set_state", "lh_rom_get_state", "lh_rom_lift", "lh_rom_step_fixed",
     "lh_rom_run_to",
@@ -175,6 +175,8 @@ def load():
     L.lh_rom_run_to.argtypes = [_vp, ctypes.c_double, ctypes.c_int64, P(lh_run_stats)]
     L.lh_peak_probe.argtypes = [ctypes.c_int32, ctypes.c_int64, _vp, _vp,
                                 ctypes.POINTER(ctypes.c_double)]
+    L.lh_peak_probe_lanes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _vp, _vp,
+                                      ctypes.POINTER(ctypes.c_double)]
     for name in API_NAMES:
         if name not in ("lh_default_phys", "lh_status_string", "lh_last_error",
                         "lh_batch_last_error", "lh_rom_last_error"):
@@ -440,6 +442,17 @@ def lh_peak_probe(fp64, iters, sink, stream=None):
     st = load().lh_peak_probe(1 if fp64 else 0, int(iters), _ptr(sink), stream, ctypes.byref(fl))
     if st != LH_OK:
         raise LaghError(st, "lh_peak_probe failed")
+    return fl.value
+
+
+def lh_peak_probe_lanes(fp64, lanes, iters, sink, stream=None):
+    """The probe with the FMA chains on the first `lanes` lanes of every warp;
+    returns the flops of the active lanes (the caller times the launch)."""
+    fl = ctypes.c_double()
+    st = load().lh_peak_probe_lanes(1 if fp64 else 0, int(lanes), int(iters), _ptr(sink), stream,
+                                    ctypes.byref(fl))
+    if st != LH_OK:
+        raise LaghError(st, "lh_peak_probe_lanes failed")
     return fl.value
 
 

@@ -171,3 +171,14 @@ def test_wrappers_reject_unknown_precision_overrides_and_tuning_keys():
         Batch([cfg], tuning={"thread": 256})
     with pytest.raises(ValueError):
         Batch([cfg], precision="single")
+
+
+def test_lane_probe_rejects_lane_counts_outside_a_warp():
+    """lh_peak_probe_lanes checks its arguments before any CUDA call."""
+    import ctypes
+    from paper_2104_11404_gb300 import lagh
+    L = lagh.load()
+    sink = (ctypes.c_double * 8)()
+    for lanes in (0, 33, -1):
+        st = L.lh_peak_probe_lanes(1, lanes, 10, ctypes.cast(sink, ctypes.c_void_p), None, None)
+        assert st == lagh.LH_EINVAL

@@ -414,3 +414,16 @@ def test_cluster_cg_matches_kernel_chain(name, n):
     vc, ec, _, _, _ = gc.get_state()
     vk, ek, _, _, _ = gk.get_state()
     assert rel_l2(host(vk), host(vc)) <= 1e-10 and rel_l2(host(ek), host(ec)) <= 1e-10
+
+
+def test_lane_probe_counts_active_lanes_only():
+    """The FMA probe on a part of every warp reports the flops of the active
+    lanes: 2 x 8 chains x iterations x 8 blocks per SM x 8 warps x lanes."""
+    from paper_2104_11404_gb300 import lagh
+    sink = torch.zeros(8 * 1024, dtype=torch.float64, device="cuda")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for lanes in (32, 4, 1):
+        fl = lagh.lh_peak_probe_lanes(True, lanes, 10, sink, torch.cuda.current_stream().cuda_stream)
+        assert fl == 2.0 * 8 * 10 * 8 * sms * 8 * lanes
+    torch.cuda.synchronize()
+    assert float(sink.abs().sum()) == 0.0
