@@ -15,7 +15,16 @@
 //    away from the diagonal; its entries within a band of half-width B are
 //    kept in FP32 and applied by one line pass per direction (a tile of node
 //    lines and its halo staged in shared memory).  The CG converges in about
-//    three iterations (Jacobi needs ~28 on the 64x64 Taylor-Green mesh);
+//    three iterations (Jacobi needs ~28 on the 64x64 Taylor-Green mesh).  On
+//    narrow meshes (the 2D tile kernel, the narrow line passes, the cluster
+//    solve) of the mixed path, each band entry is the FP32 pair hi + lo of
+//    its FP64 value and every sum is formed without rounding error (exact
+//    products, TwoSum, the errors collected apart): the preconditioner is then
+//    accurate to the FP32 rounding of its input, and the CG converges in two
+//    iterations.  The FP64 path keeps the plain FP32 sums and three
+//    iterations, which take its solves far below the tolerance: it is held to
+//    1e-8 of the oracle after tens of thousands of steps, where the solves'
+//    own errors (up to cond(M_V) times the tolerance) add up;
 //  - Jacobi: the inverse assembled diagonal.
 #include <cooperative_groups.h>
 
@@ -35,6 +44,7 @@ struct CgArgs {
   double M1[(kMaxOrder + 1) * (kMaxOrder + 1)];
   TensorPC tpc;
   const float* lfac;
+  const float* lfac_lo;
   const double* lfac64;
   const double* lchol;
   const double* rhs;
@@ -51,6 +61,7 @@ struct CgArgs {
   int has_cond;
   cudaGraphConditionalHandle cond;
   int standalone;        // a preconditioner application outside a solve: never gated
+  int comp;              // narrow band passes with error-free sums (mixed path)
 };
 
 __device__ __forceinline__ bool gated(const CgArgs& a) {
@@ -154,11 +165,26 @@ template <int K, typename T = float, int LTV = 32>
 struct PassTile {
   static constexpr int B = PB<K>::B, W = 2 * B + 1, TP = 32, ldt = TP + 2 * B + 1;
   static constexpr int LT = LTV;  // node lines per tile
+  // narrow FP32 passes: error-free sums with the band's low parts (band_fma)
+  static constexpr bool COMP = sizeof(T) == 4 && LTV == 8;
   T tile[LT * ldt];
   T wrows[TP * W];
+  float wlo[COMP ? TP * W : 1];
   int64_t lbase[LT];  // first entry of each tile line
   int lflag[LT];      // 0: past the last line, 1: free line, 2: wall-normal line (all zero)
 };
+
+// S + C += (wh + wl) t without rounding error in the main term: the product
+// wh t split exactly into p + pe (FMA), wl t rounded, p added to S by TwoSum
+// and every error collected in C.
+__device__ __forceinline__ void band_fma(float wh, float wl, float t, float& S, float& C) {
+  const float p = __fmul_rn(wh, t);
+  const float pe = __fmaf_rn(wh, t, -p);
+  float s2, e2;
+  two_sum_f(S, p, s2, e2);
+  S = s2;
+  C = __fadd_rn(C, __fadd_rn(e2, __fmaf_rn(wl, t, pe)));
+}
 
 template <int DIM>
 __host__ __device__ __forceinline__ int64_t pass_tiles(const Geom& g, int d, int lt) {
@@ -258,11 +284,19 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
       const int q = idx / W, m = idx - q * W;
       const int row = p0 + q - var;
       T wv = T(0);
+      float wl = 0.0f;
       if (row >= 0 && row < nrow) {
-        if constexpr (sizeof(T) == 8) wv = a.lfac64[a.tpc.off64[d][var] + (int64_t)row * W + m];
-        else wv = a.lfac[a.tpc.off[d][var] + (int64_t)row * W + m];
+        if constexpr (sizeof(T) == 8) {
+          wv = a.lfac64[a.tpc.off64[d][var] + (int64_t)row * W + m];
+        } else {
+          wv = a.lfac[a.tpc.off[d][var] + (int64_t)row * W + m];
+          if constexpr (PT::COMP)
+            if (a.comp) wl = a.lfac_lo[a.tpc.off[d][var] + (int64_t)row * W + m];
+        }
       }
       wrows[idx] = wv;
+      if constexpr (PT::COMP) sm.wlo[idx] = wl;
+      (void)wl;
     }
   }
   __syncthreads();
@@ -278,13 +312,28 @@ __device__ __forceinline__ void pass_tile(const CgArgs& a, int d, int mode, int 
     if (!wall && pos >= var && pos < nd - var) {
       const T* wr = wrows + q * W;
       const T* tr = tile + l * ldt + q;  // tile position of offset -B
-      T acc = T(0);
+      bool done = false;
+      if constexpr (PT::COMP) {
+        if (a.comp) {
+        // error-free sum; the last pass widens S + C to FP64, an inner pass
+        // rounds it to FP32 (the next pass stages FP32 values)
+        const float* wlr = sm.wlo + q * W;
+        float S = 0.0f, C = 0.0f;
 #pragma unroll
-      for (int m = 0; m < W; ++m) {
-        if constexpr (sizeof(T) == 4) acc = __fmaf_rn(wr[m], tr[m], acc);
-        else acc = fma(wr[m], tr[m], acc);
+        for (int m = 0; m < W; ++m) band_fma(wr[m], wlr[m], tr[m], S, C);
+        zv = last ? f2d_exact(S) + f2d_exact(C) : (double)__fadd_rn(S, C);
+        done = true;
+        }
       }
-      zv = (double)acc;
+      if (!done) {
+        T acc = T(0);
+#pragma unroll
+        for (int m = 0; m < W; ++m) {
+          if constexpr (sizeof(T) == 4) acc = __fmaf_rn(wr[m], tr[m], acc);
+          else acc = fma(wr[m], tr[m], acc);
+        }
+        zv = (double)acc;
+      }
     }
     if (mode == 0) {
       const bool ess = wall || pos < var || pos >= nd - var;
@@ -381,9 +430,11 @@ __global__ void __launch_bounds__(kLineThreads, 4) cg_pass_kernel(const CgArgs a
 // 16m elements per direction, joins the tile before it, 17 wide).  It stages
 // the input over the tile and a +-B window in both directions, applies the x
 // band to every window row at the tile's columns, then the y band to that.
-// Each output is the same FP32 sum of the same products, in the same order,
-// as the x pass followed by the y pass, so the result is bitwise that of the
-// two line passes (which round the x result to FP64 and back, exactly).
+// Each output is the same sum of the same products, in the same order, as
+// the narrow x pass followed by the y pass (plain FP32, or error-free with
+// band_fma on the mixed path, the x result rounded once to FP32), so the
+// result is bitwise that of the two line passes (which widen the rounded x
+// result to FP64 and back, exactly).
 //
 // mode / init / upd as for cg_pass_kernel, with both passes in this one
 // (first and last): mode 0 initial (b.b and r.z), upd 1 the CG update fused
@@ -401,6 +452,8 @@ struct Pass2DTile {
   float tx[WN * TM];     // x-band result on the window rows at the tile columns
   float wxT[W * TM];     // x band rows of the tile columns, [m][column]
   float wy[TM * W];      // y band rows of the tile rows, [row][m]
+  float wxTl[W * TM];    // their low parts (band_fma)
+  float wyl[TM * W];
 };
 
 // Tiles along a line of n nodes: 16 wide, the last one ragged or 17 wide.
@@ -456,18 +509,22 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
   // operands of this thread's outputs, then the window in batches of 8.
   constexpr int PB_ = (TM * W + NT - 1) / NT, PO = (TM * TM + NT - 1) / NT;
   const int vx = (c == 0) ? 1 : 0, vy = (c == 1) ? 1 : 0;
-  float bxv[PB_], byv[PB_];
+  float bxv[PB_], byv[PB_], bxl[PB_], byl[PB_];
   {
-    const float* fx = a.lfac + a.tpc.off[0][vx];
-    const float* fy = a.lfac + a.tpc.off[1][vy];
+    const int64_t ox = a.tpc.off[0][vx], oy = a.tpc.off[1][vy];
 #pragma unroll
     for (int j = 0; j < PB_; ++j) {
       const int idx = tid + j * NT;
       const int qq = idx / W, m = idx - qq * W;
       const int rx = x0 + qq - vx, ry = y0 + qq - vy;
       const bool inb = idx < TM * W;
-      bxv[j] = (inb && qq < wx && rx >= 0 && rx < n0 - 2 * vx) ? fx[(int64_t)rx * W + m] : 0.0f;
-      byv[j] = (inb && qq < wy && ry >= 0 && ry < n1 - 2 * vy) ? fy[(int64_t)ry * W + m] : 0.0f;
+      const bool okx = inb && qq < wx && rx >= 0 && rx < n0 - 2 * vx;
+      const bool oky = inb && qq < wy && ry >= 0 && ry < n1 - 2 * vy;
+      const int64_t kx = ox + (int64_t)rx * W + m, ky = oy + (int64_t)ry * W + m;
+      bxv[j] = okx ? a.lfac[kx] : 0.0f;
+      bxl[j] = (okx && a.comp) ? a.lfac_lo[kx] : 0.0f;
+      byv[j] = oky ? a.lfac[ky] : 0.0f;
+      byl[j] = (oky && a.comp) ? a.lfac_lo[ky] : 0.0f;
     }
   }
   double o_r[PO], o_ap[PO], o_p[PO], o_x[PO];
@@ -526,19 +583,26 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
       const int qq = idx / W, m = idx - qq * W;
       sm.wxT[m * TM + qq] = bxv[j];
       sm.wy[idx] = byv[j];
+      sm.wxTl[m * TM + qq] = bxl[j];
+      sm.wyl[idx] = byl[j];
     }
   }
   __syncthreads();
   // x band on the window rows, tile columns (zero off the free set)
   for (int o = tid; o < WN * TM; o += NT) {
     const int wyi = o / TM, qq = o - wyi * TM;
-    float acc = 0.0f;
+    float S = 0.0f, C = 0.0f;
     if (qq < wx && wyi < wny && is_free(x0 + qq, y0 - B + wyi)) {
       const float* wr = sm.win + wyi * ldw + qq;
+      if (a.comp) {
 #pragma unroll
-      for (int m = 0; m < W; ++m) acc = __fmaf_rn(sm.wxT[m * TM + qq], wr[m], acc);
+        for (int m = 0; m < W; ++m) band_fma(sm.wxT[m * TM + qq], sm.wxTl[m * TM + qq], wr[m], S, C);
+      } else {
+#pragma unroll
+        for (int m = 0; m < W; ++m) S = __fmaf_rn(sm.wxT[m * TM + qq], wr[m], S);
+      }
     }
-    sm.tx[o] = acc;
+    sm.tx[o] = a.comp ? __fadd_rn(S, C) : S;
   }
   __syncthreads();
   double l_bb = 0.0, l_rz = 0.0, l_rr = 0.0;
@@ -554,10 +618,17 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
     if (fr) {
       const float* tr = sm.tx + yl * TM + q;  // window row y - B
       const float* wr = sm.wy + yl * W;
-      float acc = 0.0f;
+      const float* wl = sm.wyl + yl * W;
+      float S = 0.0f, C = 0.0f;
+      if (a.comp) {
 #pragma unroll
-      for (int m = 0; m < W; ++m) acc = __fmaf_rn(wr[m], tr[m * TM], acc);
-      zv = (double)acc;
+        for (int m = 0; m < W; ++m) band_fma(wr[m], wl[m], tr[m * TM], S, C);
+        zv = f2d_exact(S) + f2d_exact(C);
+      } else {
+#pragma unroll
+        for (int m = 0; m < W; ++m) S = __fmaf_rn(wr[m], tr[m * TM], S);
+        zv = (double)S;
+      }
     }
     double rv = o_r[j];
     if (mode == 0) {
@@ -1183,6 +1254,8 @@ static CgArgs make_args(const lh_ctx* c, const double* rhs, double* out, const C
     for (int j = 0; j <= kMaxOrder; ++j) a.M1[i * (kMaxOrder + 1) + j] = c->basis.M1[i][j];
   a.tpc = c->tpc;
   a.lfac = c->a.lfac;
+  a.comp = c->precision == LH_MIXED ? 1 : 0;
+  a.lfac_lo = c->a.lfac_lo;
   a.lfac64 = c->a.lfac64;
   a.lchol = c->a.lchol;
   a.rhs = rhs;
@@ -1482,6 +1555,18 @@ cudaError_t cg_solve_eager(const lh_ctx* c, const double* rhs, double* out, cuda
 // per iteration, so the usual iterations run without it.
 constexpr int kUnrolled = 3;
 
+// The iterations a solve usually takes, unrolled ahead of the WHILE node:
+// none for Jacobi (tens of iterations), one with the exact inverse, two with
+// the FP64 band or the error-free narrow passes (mixed path), three with the
+// FP32 band.
+static int usual_iterations(const lh_ctx* c) {
+  if (!c->tpc.enabled) return 0;
+  if (c->tpc.exact) return 1;
+  const bool narrow = c->g.dim == 2 ? narrow_passes<2>(c) : narrow_passes<3>(c);
+  if (c->tpc.fp64 || (narrow && c->precision == LH_MIXED)) return 2;
+  return kUnrolled;
+}
+
 cudaError_t cg_solve_capture(const lh_ctx* c, const double* rhs, double* out, const Ctl* gate,
                              cudaStream_t s, cudaStream_t side) {
   CgArgs a = make_args(c, rhs, out, gate);
@@ -1498,7 +1583,7 @@ cudaError_t cg_solve_capture(const lh_ctx* c, const double* rhs, double* out, co
   cudaGraphConditionalHandle h;
   e = cudaGraphConditionalHandleCreate(&h, cap, 1, cudaGraphCondAssignDefault);
   if (e != cudaSuccess) return e;
-  const int unrolled = c->tpc.enabled ? kUnrolled : 0;  // Jacobi needs tens of iterations
+  const int unrolled = usual_iterations(c);
   for (int u = 0; u < unrolled; ++u) {
     CgArgs au = a;
     au.has_cond = (u == unrolled - 1) ? 1 : 0;

@@ -138,6 +138,7 @@ struct Arrays {
   double *aux;                  // 16 doubles of API scratch (estimates, flags, energy)
   float *lfac;                  // tensor preconditioner bands (FP32)
   double *lfac64;               // the same bands in FP64
+  float *lfac_lo;               // the FP64 bands minus their FP32 roundings, in FP32
   double *lchol;                // exact preconditioner: scaled Cholesky rows (FP64)
   CgDev* cg;
   Ctl* ctl;

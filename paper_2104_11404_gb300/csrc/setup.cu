@@ -320,6 +320,7 @@ static void free_all(lh_ctx* c) {
   if (c->a.lfac) { cudaFree(c->a.lfac); c->a.lfac = nullptr; }
   if (c->a.lchol) { cudaFree(c->a.lchol); c->a.lchol = nullptr; }
   if (c->a.lfac64) { cudaFree(c->a.lfac64); c->a.lfac64 = nullptr; }
+  if (c->a.lfac_lo) { cudaFree(c->a.lfac_lo); c->a.lfac_lo = nullptr; }
   if (c->side) { cudaStreamDestroy(c->side); c->side = nullptr; }
   if (c->ctl_host) { cudaFreeHost(c->ctl_host); c->ctl_host = nullptr; }
   if (c->graph_ready == 1) cudaGraphExecDestroy(c->step_graph);
@@ -493,6 +494,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   // below 1e-9 for B = 14, 22, 30 at k = 1, 2, 3) and applied in FP32.
   std::vector<float> lf;
   std::vector<double> lf64;  // the bands in FP64
+  std::vector<float> lflo;   // the bands' FP32 rounding errors (lf + lflo ~ lf64 to ~2^-48)
   std::vector<double> lc;    // exact variant: scaled banded Cholesky rows
   memset(&c->tpc, 0, sizeof(c->tpc));
   {
@@ -543,6 +545,7 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
         for (double v : band) {
           lf.push_back((float)v);
           lf64.push_back(v);
+          lflo.push_back((float)(v - (double)(float)v));
         }
       }
     }
@@ -561,6 +564,9 @@ extern "C" lh_status lh_create(const lh_mesh_desc* mesh, const lh_disc_desc* dis
   e = dalloc(&A.lfac, lf.size() > 0 ? lf.size() : 1);
   if (e == cudaSuccess && !lf.empty())
     e = cudaMemcpy(A.lfac, lf.data(), lf.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = dalloc(&A.lfac_lo, lflo.size() > 0 ? lflo.size() : 1);
+  if (e == cudaSuccess && !lflo.empty())
+    e = cudaMemcpy(A.lfac_lo, lflo.data(), lflo.size() * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = dalloc(&A.lfac64, lf64.size() > 0 ? lf64.size() : 1);
   if (e == cudaSuccess && !lf64.empty())
     e = cudaMemcpy(A.lfac64, lf64.data(), lf64.size() * sizeof(double), cudaMemcpyHostToDevice);
