@@ -530,9 +530,9 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
   double o_r[PO], o_ap[PO], o_p[PO], o_x[PO];
 #pragma unroll
   for (int j = 0; j < PO; ++j) {
-    const int o = tid + j * NT;
-    const int yl = o / TM, q = o - yl * TM;
-    const bool own = o < TM * TM && q < wx && yl < wy;
+    const int o = tid + j * NT;  // this tile's wy x wx nodes, row by row
+    const int yl = o / wx, q = o - yl * wx;
+    const bool own = o < wx * wy;
     const int x = x0 + q, y = y0 + yl;
     const int64_t kk = own ? cbase + (int64_t)y * n0 + x : 0;
     o_r[j] = o_ap[j] = o_p[j] = o_x[j] = 0.0;
@@ -589,10 +589,11 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
   }
   __syncthreads();
   // x band on the window rows, tile columns (zero off the free set)
-  for (int o = tid; o < WN * TM; o += NT) {
-    const int wyi = o / TM, qq = o - wyi * TM;
+  // (the wny x wx entries the y band reads, spread evenly over the threads)
+  for (int o = tid; o < wny * wx; o += NT) {
+    const int wyi = o / wx, qq = o - wyi * wx;
     float S = 0.0f, C = 0.0f;
-    if (qq < wx && wyi < wny && is_free(x0 + qq, y0 - B + wyi)) {
+    if (is_free(x0 + qq, y0 - B + wyi)) {
       const float* wr = sm.win + wyi * ldw + qq;
       if (a.comp) {
 #pragma unroll
@@ -602,15 +603,15 @@ __global__ void __launch_bounds__(kLineThreads) cg_pass2d_kernel(const CgArgs a,
         for (int m = 0; m < W; ++m) S = __fmaf_rn(sm.wxT[m * TM + qq], wr[m], S);
       }
     }
-    sm.tx[o] = a.comp ? __fadd_rn(S, C) : S;
+    sm.tx[wyi * TM + qq] = a.comp ? __fadd_rn(S, C) : S;
   }
   __syncthreads();
   double l_bb = 0.0, l_rz = 0.0, l_rr = 0.0;
 #pragma unroll
   for (int j = 0; j < PO; ++j) {
     const int o = tid + j * NT;
-    const int yl = o / TM, q = o - yl * TM;
-    if (o >= TM * TM || q >= wx || yl >= wy) continue;
+    const int yl = o / wx, q = o - yl * wx;
+    if (o >= wx * wy) continue;
     const int x = x0 + q, y = y0 + yl;
     const int64_t kk = cbase + (int64_t)y * n0 + x;
     const bool fr = is_free(x, y);
