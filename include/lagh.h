@@ -295,8 +295,10 @@ LH_API lh_status lh_mass_solve_v(lh_ctx* ctx, const double* rhs, double* out,
 /* out = P^{-1} in (device pointers, N_V): one application of the velocity CG's
  * tensor-product preconditioner along every direction, on the non-essential
  * components (essential entries of out are zero): the 1D inverses truncated
- * to a band in FP32 (TENSOR, an approximation of M_V^{-1}) or FP64
- * (TENSOR64), or the exact inverse by banded Cholesky solves (EXACT).
+ * to a band in FP32 (TENSOR, an approximation of M_V^{-1}; a mixed context on
+ * a mesh small enough for the narrow passes keeps each band entry as an FP32
+ * pair hi + lo and sums without rounding error) or FP64 (TENSOR64), or the
+ * exact inverse by banded Cholesky solves (EXACT).
  * Launches lh_layout_info.precond_kernels kernels on the context's stream.
  * LH_EUNSUPPORTED if the context uses the Jacobi preconditioner. */
 LH_API lh_status lh_precond_apply(lh_ctx* ctx, const double* in, double* out);
