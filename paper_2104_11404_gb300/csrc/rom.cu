@@ -98,6 +98,38 @@ __global__ void rom_lift_kernel(int64_t nr, int nb, const double* __restrict__ P
   }
 }
 
+// The three lifts of a stage state in one launch: rows [0, nrv) of v,
+// [nrv, nrv + nre) of e, [nrv + nre, 2 nrv + nre) of x (x uses v's rows);
+// each row as rom_lift_kernel forms it.
+__global__ void rom_lift3_kernel(int64_t nrv, int64_t nre, int nbv, int nbe, int nbx,
+                                 const double* __restrict__ Pv, const double* __restrict__ vos,
+                                 const int64_t* __restrict__ rows_v, const double* __restrict__ cv,
+                                 double* __restrict__ vF, const double* __restrict__ Pe,
+                                 const double* __restrict__ eos, const int64_t* __restrict__ rows_e,
+                                 const double* __restrict__ ce, double* __restrict__ eF,
+                                 const double* __restrict__ Px, const double* __restrict__ xos,
+                                 const double* __restrict__ cx, double* __restrict__ xF,
+                                 const Ctl* ctl) {
+  pdl_enter();
+  if (ctl != nullptr && ctl->done) return;
+  const int64_t n = 2 * nrv + nre;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double *P, *os, *c;
+    const int64_t* rows;
+    double* out;
+    int nb;
+    int64_t i;
+    if (t < nrv) { i = t; P = Pv; os = vos; rows = rows_v; c = cv; out = vF; nb = nbv; }
+    else if (t < nrv + nre) { i = t - nrv; P = Pe; os = eos; rows = rows_e; c = ce; out = eF; nb = nbe; }
+    else { i = t - nrv - nre; P = Px; os = xos; rows = rows_v; c = cx; out = xF; nb = nbx; }
+    double s = os[i];
+    const double* p = P + i * nb;
+    for (int j = 0; j < nb; ++j) s = fma(p[j], c[j], s);
+    out[rows[i]] = s;
+  }
+}
+
 struct RomStage {
   int stage;   // 0 or 1
   int which;   // 0: F.1 part (velocity), 1: F^T w part (energy, position)
@@ -346,18 +378,13 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
     const double* cv = st == 0 ? r->vh : r->vh2;
     const double* ce = st == 0 ? r->eh : r->eh2;
     const double* cx = st == 0 ? r->xh : r->xh2;
-    // lift the stage state at the sampled rows
-    if ((e = launch_k(pdl, rom_lift_kernel, dim3(blocks(r->nrv)), dim3(lb), 0, s, r->nrv, r->nbv,
-                      (const double*)r->Pv, (const double*)r->vos, (const int64_t*)r->rows_v, cv,
-                      r->vF, (const Ctl*)r->ctl)) != cudaSuccess)
-      return e;
-    if ((e = launch_k(pdl, rom_lift_kernel, dim3(blocks(r->nre)), dim3(lb), 0, s, r->nre, r->nbe,
+    // lift the stage state at the sampled rows (v, e, x in one launch)
+    if ((e = launch_k(pdl, rom_lift3_kernel, dim3(blocks(2 * r->nrv + r->nre)), dim3(lb), 0, s,
+                      r->nrv, r->nre, r->nbv, r->nbe, r->nbx, (const double*)r->Pv,
+                      (const double*)r->vos, (const int64_t*)r->rows_v, cv, r->vF,
                       (const double*)r->Pe, (const double*)r->eos, (const int64_t*)r->rows_e, ce,
-                      r->eF, (const Ctl*)r->ctl)) != cudaSuccess)
-      return e;
-    if ((e = launch_k(pdl, rom_lift_kernel, dim3(blocks(r->nrv)), dim3(lb), 0, s, r->nrv, r->nbx,
-                      (const double*)r->Px, (const double*)r->xos, (const int64_t*)r->rows_v, cx,
-                      r->xF, (const Ctl*)r->ctl)) != cudaSuccess)
+                      r->eF, (const double*)r->Px, (const double*)r->xos, cx, r->xF,
+                      (const Ctl*)r->ctl)) != cudaSuccess)
       return e;
     // restricted force: F.1 element rows and the estimate of this stage
     ForceArgs f = {};
