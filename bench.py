@@ -642,7 +642,9 @@ def measure_rom(stream, t_final=0.1):
     bases (0.9999 criterion), SNS bases and over-sampled DEIM (twice the basis
     sizes), then the hyper-reduced online run against the full-order run over
     the same interval: wall time of each time loop, speed-up, and the lifted
-    reduced state's relative L2 error at t = 0.1 (eq:relerrors)."""
+    reduced state's relative L2 error at t = 0.1 (eq:relerrors).  The same
+    bases then run on a mixed context against the mixed full-order run
+    ("mixed": the stress and F_K of the sampled elements in FP32)."""
     import numpy as np
     import torch
     from paper_2104_11404_gb300 import lagh
@@ -701,6 +703,34 @@ def measure_rom(stream, t_final=0.1):
         r.close()
         g.close()
         f.close()
+        # the same reduced model on mixed contexts
+        fm = Hydro(cfg, precision="mixed", stream=stream)
+        fm.init_state()
+        ev0.record(stream)
+        stfm = fm.run_to(t_final)
+        ev1.record(stream)
+        ev1.synchronize()
+        fom_m_ms = ev0.elapsed_time(ev1)
+        gm = Hydro(cfg, precision="mixed", stream=stream)
+        rm = Rom(gm, bases[0], bases[1], bases[2], v0, e0, x0, min(2 * nb[0], gm.nv),
+                 min(2 * nb[1], gm.ne))
+        rm.run_to(t_final)
+        rm.set_state(np.zeros(nb[0]), np.zeros(nb[1]), np.zeros(nb[2]))
+        ev0.record(stream)
+        stm = rm.run_to(t_final)
+        ev1.record(stream)
+        ev1.synchronize()
+        rom_m_ms = ev0.elapsed_time(ev1)
+        mv, me, mx = rm.lift()
+        out["mixed"] = {"fom": {"steps": stfm["steps"], "ms": fom_m_ms},
+                        "rom": {"steps": stm["steps"], "ms": rom_m_ms},
+                        "speedup_rom_over_fom": fom_m_ms / rom_m_ms,
+                        "speedup_over_fp64_fom": fom_ms / rom_m_ms,
+                        "rel_l2_error_at_t_final_vs_fp64_fom": {"v": rel(fv, mv), "e": rel(fe, me),
+                                                               "x": rel(fx, mx)}}
+        rm.close()
+        gm.close()
+        fm.close()
     return out
 
 

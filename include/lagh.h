@@ -373,8 +373,11 @@ LH_API lh_status lh_check_conversions(const double* in, int64_t n, float* f_out,
  * its essential rows zero, as those of F.1, and Phi_G = M_E Phi_e) and DEIM
  * sampling (Section 4.3), under the step control of Section 2.2.3 with the
  * estimate taken over the sampled elements (the lifted state exists only
- * there).  Built on an FP64 context of a problem without an energy source;
- * the context's force kernel evaluates the sampled elements.
+ * there).  Built on a context of a problem without an energy source, FP64
+ * or mixed; the context's force kernel evaluates the sampled elements in its
+ * precision (mixed: FP32 stress and F_K, the error-free F.1 and F^T w sums and
+ * the FP64 reference-pressure part, as in the full-order step), and the
+ * reduced state, projections and updates are FP64.
  * ------------------------------------------------------------------------ */
 typedef struct lh_rom lh_rom;
 typedef struct lh_rom_info_t {
@@ -386,7 +389,7 @@ typedef struct lh_rom_info_t {
   int64_t n_rows_v, n_rows_e;  /* lifted rows (kinematic, thermodynamic) */
 } lh_rom_info_t;
 
-/* Creates the reduced model of ctx (FP64, no source term): Phi_v (N_V x
+/* Creates the reduced model of ctx (no source term): Phi_v (N_V x
  * nb_v), Phi_e (N_E x nb_e), Phi_x (N_V x nb_x) column-major bases and the
  * offsets v_os, e_os, x_os (eq:solrepresentation), all host or device
  * pointers, copied.  ns_f >= nb_v and ns_g >= nb_e sampled entries; samples_f
@@ -397,8 +400,8 @@ typedef struct lh_rom_info_t {
  * Forms the SNS bases, the least-squares matrices (Z^T Phi)^+ of
  * eq:sol-ls-hyper, the sampled elements and their basis rows, and allocates
  * the reduced state (zero).  Errors: LH_EINVAL (sizes, samples, a
- * rank-deficient sampled basis), LH_EUNSUPPORTED (mixed context, source
- * term), LH_ENOMEM, LH_ECUDA.  Basis sizes <= 1024, samples <= 6144. */
+ * rank-deficient sampled basis), LH_EUNSUPPORTED (source term), LH_ENOMEM,
+ * LH_ECUDA.  Basis sizes <= 1024, samples <= 6144. */
 LH_API lh_status lh_rom_create(lh_ctx* ctx, const double* Phi_v, int32_t nb_v,
                                const double* Phi_e, int32_t nb_e, const double* Phi_x,
                                int32_t nb_x, const double* v_os, const double* e_os,

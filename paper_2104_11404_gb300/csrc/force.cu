@@ -104,9 +104,9 @@ static cudaError_t launch_energy_t(const lh_ctx* c, const EnergyArgs& ea, cudaSt
   return launch_k(c->use_pdl != 0, kern, dim3((unsigned)blocks), dim3(F::NT), F::BYTES, s, prm);
 }
 
-template <int DIM, int K>
-static cudaError_t launch_ftv_list_dk(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s) {
-  using F = EL<DIM, K, false>;
+template <int DIM, int K, bool MIXED>
+static cudaError_t launch_ftv_list_t(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s) {
+  using F = EL<DIM, K, MIXED>;
   if (ea.nslots == 0) return cudaSuccess;
   EnergyKParams prm;
   prm.g = c->g;
@@ -114,8 +114,14 @@ static cudaError_t launch_ftv_list_dk(const lh_ctx* c, const EnergyArgs& ea, cud
   prm.a = ea;
   prm.rho0K = c->a.rho0K;
   int64_t blocks = (ea.nslots + F::EPB - 1) / F::EPB;
-  return launch_k(c->use_pdl != 0, energy_update_kernel<DIM, K, false>, dim3((unsigned)blocks),
+  return launch_k(c->use_pdl != 0, energy_update_kernel<DIM, K, MIXED>, dim3((unsigned)blocks),
                   dim3(F::NT), F::BYTES, s, prm);
+}
+
+template <int DIM, int K>
+static cudaError_t launch_ftv_list_dk(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s) {
+  if (c->precision == LH_MIXED) return launch_ftv_list_t<DIM, K, true>(c, ea, s);
+  return launch_ftv_list_t<DIM, K, false>(c, ea, s);
 }
 
 cudaError_t launch_ftv_list(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s) {

@@ -261,8 +261,10 @@ struct EnergyArgs {
   const double* rho0Kinv;  // 1 / (rho0 |J0|) per element (NULL: divide)
 };
 cudaError_t launch_energy_update(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s);
-// F^T w element rows of the listed elements from the stress weights D that the
-// FP64 force kernel stored for them (ea.list, ea.nslots, ea.FTvE, ea.w, ea.D).
+// F^T w element rows of the listed elements from what the force kernel stored
+// for them (ea.list, ea.nslots, ea.FTvE, ea.w): the stress weights D (FP64),
+// or the FP32 element matrices F_K with the FP64 reference-pressure part from
+// ea.x and ea.p_ref (mixed).
 cudaError_t launch_ftv_list(const lh_ctx* c, const EnergyArgs& ea, cudaStream_t s);
 
 // Mass operations.

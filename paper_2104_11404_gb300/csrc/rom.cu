@@ -373,6 +373,7 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
   const int nd1 = g.dim == 3 ? (g.k + 1) * (g.k + 1) * (g.k + 1) : (g.k + 1) * (g.k + 1);
   (void)nd1;
   const size_t zsm = sizeof(double) * (size_t)std::max(r->nsf, r->nsg);
+  const bool mixed = c->precision == LH_MIXED;
   cudaError_t e;
   for (int st = 0; st < 2; ++st) {
     const double* cv = st == 0 ? r->vh : r->vh2;
@@ -391,7 +392,10 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
     f.v = r->vF; f.e = r->eF; f.x = r->xF; f.vtest = nullptr;
     f.list = r->sel; f.nslots = r->nsel;
     f.F1E = r->F1E;
-    f.D = c->a.D;  // stress weights of the sampled elements, for F^T w below
+    // kept for F^T w below: the stress weights (FP64) or the FP32 element
+    // matrices (mixed) of the sampled elements
+    f.D = mixed ? nullptr : c->a.D;
+    f.FK = mixed ? c->a.FK : nullptr;
     f.tau_bits = &r->ctl->tau_bits[st];
     f.status = &r->ctl->status;
     f.ctl = r->ctl;
@@ -417,6 +421,10 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
     EnergyArgs ea = {};
     ea.w = r->wF;
     ea.D = c->a.D;
+    ea.FK = c->a.FK;
+    // mixed: the reference pressure's F^T w in FP64 from the stage positions
+    ea.x = mixed ? r->xF : nullptr;
+    ea.p_ref = mixed ? &c->a.ctl->p_ref : nullptr;
     ea.list = r->sel;
     ea.nslots = r->nsel;
     ea.FTvE = r->FTvE;
@@ -553,8 +561,6 @@ extern "C" lh_status lh_rom_create(lh_ctx* c, const double* Phi_v, int32_t nbv, 
   if (!c || !Phi_v || !Phi_e || !Phi_x || !v_os || !e_os || !x_os) return LH_EINVAL;
   if (nbv < 1 || nbe < 1 || nbx < 1 || nbv > 1024 || nbe > 1024 || nbx > 1024) return LH_EINVAL;
   if (nsf < nbv || nsg < nbe || nsf > 6144 || nsg > 6144) return LH_EINVAL;
-  if (c->precision != LH_FP64)
-    return set_error(c, LH_EUNSUPPORTED, "the hyper-reduced step runs on an FP64 context");
   if (c->ph.source)
     return set_error(c, LH_EUNSUPPORTED, "the hyper-reduced step has no energy source term");
   const Geom& g = c->g;

@@ -177,3 +177,34 @@ def test_gpu_offline_and_online_pipeline_matches_oracle():
     assert np.linalg.norm(le - oe) <= 1e-6 * np.linalg.norm(oe)
     assert np.linalg.norm(lx - ox) <= 1e-8 * np.linalg.norm(ox)
     r.close()
+
+
+def test_mixed_rom_follows_the_fp64_reduced_model():
+    """The hyper-reduced step on a mixed context (FP32 stress and F_K of the
+    sampled elements, error-free F.1 / F^T w sums, FP64 reduced state): step
+    by step within FP32 accuracy of the oracle's FP64 reduced step, and under
+    the step control to t = 0.1 within 1e-4 of the oracle's reduced run."""
+    cfg = _sedov((8, 8))
+    o, (v0, e0, x0), (Pv, Pe, Px), pF, pG = _trained(cfg, 0.1)
+    R = OR.RomOracle(o, Pv, Pe, Px, v0, e0, x0, pF, pG)
+    g = gpu_for(cfg, "mixed")
+    r = _rom(g, Pv, Pe, Px, v0, e0, x0, pF, pG)
+    nb = (Pv.shape[1], Pe.shape[1], Px.shape[1])
+    vh, eh, xh = (np.zeros(n) for n in nb)
+    for dt in (1e-3, 1.5e-3, 2e-3):
+        tau_g = r.step_fixed(dt)
+        vh, eh, xh, tau_o = R.step(dt, vh, eh, xh)
+        assert abs(tau_g - tau_o) <= 1e-5 * tau_o
+        gv, ge, gx, _, _ = r.get_state()
+        for a, b in ((vh, gv), (eh, ge), (xh, gx)):
+            assert np.abs(_host(b) - a).max() <= 1e-5 * max(np.abs(a).max(), 1e-300)
+    r.set_state(np.zeros(nb[0]), np.zeros(nb[1]), np.zeros(nb[2]))
+    st = r.run_to(0.1)
+    ovh, oeh, oxh, t, dt, steps, rejects, log = R.run(0.1, *(np.zeros(n) for n in nb))
+    assert st["t"] == 0.1 and abs(st["steps"] - steps) <= 2
+    ov, oe, ox = R.lift(ovh, oeh, oxh)
+    lv, le, lx = (_host(a) for a in r.lift())
+    assert np.linalg.norm(lv - ov) <= 1e-4 * np.linalg.norm(ov)
+    assert np.linalg.norm(le - oe) <= 1e-4 * np.linalg.norm(oe)
+    assert np.linalg.norm(lx - ox) <= 1e-6 * np.linalg.norm(ox)
+    r.close()
