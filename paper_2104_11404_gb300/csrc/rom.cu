@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(256) rom_update_kernel(
     const double* __restrict__ AF, const double* __restrict__ AG, const double* __restrict__ C,
     const double* __restrict__ bx, double* vh, double* eh, double* xh, double* vh2, double* eh2,
     double* xh2, double* vhn, double* ehn, double* xhn, double* vbar, double* fh, double* gh,
-    const Ctl* ctl) {
+    const Ctl* ctl, Ctl* ctlw, CtlConsts k) {
   pdl_enter();
   if (ctl->done) return;
   extern __shared__ double zs[];
@@ -192,18 +192,20 @@ __global__ void __launch_bounds__(256) rom_update_kernel(
       (rs.stage == 0 ? xh2 : xhn)[j] = xh[j] + c * px;
     }
   }
-}
-
-__global__ void rom_control_kernel(Ctl* ctl, CtlConsts k, int nb, double* cur, const double* cand) {
-  pdl_enter();
-  __shared__ int acc;
-  if (threadIdx.x == 0) {
-    control_update(ctl, k);
-    acc = ctl->accepted;
+  if (ctlw != nullptr) {
+    // end of the attempt (ctlw = the control block): the step control, and
+    // the commit of the candidate coordinates vhn, ehn, xhn (contiguous, as
+    // are vh, eh, xh) if accepted
+    __shared__ int acc;
+    __syncthreads();
+    if (tid == 0) {
+      control_update(ctlw, k);
+      acc = ctlw->accepted;
+    }
+    __syncthreads();
+    if (acc)
+      for (int j = tid; j < nbv + nbe + nbx; j += blockDim.x) vh[j] = vhn[j];
   }
-  __syncthreads();
-  if (acc)
-    for (int j = threadIdx.x; j < nb; j += blockDim.x) cur[j] = cand[j];
 }
 
 __global__ void rom_begin_kernel(Ctl* ctl, double t_final, long long max_steps, double dt_min,
@@ -374,6 +376,10 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
   (void)nd1;
   const size_t zsm = sizeof(double) * (size_t)std::max(r->nsf, r->nsg);
   const bool mixed = c->precision == LH_MIXED;
+  CtlConsts k;
+  k.beta1 = c->phys_desc.beta1;
+  k.beta2 = c->phys_desc.beta2;
+  k.gamma_dt = c->phys_desc.gamma_dt;
   cudaError_t e;
   for (int st = 0; st < 2; ++st) {
     const double* cv = st == 0 ? r->vh : r->vh2;
@@ -409,7 +415,7 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
                       (const int32_t*)r->gg_idx, (const double*)r->AF, (const double*)r->AG,
                       (const double*)r->C, (const double*)r->bx, r->vh, r->eh, r->xh, r->vh2,
                       r->eh2, r->xh2, r->vhn, r->ehn, r->xhn, r->vbar, r->fh, r->gh,
-                      (const Ctl*)r->ctl)) != cudaSuccess)
+                      (const Ctl*)r->ctl, (Ctl*)nullptr, k)) != cudaSuccess)
       return e;
     // the test velocity of the energy equation, lifted at the sampled rows
     const double* cw = st == 0 ? r->vh2 : r->vbar;
@@ -431,22 +437,18 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
     ea.ctl = r->ctl;
     if ((e = launch_ftv_list(c, ea, s)) != cudaSuccess) return e;
     rs.which = 1;
+    // the second stage's energy and position update also ends the attempt:
+    // step control and commit in the same single-CTA kernel
     if ((e = launch_k(pdl, rom_update_kernel, dim3(1), dim3(256), zsm, s, rs, r->nbv, r->nbe, r->nbx,
                       r->nsf, r->nsg, (const double*)r->F1E, (const double*)r->FTvE,
                       (const int32_t*)r->gf_off, (const int32_t*)r->gf_idx,
                       (const int32_t*)r->gg_idx, (const double*)r->AF, (const double*)r->AG,
                       (const double*)r->C, (const double*)r->bx, r->vh, r->eh, r->xh, r->vh2,
                       r->eh2, r->xh2, r->vhn, r->ehn, r->xhn, r->vbar, r->fh, r->gh,
-                      (const Ctl*)r->ctl)) != cudaSuccess)
+                      (const Ctl*)r->ctl, st == 1 ? r->ctl : (Ctl*)nullptr, k)) != cudaSuccess)
       return e;
   }
-  CtlConsts k;
-  k.beta1 = c->phys_desc.beta1;
-  k.beta2 = c->phys_desc.beta2;
-  k.gamma_dt = c->phys_desc.gamma_dt;
-  // the candidate coordinates vhn, ehn, xhn are contiguous, as are vh, eh, xh
-  return launch_k(pdl, rom_control_kernel, dim3(1), dim3(256), 0, s, r->ctl, k,
-                  r->nbv + r->nbe + r->nbx, r->vh, (const double*)r->vhn);
+  return cudaSuccess;
 }
 
 static lh_status rom_build_graph(lh_rom* r) {
