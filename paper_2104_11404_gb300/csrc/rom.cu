@@ -136,8 +136,17 @@ struct RomStage {
 };
 
 // Projection of the sampled entries and the reduced update of one part of a
-// stage, one CTA (the reduced sizes are small).
-__global__ void __launch_bounds__(256) rom_update_kernel(
+// stage, one CTA (the reduced sizes are small).  Each matrix-vector product
+// gives one row to one warp: the lanes take every 32nd column and the warp
+// adds them by a fixed shuffle tree.
+__device__ __forceinline__ double row_dot(const double* __restrict__ row, const double* x, int n,
+                                          int lane) {
+  double acc = 0.0;
+  for (int s = lane; s < n; s += 32) acc = fma(row[s], x[s], acc);
+  return warp_sum(acc);
+}
+
+__global__ void __launch_bounds__(1024) rom_update_kernel(
     RomStage rs, int nbv, int nbe, int nbx, int nsf, int nsg, const double* __restrict__ F1E,
     const double* __restrict__ FTvE, const int32_t* __restrict__ gf_off,
     const int32_t* __restrict__ gf_idx, const int32_t* __restrict__ gg_idx,
@@ -159,10 +168,9 @@ __global__ void __launch_bounds__(256) rom_update_kernel(
       zs[s] = acc;
     }
     __syncthreads();
-    for (int j = tid; j < nbv; j += blockDim.x) {
-      double acc = 0.0;
-      for (int s = 0; s < nsf; ++s) acc = fma(AF[(int64_t)j * nsf + s], zs[s], acc);
-      fh[j] = acc;
+    for (int j = tid >> 5; j < nbv; j += blockDim.x >> 5) {
+      const double acc = row_dot(AF + (int64_t)j * nsf, zs, nsf, tid & 31);
+      if ((tid & 31) == 0) fh[j] = acc;
     }
     __syncthreads();
     for (int j = tid; j < nbv; j += blockDim.x) {
@@ -177,19 +185,18 @@ __global__ void __launch_bounds__(256) rom_update_kernel(
   } else {
     for (int s = tid; s < nsg; s += blockDim.x) zs[s] = FTvE[gg_idx[s]];
     __syncthreads();
-    for (int j = tid; j < nbe; j += blockDim.x) {
-      double acc = 0.0;
-      for (int s = 0; s < nsg; ++s) acc = fma(AG[(int64_t)j * nsg + s], zs[s], acc);
-      gh[j] = acc;
+    for (int j = tid >> 5; j < nbe; j += blockDim.x >> 5) {
+      const double acc = row_dot(AG + (int64_t)j * nsg, zs, nsg, tid & 31);
+      if ((tid & 31) == 0) gh[j] = acc;
     }
     __syncthreads();
     const double* w = rs.stage == 0 ? vh2 : vbar;
     const double c = rs.stage == 0 ? 0.5 * dt : dt;
     for (int j = tid; j < nbe; j += blockDim.x) (rs.stage == 0 ? eh2 : ehn)[j] = eh[j] + c * gh[j];
-    for (int j = tid; j < nbx; j += blockDim.x) {
-      double px = bx[j];  // Phi_x^T (v_os + Phi_v w)
-      for (int l = 0; l < nbv; ++l) px = fma(C[(int64_t)j * nbv + l], w[l], px);
-      (rs.stage == 0 ? xh2 : xhn)[j] = xh[j] + c * px;
+    for (int j = tid >> 5; j < nbx; j += blockDim.x >> 5) {
+      // Phi_x^T (v_os + Phi_v w) = bx + C w
+      const double d = row_dot(C + (int64_t)j * nbv, w, nbv, tid & 31);
+      if ((tid & 31) == 0) (rs.stage == 0 ? xh2 : xhn)[j] = xh[j] + c * (bx[j] + d);
     }
   }
   if (ctlw != nullptr) {
@@ -409,7 +416,7 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
     f.mode = kForceFull;
     if ((e = launch_force(c, f, s)) != cudaSuccess) return e;
     RomStage rs = {st, 0};
-    if ((e = launch_k(pdl, rom_update_kernel, dim3(1), dim3(256), zsm, s, rs, r->nbv, r->nbe, r->nbx,
+    if ((e = launch_k(pdl, rom_update_kernel, dim3(1), dim3(1024), zsm, s, rs, r->nbv, r->nbe, r->nbx,
                       r->nsf, r->nsg, (const double*)r->F1E, (const double*)r->FTvE,
                       (const int32_t*)r->gf_off, (const int32_t*)r->gf_idx,
                       (const int32_t*)r->gg_idx, (const double*)r->AF, (const double*)r->AG,
@@ -439,7 +446,7 @@ static cudaError_t rom_enqueue_attempt(lh_rom* r, cudaStream_t s) {
     rs.which = 1;
     // the second stage's energy and position update also ends the attempt:
     // step control and commit in the same single-CTA kernel
-    if ((e = launch_k(pdl, rom_update_kernel, dim3(1), dim3(256), zsm, s, rs, r->nbv, r->nbe, r->nbx,
+    if ((e = launch_k(pdl, rom_update_kernel, dim3(1), dim3(1024), zsm, s, rs, r->nbv, r->nbe, r->nbx,
                       r->nsf, r->nsg, (const double*)r->F1E, (const double*)r->FTvE,
                       (const int32_t*)r->gf_off, (const int32_t*)r->gf_idx,
                       (const int32_t*)r->gg_idx, (const double*)r->AF, (const double*)r->AG,
